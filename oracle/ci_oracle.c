@@ -1,0 +1,476 @@
+/*
+ * ci_oracle.c -- plain, single-threaded CPU oracle for the chaotic-iterations
+ * (CI) pseudorandom generator of Bahi, Couturier, Guyeux & Heam,
+ * "Efficient and Cryptographically Secure Generation of Chaotic Pseudorandom
+ * Numbers on GPU" (arXiv 1112.5239).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load the shared object built from it.  It shares
+ * no code, header, table or constant generator with the CUDA path.
+ *
+ * It is slow on purpose: one lane at a time, one output at a time, in the
+ * order the paper's algorithms state, with `unsigned __int128 %` for the BBS
+ * modular squaring (the definition, not a fast reduction).
+ *
+ * What it computes (paper construct -> function):
+ *   Eq. (Oplus), x^n = x^{n-1} XOR S^n ............ orc_ci_step
+ *   Algorithm 2 (XORshift round) ................... orc_xorshift32_step
+ *   xor128 with 32-bit words (Sec. 6.2 text) ........ orc_xor128_step
+ *   Algorithm 4 (one xor-like per thread, two
+ *     combination arrays, mixing with the partners'
+ *     previous strategies) ......................... orc_run (xor variant)
+ *   BBS x_{n+1} = x_n^2 mod M (Sec. 9.1) ............ orc_bbs_step
+ *   Algorithm 5 strategy assembly (w-bit chunks,
+ *     two extra shift steps, array_shift) .......... orc_bbs_strategy
+ *   Algorithm 5 (16 combination arrays, selection
+ *     from the BBS state's low bits) ............... orc_run (BBS variant)
+ *   Quarter-circle consumer of output pairs ......... orc_run (counts)
+ *
+ * Readings where the paper is silent or garbled (the same readings the CUDA
+ * path takes; listed with reasons in the design notes):
+ *   - seeding: counter-based splitmix64 replaces the paper's host ISAAC
+ *     (Sec. 6.1): draw(seed, i) = mix64(seed + (i + 1) * gamma); lane s owns
+ *     indices [s * 2^32, (s + 1) * 2^32).
+ *   - synchronous mixing: iteration i reads the partners' strategies of
+ *     iteration i - 1 (what warp lockstep gives Algorithm 4's unsynchronised
+ *     shared-memory read/write); partner = group * C + comb[offset].
+ *   - stream-major output out[s * L + i] = x after the (i + 1)-th update.
+ *   - BBS: one generator per lane, w = floor(log2(floor(log2 M))) bits per
+ *     squaring, ceil(32 / w) chunks, then Algorithm 5's two shift steps;
+ *     combination arrays chosen once from the seed's low bits.
+ *
+ * Parity pins (the tests that tie this file to the paper and to mathematics):
+ *   Table 1 worked example; brute force of the single-cell and subset CI
+ *   definitions on tiny widths; exhaustive period 2^32 - 1 of Algorithm 2;
+ *   full period of xor128 as a GF(2)-linear map; mixing special cases and a
+ *   hand-worked small case; GF(2) linearity; BBS squaring on tiny Blum moduli;
+ *   Algorithm 5's 4-bit packing on hand-fed BBS values; quarter-circle counts
+ *   against the real-number test.  The splitmix64 seeding and the exact xor128
+ *   shift triple are readings taken from outside the paper: their values are
+ *   "parity unpinned" beyond the structural checks above.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Seeding: splitmix64 (Steele, Lea & Flood, OOPSLA 2014), counter-based.     */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_GAMMA 0x9E3779B97F4A7C15ULL
+
+static uint64_t orc_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* The (index + 1)-th output of a splitmix64 generator started at `seed`. */
+uint64_t orc_draw(uint64_t seed, uint64_t index)
+{
+    return orc_mix64(seed + (index + 1) * ORC_GAMMA);
+}
+
+/* Draw k of lane s: index s * 2^32 + k. */
+static uint64_t orc_lane_draw(uint64_t seed, uint64_t lane, uint64_t k)
+{
+    return orc_draw(seed, (lane << 32) + k);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. (Oplus): bit k of the state flips iff bit k of the strategy is 1.      */
+/* ------------------------------------------------------------------------- */
+
+uint32_t orc_ci_step(uint32_t x, uint32_t strategy)
+{
+    return x ^ strategy;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Strategy sources.                                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Algorithm 2: one round of the 32-bit XORshift; returns the new z. */
+uint32_t orc_xorshift32_step(uint32_t z)
+{
+    z = z ^ (z << 13);
+    z = z ^ (z >> 17);
+    z = z ^ (z << 5);
+    return z;
+}
+
+/* Exhaustive period from a nonzero start: number of rounds until the orbit
+ * returns to its start (stops after `limit` rounds and returns 0). */
+uint64_t orc_xorshift32_period(uint32_t start, uint64_t limit)
+{
+    uint32_t z = start;
+    uint64_t n = 0;
+    do {
+        z = orc_xorshift32_step(z);
+        ++n;
+        if (n > limit)
+            return 0;
+    } while (z != start);
+    return n;
+}
+
+/* xor128 with 32-bit words (the Alg. 4 xor-like per Sec. 6.2): s = {a,b,c,d};
+ * the new word d is the output. */
+uint32_t orc_xor128_step(uint32_t *s)
+{
+    uint32_t a = s[0];
+    uint32_t tmp = a ^ (a << 11);
+    s[0] = s[1];
+    s[1] = s[2];
+    s[2] = s[3];
+    s[3] = s[3] ^ (s[3] >> 19) ^ (tmp ^ (tmp >> 8));
+    return s[3];
+}
+
+/* BBS (Sec. 9.1): x_{n+1} = x_n^2 mod M, by the definition. */
+uint64_t orc_bbs_step(uint64_t y, uint64_t M)
+{
+    unsigned __int128 sq = (unsigned __int128)y * (unsigned __int128)y;
+    return (uint64_t)(sq % (unsigned __int128)M);
+}
+
+/* Number of secure low bits per BBS output: floor(log2(floor(log2 M))). */
+uint32_t orc_bbs_w(uint64_t M)
+{
+    uint32_t lg = 0, w = 0;
+    while ((M >> lg) > 1)
+        ++lg;               /* lg = floor(log2 M) */
+    while ((lg >> w) > 1)
+        ++w;                /* w = floor(log2 lg) */
+    return w;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Primes for BBS: trial division (the definition of primality).             */
+/* ------------------------------------------------------------------------- */
+
+int orc_is_prime(uint64_t n)
+{
+    if (n < 2)
+        return 0;
+    if (n % 2 == 0)
+        return n == 2;
+    for (uint64_t d = 3; d * d <= n; d += 2)
+        if (n % d == 0)
+            return 0;
+    return 1;
+}
+
+static uint64_t orc_gcd(uint64_t a, uint64_t b)
+{
+    while (b) {
+        uint64_t r = a % b;
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-lane state.                                                            */
+/* ------------------------------------------------------------------------- */
+
+enum { ORC_VAR_XOR = 0, ORC_VAR_BBS = 1 };
+enum { ORC_XL_XOR128 = 0, ORC_XL_XORSHIFT32 = 1 };
+
+typedef struct {
+    uint32_t w[4];   /* xor-like words: xor128 {a,b,c,d}; xorshift32 uses w[0] */
+    uint32_t x;      /* CI state x */
+    uint32_t tprev;  /* the lane's last strategy (its shared-memory slot)     */
+    uint32_t p, q;   /* BBS Blum primes                                      */
+    uint64_t M;      /* BBS modulus p*q                                      */
+    uint64_t y;      /* BBS state, canonical residue in [0, M)               */
+    uint32_t sel1;   /* BBS: first combination array index, in [0, 8)      */
+    uint32_t sel2;   /* BBS: second combination array index is 8 + sel2    */
+} orc_lane;
+
+uint32_t orc_lane_size(void) { return (uint32_t)sizeof(orc_lane); }
+
+/* xor variant seeding: draws 0 and 1 fill the xor-like words, draw 2 gives x
+ * and the initial shared-memory slot (Alg. 4 loads both with the state). */
+static void orc_init_xor_lane(int xl, uint64_t seed, uint64_t lane, orc_lane *L)
+{
+    memset(L, 0, sizeof *L);
+    uint64_t d0 = orc_lane_draw(seed, lane, 0);
+    uint64_t d1 = orc_lane_draw(seed, lane, 1);
+    uint64_t d2 = orc_lane_draw(seed, lane, 2);
+    if (xl == ORC_XL_XOR128) {
+        L->w[0] = (uint32_t)d0;
+        L->w[1] = (uint32_t)(d0 >> 32);
+        L->w[2] = (uint32_t)d1;
+        L->w[3] = (uint32_t)(d1 >> 32);
+        if ((L->w[0] | L->w[1] | L->w[2] | L->w[3]) == 0)
+            L->w[0] = 1;
+    } else {
+        L->w[0] = (uint32_t)d0;
+        if (L->w[0] == 0)
+            L->w[0] = 1;
+    }
+    L->x = (uint32_t)d2;
+    L->tprev = (uint32_t)(d2 >> 32);
+}
+
+/* BBS seeding by rejection: candidate c = 2^30 + (draw >> 34), c |= 3, kept if
+ * prime; q likewise and distinct from p; seed v = 2 + draw mod (M - 2) kept if
+ * coprime to M; then one draw for x and the initial slot.  The combination
+ * arrays are chosen by v's low bits (sel1 = v & 7, sel2 = (v >> 3) & 7). */
+static void orc_init_bbs_lane(uint64_t seed, uint64_t lane, orc_lane *L)
+{
+    memset(L, 0, sizeof *L);
+    uint64_t k = 0, d, v;
+    uint32_t p, q;
+    do {
+        d = orc_lane_draw(seed, lane, k++);
+        p = (uint32_t)((1ULL << 30) + (d >> 34)) | 3u;
+    } while (!orc_is_prime(p));
+    do {
+        d = orc_lane_draw(seed, lane, k++);
+        q = (uint32_t)((1ULL << 30) + (d >> 34)) | 3u;
+    } while (!orc_is_prime(q) || q == p);
+    uint64_t M = (uint64_t)p * (uint64_t)q;
+    do {
+        d = orc_lane_draw(seed, lane, k++);
+        v = 2 + d % (M - 2);
+    } while (orc_gcd(v, M) != 1);
+    d = orc_lane_draw(seed, lane, k++);
+    L->p = p;
+    L->q = q;
+    L->M = M;
+    L->y = v;
+    L->x = (uint32_t)d;
+    L->tprev = (uint32_t)(d >> 32);
+    L->sel1 = (uint32_t)(v & 7);
+    L->sel2 = (uint32_t)((v >> 3) & 7);
+}
+
+/* Seed lanes [lane0, lane0 + nl) by their global index. */
+void orc_init_lanes(int variant, int xl, uint64_t seed, uint64_t lane0, uint64_t nl,
+                    orc_lane *lanes)
+{
+    for (uint64_t i = 0; i < nl; ++i) {
+        if (variant == ORC_VAR_BBS)
+            orc_init_bbs_lane(seed, lane0 + i, &lanes[i]);
+        else
+            orc_init_xor_lane(xl, seed, lane0 + i, &lanes[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Combination arrays (Alg. 4: two; Alg. 5: sixteen), each a permutation of  */
+/* [0, C) drawn by Fisher-Yates from splitmix64(comb_seed).                   */
+/* ------------------------------------------------------------------------- */
+
+static void orc_permutation(uint32_t C, uint64_t comb_seed, uint64_t *ctr, uint8_t *a)
+{
+    for (uint32_t i = 0; i < C; ++i)
+        a[i] = (uint8_t)i;
+    for (uint32_t i = C - 1; i >= 1; --i) {
+        uint64_t r = orc_draw(comb_seed, (*ctr)++);
+        uint32_t j = (uint32_t)(r % (uint64_t)(i + 1));
+        uint8_t tmp = a[i];
+        a[i] = a[j];
+        a[j] = tmp;
+    }
+}
+
+/* Writes 2*C bytes (xor) or 16*C bytes (BBS).  For the xor variant the second
+ * array is redrawn until comb1[j] != comb2[j] for every j (equal partners would
+ * cancel in the XOR); C == 1 has no such pair and keeps the single draw. */
+int orc_comb_arrays(int variant, uint32_t C, uint64_t comb_seed, uint8_t *out)
+{
+    if (C < 1 || C > 32 || (C & (C - 1)))
+        return -1;
+    uint64_t ctr = 0;
+    if (variant == ORC_VAR_BBS) {
+        for (int a = 0; a < 16; ++a)
+            orc_permutation(C, comb_seed, &ctr, out + (size_t)a * C);
+        return 0;
+    }
+    orc_permutation(C, comb_seed, &ctr, out);
+    for (;;) {
+        orc_permutation(C, comb_seed, &ctr, out + C);
+        if (C == 1)
+            break;
+        int clash = 0;
+        for (uint32_t j = 0; j < C; ++j)
+            if (out[j] == out[C + j])
+                clash = 1;
+        if (!clash)
+            break;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 5 strategy assembly.                                            */
+/* ------------------------------------------------------------------------- */
+
+/* Source of BBS outputs: either the lane's generator, or (for the hand-fed
+ * pin) a caller-given list of values. */
+typedef struct {
+    orc_lane *lane;
+    const uint64_t *feed;
+    uint32_t fed;
+} orc_bbs_src;
+
+static uint64_t orc_bbs_next(orc_bbs_src *s)
+{
+    if (s->feed)
+        return s->feed[s->fed++];
+    s->lane->y = orc_bbs_step(s->lane->y, s->lane->M);
+    return s->lane->y;
+}
+
+static uint32_t orc_bbs_strategy_src(orc_bbs_src *s, uint32_t w)
+{
+    static const uint32_t array_shift[4] = {0u, 1u, 3u, 7u};
+    uint32_t mask = (1u << w) - 1u;
+    uint32_t chunks = (32u + w - 1u) / w;
+    uint32_t t = 0;
+    /* fill t w bits at a time ("t <<= 4; t |= BBSk(bbsk) & 15" for w = 4) */
+    for (uint32_t c = 0; c < chunks; ++c) {
+        t <<= w;
+        t |= (uint32_t)(orc_bbs_next(s) & mask);
+    }
+    /* the two extra shifts: shift by the draw's last 2 bits, then put exactly
+     * that many low bits of the next draw in the vacated positions */
+    for (int r = 0; r < 2; ++r) {
+        uint32_t shift = (uint32_t)(orc_bbs_next(s) & 3u);
+        t <<= shift;
+        t |= (uint32_t)(orc_bbs_next(s) & array_shift[shift]);
+    }
+    return t;
+}
+
+/* Hand-fed form: assembles one strategy word from `feed` (needs
+ * ceil(32/w) + 4 values) and reports how many values it used. */
+uint32_t orc_bbs_strategy_fed(uint32_t w, const uint64_t *feed, uint32_t *used)
+{
+    orc_bbs_src s = {NULL, feed, 0};
+    uint32_t t = orc_bbs_strategy_src(&s, w);
+    if (used)
+        *used = s.fed;
+    return t;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithms 4 and 5: mixing and the CI update, synchronous over lanes.      */
+/* ------------------------------------------------------------------------- */
+
+/* One synchronous iteration over lanes [0, nl) given this iteration's own
+ * strategy words xl[]: every lane reads its two partners' previous strategies,
+ * then all slots and states are updated together.  part1/part2 give each
+ * lane's partners as lane indices within [0, nl). */
+static void orc_mix_ci_iteration(uint64_t nl, const uint32_t *xl, const uint64_t *part1,
+                                 const uint64_t *part2, uint32_t *tprev, uint32_t *x,
+                                 uint32_t *tnew)
+{
+    for (uint64_t l = 0; l < nl; ++l)
+        tnew[l] = xl[l] ^ tprev[part1[l]] ^ tprev[part2[l]];
+    for (uint64_t l = 0; l < nl; ++l) {
+        tprev[l] = tnew[l];
+        x[l] = orc_ci_step(x[l], tnew[l]);
+    }
+}
+
+/* Hand-fed mixing: given per-iteration strategy words xl[i * nl + l] and the
+ * partner lists, runs L iterations from (x, tprev), writing out[l * L + i]. */
+void orc_mix_ci_fed(uint64_t nl, uint64_t L, const uint32_t *xl, const uint64_t *part1,
+                    const uint64_t *part2, uint32_t *x, uint32_t *tprev, uint32_t *out)
+{
+    uint32_t *tnew = (uint32_t *)malloc(sizeof(uint32_t) * (nl ? nl : 1));
+    for (uint64_t i = 0; i < L; ++i) {
+        orc_mix_ci_iteration(nl, xl + i * nl, part1, part2, tprev, x, tnew);
+        for (uint64_t l = 0; l < nl; ++l)
+            out[l * L + i] = x[l];
+    }
+    free(tnew);
+}
+
+/* Runs L iterations of the generator on lanes[0..nl) (nl a multiple of C;
+ * lanes[0] must be the first lane of a group).  comb holds the combination
+ * arrays (2*C bytes for xor, 16*C for BBS).  Writes out[l * L + i] when `out`
+ * is not NULL; when `counts` is not NULL adds, per lane, the number of output
+ * pairs (out[2k], out[2k+1]) whose 24-bit fixed-point coordinates
+ * (a, b) = (o0 >> 8, o1 >> 8) fall inside the quarter circle
+ * a^2 + b^2 < 2^48 (L must then be even).  Returns 0, or -1 on bad arguments. */
+int orc_run(int variant, int xl, uint32_t C, const uint8_t *comb, orc_lane *lanes,
+            uint64_t nl, uint64_t L, uint32_t *out, uint64_t *counts)
+{
+    if (C < 1 || C > 32 || (C & (C - 1)) || nl % C != 0)
+        return -1;
+    if (counts && (L & 1))
+        return -1;
+    uint64_t *p1 = (uint64_t *)malloc(sizeof(uint64_t) * (nl ? nl : 1));
+    uint64_t *p2 = (uint64_t *)malloc(sizeof(uint64_t) * (nl ? nl : 1));
+    uint32_t *xs = (uint32_t *)malloc(sizeof(uint32_t) * (nl ? nl : 1));
+    uint32_t *tp = (uint32_t *)malloc(sizeof(uint32_t) * (nl ? nl : 1));
+    uint32_t *tn = (uint32_t *)malloc(sizeof(uint32_t) * (nl ? nl : 1));
+    uint32_t *sw = (uint32_t *)malloc(sizeof(uint32_t) * (nl ? nl : 1));
+    uint32_t *held = (uint32_t *)malloc(sizeof(uint32_t) * (nl ? nl : 1));
+
+    /* offset = lane % C; o = lane - offset + comb[offset] */
+    for (uint64_t l = 0; l < nl; ++l) {
+        uint64_t offset = l % C, base = l - offset;
+        const uint8_t *c1, *c2;
+        if (variant == ORC_VAR_BBS) {
+            c1 = comb + (size_t)lanes[l].sel1 * C;
+            c2 = comb + (size_t)(8 + lanes[l].sel2) * C;
+        } else {
+            c1 = comb;
+            c2 = comb + C;
+        }
+        p1[l] = base + c1[offset];
+        p2[l] = base + c2[offset];
+        xs[l] = lanes[l].x;
+        tp[l] = lanes[l].tprev;
+    }
+
+    for (uint64_t i = 0; i < L; ++i) {
+        for (uint64_t l = 0; l < nl; ++l) {
+            if (variant == ORC_VAR_BBS) {
+                orc_bbs_src s = {&lanes[l], NULL, 0};
+                sw[l] = orc_bbs_strategy_src(&s, orc_bbs_w(lanes[l].M));
+            } else if (xl == ORC_XL_XOR128) {
+                sw[l] = orc_xor128_step(lanes[l].w);
+            } else {
+                lanes[l].w[0] = orc_xorshift32_step(lanes[l].w[0]);
+                sw[l] = lanes[l].w[0];
+            }
+        }
+        orc_mix_ci_iteration(nl, sw, p1, p2, tp, xs, tn);
+        for (uint64_t l = 0; l < nl; ++l) {
+            if (out)
+                out[l * L + i] = xs[l];
+            if (counts) {
+                if ((i & 1) == 0) {
+                    held[l] = xs[l];
+                } else {
+                    uint64_t a = held[l] >> 8, b = xs[l] >> 8;
+                    if (a * a + b * b < (1ULL << 48))
+                        counts[l] += 1;
+                }
+            }
+        }
+    }
+
+    for (uint64_t l = 0; l < nl; ++l) {
+        lanes[l].x = xs[l];
+        lanes[l].tprev = tp[l];
+    }
+    free(p1);
+    free(p2);
+    free(xs);
+    free(tp);
+    free(tn);
+    free(sw);
+    free(held);
+    return 0;
+}
