@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 chaotic-iterations PRNG.
+
+Workload (one "step"): 2^20 streams x 4096 uint32 outputs (2^32 numbers) of
+the xor128-driven generator with Algorithm 4 mixing (C = 32, seed 2), written
+to HBM as 16 time chunks of 256 outputs per stream (1 GiB per launch).
+Alongside: the same workload fused into the quarter-circle consumer (no
+stores), the BBS-driven secure variant on 2^16 streams x 16384, the
+end-to-end figure through the public API with host buffers, and the CPU
+oracle timed on the host cores.
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): each rank generates its
+own slice of a global stream range (first_stream = rank * 2^20), no exchange;
+timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "uint32/s on 1 GB300 (written & fused) vs HBM roofline; batched vs per-launch; p99"
+S_MAIN, L_MAIN, CHUNK = 1 << 20, 1 << 12, 256
+SEED_MAIN = 2
+S_BBS, L_BBS, SEED_BBS = 1 << 16, 1 << 14, 3
+STATE_BYTES_PER_LANE_XOR128 = 24      # a, b, c, d, x, slot: read once and written once per launch
+FALLBACK_HBM_GBS = 6800.0
+GPU_SM_COUNT_NOMINAL = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="main written-mode line only")
+    ap.add_argument("--cpu-sample-streams", type=int, default=1 << 17)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples SM clock and clock-event reasons through NVML (ctypes) while a
+    timed region runs; falls back to nvidia-smi if NVML is unavailable."""
+
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+    def __init__(self, torch_device: int):
+        self.samples = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        self.nvml = None
+        self.handle = None
+        try:
+            import torch
+
+            props = torch.cuda.get_device_properties(torch_device)
+            bus = "%08X:%02X:%02X.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                        props.pci_device_id)
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle for " + bus)
+            self.nvml, self.handle = nv, h
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self._reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            self.bus = bus
+        except Exception as e:  # noqa: BLE001
+            self.error = str(e)
+
+    def _poll(self):
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.handle, 1, ctypes.byref(clk)) == 0 and \
+                    self._reasons_fn(self.handle, ctypes.byref(rs)) == 0:
+                self.samples.append((clk.value, rs.value))
+            time.sleep(0.002)
+
+    def start(self):
+        if self.nvml is None:
+            return
+        self._stop.clear()
+        self._thread = threading.Thread(target=self._poll, daemon=True)
+        self._thread.start()
+
+    def stop(self) -> dict:
+        if self.nvml is None:
+            return self._smi_once()
+        self._stop.set()
+        self._thread.join()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0}
+        mhz = [s[0] for s in self.samples]
+        bits = 0
+        for _, r in self.samples:
+            bits |= r
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": self.max_mhz,
+                "reasons": [n for b, n in self.REASONS.items() if bits & b and n != "gpu_idle"],
+                "samples": len(self.samples), "source": "nvml"}
+
+    def _smi_once(self) -> dict:
+        try:
+            q = "clocks.sm,clocks.max.sm,clocks_event_reasons.active"
+            out = subprocess.run(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=20).stdout.strip().splitlines()[0]
+            sm, mx, act = [v.strip() for v in out.split(",")]
+            bits = int(act, 16)
+            return {"sm_mhz": float(sm), "sm_max_mhz": float(mx),
+                    "reasons": [n for b, n in self.REASONS.items() if bits & b and n != "gpu_idle"],
+                    "samples": 1, "source": "nvidia-smi after the timed region"}
+        except Exception as e:  # noqa: BLE001
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured", d
+    except Exception:  # noqa: BLE001
+        return FALLBACK_HBM_GBS, "fallback", {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1112_5239_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(kernel_key)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e.get("dram_bytes_per_full_launch")
+    except Exception:  # noqa: BLE001
+        pass
+    return None
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------- CPU baseline
+def oracle_sample(n_streams: int, reps_chunks: int = L_MAIN // CHUNK) -> tuple[float, int, float]:
+    """Times the oracle as it stands (single thread) on the first n_streams
+    streams of the main workload, all 4096 outputs each in 256-output chunks.
+    Returns (uint32/s, outputs, seconds)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    g = oracle.Generator(0, 0, 32, SEED_MAIN, 0, n_streams)
+    for _ in range(reps_chunks):
+        g.generate(CHUNK)
+    dt = time.perf_counter() - t0
+    n = n_streams * CHUNK * reps_chunks
+    return n / dt, n, dt
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the oracle on the host cores, each step a bounded
+    sample of the main workload (2^15 streams x 4096)."""
+    if rank != 0:
+        return
+    n_streams = 1 << 15
+    for _ in range(args.warmup):
+        oracle_sample(n_streams)
+    rates, total_n, total_t = [], 0, 0.0
+    for _ in range(args.steps):
+        r, n, dt = oracle_sample(n_streams)
+        rates.append(r)
+        total_n += n
+        total_t += dt
+    value = total_n / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "uint32/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "xor128 CI PRNG (Alg. 4, C=32, seed 2), first 2^15 of 2^20 streams x 4096 "
+                               "outputs per step (bounded sample), written in 256-output chunks"},
+        "cpu_baseline": {"value": value, "unit": "uint32/s", "cores": 1, "kind": "oracle",
+                         "sample": "2^15 streams x 4096 outputs per step"},
+        "e2e": {"value": value, "unit": "uint32/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_1112_5239_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1112_5239_gb300 as ci
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    first = rank * S_MAIN
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------------------------------------------- written mode
+    st = ci.States(S_MAIN, variant="xor", xl="xor128", comb_size=32, seed=SEED_MAIN, first_stream=first)
+    out = torch.empty((S_MAIN, CHUNK), dtype=torch.int32, device=dev)  # 1 GiB, reused by every chunk
+    nchunks = L_MAIN // CHUNK
+
+    def step(evs=None):
+        for c in range(nchunks):
+            if evs is not None:
+                evs[c][0].record(stream)
+            st.generate(CHUNK, out=out)
+            if evs is not None:
+                evs[c][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier_sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launch_evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(nchunks)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(launch_evs[k])
+    t1.record(stream)
+    barrier_sync()
+    clk = clocks.stop()
+    ms = max_over_ranks(t0.elapsed_time(t1))
+    launch_ms = [a.elapsed_time(b) for row in launch_evs for a, b in row]
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    total = world * S_MAIN * L_MAIN * args.steps
+    value = total / (ms / 1e3)
+
+    peak, peak_kind, peaks = measured_peaks()
+    alg_bytes = S_MAIN * CHUNK * 4 + S_MAIN * 2 * STATE_BYTES_PER_LANE_XOR128
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy read+write)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "traffic": ncu_traffic("k_generate<SrcXor128,SINK_V4>"),
+                "kernel": "k_generate<SrcXor128,SINK_V4>", "alg_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": avg_launch_s * 1e3}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "uint32/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "xor128-driven CI PRNG (Alg. 4 mixing, C=32, seed 2): 2^20 streams x 4096 "
+                               "uint32 per GPU, written to HBM in 16 time chunks of 256 per stream (1 GiB "
+                               "per launch)",
+                   "streams_per_gpu": S_MAIN, "n_per_stream": L_MAIN, "chunk": CHUNK,
+                   "l2": "each launch writes 1 GiB (> 129 MB L2): no flush between steps",
+                   "parallelism": "dp%d (disjoint stream slices, no exchange)" % world},
+        "roofline": roofline, "gpu_launches": args.steps * nchunks, "clocks": clk,
+    }
+    del out
+    st.free()
+
+    if not args.no_extras:
+        result["fused"] = bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
+        result["bbs"] = bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
+        result["e2e"] = bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
+        if rank == 0 and world == 1:
+            r, n, dt = oracle_sample(args.cpu_sample_streams)
+            result["cpu_baseline"] = {"value": r, "unit": "uint32/s", "cores": 1, "kind": "oracle",
+                                      "sample": "first %d of 2^20 streams x 4096 outputs (%.1f s)"
+                                                % (args.cpu_sample_streams, dt)}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world):
+    st = ci.States(S_MAIN, variant="xor", xl="xor128", comb_size=32, seed=SEED_MAIN, first_stream=first)
+    counts = torch.zeros(S_MAIN, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        st.generate_fused_qc(L_MAIN, counts=counts)
+    barrier_sync()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict the 24 MB state from L2 between steps
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.generate_fused_qc(L_MAIN, counts=counts)
+        b.record(stream)
+        evs.append((a, b))
+    barrier_sync()
+    kms = [a.elapsed_time(b) for a, b in evs]
+    ms = max_over_ranks(statistics.mean(kms))
+    value = world * S_MAIN * L_MAIN / (ms / 1e3)
+    # integer lane-ops per output (xor128 7, mixing 2 shuffles + 2 xor, CI 1,
+    # quarter-circle 8 per pair); peak: 152 SMs x 128 lanes x max SM clock.
+    ops = 7 + 4 + 1 + 4
+    peak = GPU_SM_COUNT_NOMINAL * 128 * 2.07e9
+    st.free()
+    return {"value": value, "unit": "uint32/s", "ms_per_step": ms,
+            "workload": "same 2^20 x 4096 streams, outputs consumed in-kernel by the quarter-circle counter",
+            "roofline": {"bound": "alu", "achieved": ops * value / world / 1e9, "peak": peak / 1e9,
+                         "unit": "Gop/s", "frac": ops * value / world / peak, "ops_per_output": ops,
+                         "peak_source": "152 SMs x 128 int lanes/clk x 2.07 GHz"},
+            "l2": "256 MiB flush between steps"}
+
+
+def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):
+    st = ci.States(S_BBS, variant="bbs", comb_size=32, seed=SEED_BBS, first_stream=rank * S_BBS)
+    out = torch.empty((S_BBS, L_BBS), dtype=torch.int32, device=dev)  # 4 GiB
+    steps = max(1, min(args.steps, 5))
+    for _ in range(min(args.warmup, 2)):
+        st.generate(L_BBS, out=out)
+    barrier_sync()
+    evs = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.generate(L_BBS, out=out)
+        b.record(stream)
+        evs.append((a, b))
+    barrier_sync()
+    ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
+    value = world * S_BBS * L_BBS / (ms / 1e3)
+    del out
+    st.free()
+    return {"value": value, "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
+            "workload": "BBS-driven CI PRNG (Alg. 5, 62-bit Blum moduli, 11 Montgomery squarings per output,"
+                        " C=32, seed 3): 2^16 streams x 16384, written (4 GiB per launch)",
+            "modsq_per_s": 11 * value}
+
+
+def bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world):
+    """End to end through the public API: seed a fresh state from the host
+    parameters, generate all 4096 outputs of every stream chunk by chunk, and
+    copy every chunk to pinned host memory (two 1 GiB device and host buffers
+    alternate; generation of chunk c+1 overlaps the copy of chunk c)."""
+    copy_stream = torch.cuda.Stream(device=dev)
+    dbuf = [torch.empty((S_MAIN, CHUNK), dtype=torch.int32, device=dev) for _ in range(2)]
+    hbuf = [torch.empty((S_MAIN, CHUNK), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    nchunks = L_MAIN // CHUNK
+
+    def one():
+        st = ci.States(S_MAIN, variant="xor", xl="xor128", comb_size=32, seed=SEED_MAIN, first_stream=first)
+        done = [None, None]
+        for c in range(nchunks):
+            b = c & 1
+            if done[b] is not None:
+                stream.wait_event(done[b])
+            st.generate(CHUNK, out=dbuf[b])
+            gen = torch.cuda.Event()
+            gen.record(stream)
+            copy_stream.wait_event(gen)
+            with torch.cuda.stream(copy_stream):
+                hbuf[b].copy_(dbuf[b], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+            done[b] = ev
+        copy_stream.synchronize()
+        torch.cuda.current_stream().synchronize()
+        st.free()
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        one()
+    barrier_sync()
+    steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    barrier_sync()
+    sec = max_over_ranks(time.perf_counter() - t0)
+    value = world * S_MAIN * L_MAIN * steps / sec
+    return {"value": value, "unit": "uint32/s", "ms_per_step": 1e3 * sec / steps, "steps": steps,
+            "h2d_bytes_per_step": 512 + 64, "d2h_bytes_per_step": S_MAIN * L_MAIN * 4,
+            "path": "ci_init_states (host params -> device) + 16 x ci_generate + D2H to pinned host"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * ci_prng.h -- C ABI of the GB300 chaotic-iterations PRNG library
+ * (libci_prng.so).
+ *
+ * The generator is the one of Bahi, Couturier, Guyeux & Heam, arXiv 1112.5239:
+ *   - Eq. (Oplus): x^n = x^{n-1} XOR S^n -- bit k of the 32-bit state x flips
+ *     iff bit k of the strategy word S^n is 1 (Sec. 4.2);
+ *   - Algorithm 4 (Sec. 6.2): each stream ("thread") draws one word from its
+ *     own xor-like generator and XORs in the previous strategies of two
+ *     partner streams of its group, chosen through two combination arrays of
+ *     size combination_size; the result is the strategy S^n;
+ *   - Algorithm 5 (Sec. 9.1): the secure variant, whose own word is assembled
+ *     from the low bits of a Blum Blum Shub generator x_{k+1} = x_k^2 mod M,
+ *     with sixteen combination arrays of which each stream uses two.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns a ci_status; nothing throws across the ABI.
+ *     On failure ci_last_error() returns a message (per calling thread).
+ *   - Device pointers ("_dev") are CUDA global-memory addresses on the current
+ *     device; host pointers are ordinary process memory.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL: the legacy default
+ *     stream).  Generation calls are asynchronous on that stream: they return
+ *     after enqueueing, and the caller synchronises before reading outputs.
+ *   - Output layout is stream-major: out[s * n_per_stream + i] is stream s's
+ *     (i + 1)-th output of the call, i.e. the state x after its (i + 1)-th
+ *     update, for s < n_streams.
+ *   - Results depend only on (parameters, stream index, position in the
+ *     stream): not on launch shape, batching, or how a stream's length is split
+ *     over calls (a call continues exactly where the previous one stopped).
+ */
+#ifndef CI_PRNG_H
+#define CI_PRNG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef int32_t ci_status;
+enum {
+    CI_OK = 0,          /* success                                          */
+    CI_PENDING = 1,     /* ci_poll: request not finished yet                */
+    CI_E_INVAL = -1,    /* bad argument (null pointer, size, capacity)      */
+    CI_E_NOMEM = -2,    /* device or arena memory exhausted                 */
+    CI_E_CUDA = -3,     /* a CUDA runtime call failed                       */
+    CI_E_BUSY = -4,     /* server queue full / admission refused            */
+    CI_E_TIMEOUT = -5,  /* a bounded wait gave up                           */
+    CI_E_STATE = -6     /* handle of the wrong variant, or freed            */
+};
+
+/* --------------------------------------------------------------- params */
+enum { CI_VAR_XOR = 0, CI_VAR_BBS = 1 };           /* Alg. 4 / Alg. 5       */
+enum { CI_XL_XOR128 = 0, CI_XL_XORSHIFT32 = 1 };   /* xor-like of Alg. 4    */
+
+typedef struct {
+    int32_t variant;      /* CI_VAR_XOR or CI_VAR_BBS                           */
+    int32_t xl;           /* xor variant: CI_XL_XOR128 (the 32-bit xor128 the
+                             paper uses for Alg. 4, Sec. 6.2) or
+                             CI_XL_XORSHIFT32 (Alg. 2); ignored for BBS       */
+    uint32_t comb_size;   /* combination_size C of Alg. 4/5: 1, 2, 4, 8, 16 or
+                             32; a group of C streams mixes within itself     */
+    uint32_t flags;       /* reserved, must be 0                               */
+    uint64_t seed;        /* per-stream state seed (counter-based splitmix64) */
+    uint64_t comb_seed;   /* seed of the combination arrays                    */
+    uint64_t first_stream;/* global index of this handle's stream 0, a multiple
+                             of 32 (0 for a standalone handle): stream s is
+                             seeded as global stream first_stream + s, so
+                             handles holding consecutive slices of one stream
+                             range (e.g. one per GPU) reproduce it exactly   */
+    const uint8_t *comb;  /* NULL: derive the arrays from comb_seed.  Else
+                             host array of 2*C bytes (xor: comb1 then comb2) or
+                             16*C bytes (BBS: array a at comb[a*C]); every
+                             entry must be < C.  Copied during the call.      */
+} ci_params;
+
+/* Opaque per-parameter-set stream state (the paper's InternalVar...Array,
+ * x and the shared-memory slots), resident in device memory between calls. */
+typedef struct ci_states_s *ci_states;
+
+/* What a handle holds (filled by ci_states_query). */
+typedef struct {
+    int32_t variant, xl;
+    uint32_t comb_size;
+    uint32_t reserved;
+    uint64_t n_streams;     /* streams requested                               */
+    uint64_t n_lanes;       /* lanes computed: n_streams rounded up to 32      */
+    uint64_t state_bytes;   /* size of the device state (export/import size)   */
+    void *state_dev;        /* device address of the state                     */
+    uint8_t comb[16 * 32];  /* the combination arrays in use (2*C or 16*C)     */
+} ci_states_desc;
+
+/* Bytes of device memory a state of n_streams streams needs (layout in
+ * ci_export_state).  For callers that place states in their own memory. */
+ci_status ci_state_bytes(const ci_params *params, uint64_t n_streams, uint64_t *bytes);
+
+/* Creates a state for n_streams independent streams
+ * (1 <= n_streams, first_stream + n_streams <= 2^32)
+ * and seeds it on cuda_stream (Sec. 6.1: the paper seeds every thread's
+ * xor-like parameters on the host with ISAAC; here lane s takes draws
+ * s*2^32 + k of a counter-based splitmix64 of params->seed, k = 0, 1, 2:
+ * xor128 words (lo, hi of draw 0, lo, hi of draw 1; all-zero -> first word 1),
+ * XORshift word (lo of draw 0, 0 -> 1), x (lo of draw 2) and the shared-memory
+ * slot (hi of draw 2).  BBS lanes draw Blum primes p, q in [2^30, 2^31),
+ * p = q = 3 mod 4, p != q, by rejection, a seed coprime to M = p q in
+ * [2, M), then x and the slot).  Streams are padded to a multiple of 32 lanes;
+ * padding lanes are computed but never returned.
+ * The library allocates the device memory (cudaMalloc); ci_free_states frees it.
+ * Errors: CI_E_INVAL (bad params, n_streams out of range), CI_E_NOMEM,
+ * CI_E_CUDA. */
+ci_status ci_init_states(const ci_params *params, uint64_t n_streams, void *cuda_stream,
+                         ci_states *out);
+
+/* As ci_init_states, but the state lives in caller-owned device memory
+ * state_dev (state_bytes >= ci_state_bytes(), 256-byte aligned), which must
+ * outlive the handle; ci_free_states then frees only the handle. */
+ci_status ci_init_states_at(const ci_params *params, uint64_t n_streams, void *state_dev,
+                            uint64_t state_bytes, void *cuda_stream, ci_states *out);
+
+/* Frees the handle (and its device memory if the library allocated it).
+ * The caller must ensure no enqueued call still uses it.  NULL is a no-op. */
+ci_status ci_free_states(ci_states states);
+
+ci_status ci_states_query(ci_states states, ci_states_desc *out);
+
+/* ---------------------------------------------------------- generation */
+
+/* Algorithm 4 (Sec. 6.2) with Eq. (Oplus): advances every stream of a
+ * CI_VAR_XOR state by n_per_stream iterations and writes the outputs to
+ * out_dev[s * n_per_stream + i] (uint32, stream-major, caller-owned device
+ * memory of out_capacity_u32 elements).  Per iteration and stream:
+ * t = xorlike() ^ slot[o1] ^ slot[o2] (partners' previous strategies,
+ * o = group base + comb[s % C]); slot[s] = t; x ^= t; output x.
+ * Errors: CI_E_STATE (BBS handle), CI_E_INVAL (null output, or
+ * out_capacity_u32 < n_streams * n_per_stream), CI_E_CUDA.
+ * n_per_stream == 0 is a no-op. */
+ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev,
+                      uint64_t out_capacity_u32, void *cuda_stream);
+
+/* Algorithm 5 (Sec. 9.1): the same for a CI_VAR_BBS state.  Each strategy
+ * word takes ceil(32/w) BBS outputs' low w bits (w = floor(log2 log2 M) = 5
+ * for these 62-bit moduli), then twice: shift = BBS & 3; t <<= shift;
+ * t |= BBS & {0,1,3,7}[shift] -- 11 modular squarings per output, done with
+ * 64x64->128-bit multiplies and Montgomery reduction.  The stream's two
+ * combination arrays are comb[sel1] and comb[8 + sel2] with sel1 = v & 7,
+ * sel2 = (v >> 3) & 7 of its BBS seed v.  Errors as ci_generate
+ * (CI_E_STATE for an xor handle). */
+ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out_dev,
+                          uint64_t out_capacity_u32, void *cuda_stream);
+
+/* Generation fused with its consumer (Sec. 7: numbers consumed right after
+ * generation, without storage): the call's outputs of each stream are taken
+ * in pairs (o0, o1) = (out[2k], out[2k+1]) and mapped to the point
+ * (a, b) = (o0 >> 8, o1 >> 8) / 2^24 in [0,1)^2; counts_dev[s] (uint64,
+ * caller-owned, n_streams elements) is INCREMENTED by the number of points
+ * with a^2 + b^2 < 1 (exact integer test (o0>>8)^2 + (o1>>8)^2 < 2^48).
+ * Works for both variants; the state advances exactly as in the written
+ * form.  n_per_stream must be even (CI_E_INVAL otherwise). */
+ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t *counts_dev,
+                               void *cuda_stream);
+
+/* -------------------------------------------------- checkpoint / resume */
+
+/* Copies the whole device state (bytes == state_bytes) to host_buf /
+ * from host_buf, ordered on cuda_stream (the call waits for the copy).
+ * Layout for P = n_lanes lanes:
+ *   [0, 512)            partner table u8[16][32]: lane j of a warp mixes with
+ *                       lanes table[a][j] (xor: a = 0, 1; BBS: a = sel1, 8+sel2)
+ *   then 9 uint32 fields of P lanes each (field f at 512 + 4*f*P):
+ *     0..3 xor-like words (xor128 a, b, c, d; XORshift z in field 0),
+ *     4 x, 5 slot (last strategy), 6 sel1 | sel2 << 8, 7 p, 8 q
+ *   then (BBS only) 4 uint64 fields of P lanes: 0 y (canonical residue, BBS
+ *     state), 1 M, 2 -M^-1 mod 2^64, 3 2^128 mod M.
+ * Importing replaces the state of a handle with the same parameters and
+ * n_streams; an imported BBS state must hold y < 2^64 and the constants of M.
+ * Errors: CI_E_INVAL (size mismatch), CI_E_CUDA. */
+ci_status ci_export_state(ci_states states, void *host_buf, uint64_t bytes, void *cuda_stream);
+ci_status ci_import_state(ci_states states, const void *host_buf, uint64_t bytes,
+                          void *cuda_stream);
+
+/* --------------------------------------------------------------- misc */
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *ci_last_error(void);
+
+/* Library version, as major * 10000 + minor * 100 + patch. */
+uint32_t ci_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CI_PRNG_H */

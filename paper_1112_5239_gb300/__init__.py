@@ -1,0 +1,139 @@
+"""GB300-native chaotic-iterations PRNG (Bahi, Couturier, Guyeux & Heam,
+arXiv 1112.5239): Python face of the C ABI in include/ci_prng.h.
+
+PyTorch supplies device memory and streams only; every step of generation
+runs in the library's CUDA kernels (libci_prng.so).  Outputs are returned as
+torch.int32 tensors holding the uint32 bit patterns (view them as uint32 with
+``.cpu().numpy().view(numpy.uint32)``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CIError, ci_params, ci_states_desc
+
+VARIANTS = {"xor": _lib.CI_VAR_XOR, "bbs": _lib.CI_VAR_BBS}
+XORLIKES = {"xor128": _lib.CI_XL_XOR128, "xorshift32": _lib.CI_XL_XORSHIFT32}
+
+__all__ = ["States", "CIError", "make_params", "stream_ptr", "VARIANTS", "XORLIKES"]
+
+
+def stream_ptr(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def make_params(variant="xor", xl="xor128", comb_size=32, seed=0, comb_seed=0, comb=None, first_stream=0):
+    """A ci_params struct (and the buffer keeping explicit arrays alive)."""
+    p = ci_params()
+    p.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    p.xl = XORLIKES[xl] if isinstance(xl, str) else int(xl)
+    p.comb_size = int(comb_size)
+    p.flags = 0
+    p.seed = int(seed) & (2**64 - 1)
+    p.comb_seed = int(comb_seed) & (2**64 - 1)
+    p.first_stream = int(first_stream)
+    keep = None
+    if comb is not None:
+        keep = np.ascontiguousarray(np.asarray(comb, dtype=np.uint8))
+        p.comb = keep.ctypes.data
+    else:
+        p.comb = None
+    return p, keep
+
+
+class States:
+    """Device-resident stream state for one parameter set (a ``ci_states``).
+
+    ``memory="library"`` lets the library cudaMalloc the state;
+    ``memory="torch"`` places it in a torch uint8 tensor (``ci_init_states_at``).
+    """
+
+    def __init__(self, n_streams, variant="xor", xl="xor128", comb_size=32, seed=0, comb_seed=0,
+                 comb=None, stream=None, memory="library", first_stream=0):
+        self.handle = ctypes.c_void_p()
+        self.n_streams = int(n_streams)
+        p, _keep = make_params(variant, xl, comb_size, seed, comb_seed, comb, first_stream)
+        self.variant = p.variant
+        self._buf = None
+        if memory == "torch":
+            nbytes = ctypes.c_uint64()
+            _lib.call("ci_state_bytes", ctypes.byref(p), self.n_streams, ctypes.byref(nbytes))
+            self._buf = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device="cuda")
+            base = self._buf.data_ptr()
+            aligned = (base + 255) & ~255
+            _lib.call("ci_init_states_at", ctypes.byref(p), self.n_streams, aligned, nbytes.value,
+                      stream_ptr(stream), ctypes.byref(self.handle))
+        else:
+            _lib.call("ci_init_states", ctypes.byref(p), self.n_streams, stream_ptr(stream),
+                      ctypes.byref(self.handle))
+
+    # ------------------------------------------------------------ queries
+    def query(self) -> ci_states_desc:
+        d = ci_states_desc()
+        _lib.call("ci_states_query", self.handle, ctypes.byref(d))
+        return d
+
+    @property
+    def state_bytes(self) -> int:
+        return int(self.query().state_bytes)
+
+    # --------------------------------------------------------- generation
+    def generate(self, n_per_stream, out=None, stream=None) -> torch.Tensor:
+        """Next n_per_stream outputs of every stream: int32 [n_streams, n]."""
+        n = int(n_per_stream)
+        if out is None:
+            out = torch.empty((self.n_streams, n), dtype=torch.int32, device="cuda")
+        name = "ci_generate_bbs" if self.variant == _lib.CI_VAR_BBS else "ci_generate"
+        _lib.call(name, self.handle, n, out.data_ptr(), out.numel(), stream_ptr(stream))
+        return out
+
+    def generate_fused_qc(self, n_per_stream, counts=None, stream=None) -> torch.Tensor:
+        """Adds each stream's quarter-circle hits over the next n outputs to
+        ``counts`` (int64 [n_streams], zero-initialised if not given)."""
+        if counts is None:
+            counts = torch.zeros(self.n_streams, dtype=torch.int64, device="cuda")
+        _lib.call("ci_generate_fused_qc", self.handle, int(n_per_stream), counts.data_ptr(),
+                  stream_ptr(stream))
+        return counts
+
+    # ------------------------------------------------- checkpoint/resume
+    def export_state(self, stream=None) -> np.ndarray:
+        buf = np.zeros(self.state_bytes, dtype=np.uint8)
+        _lib.call("ci_export_state", self.handle, buf.ctypes.data, buf.size, stream_ptr(stream))
+        return buf
+
+    def import_state(self, buf, stream=None) -> None:
+        b = np.ascontiguousarray(np.asarray(buf, dtype=np.uint8))
+        _lib.call("ci_import_state", self.handle, b.ctypes.data, b.size, stream_ptr(stream))
+
+    # ------------------------------------------------------------- freeing
+    def free(self) -> None:
+        if self.handle:
+            torch.cuda.current_stream().synchronize()
+            _lib.call("ci_free_states", self.handle)
+            self.handle = ctypes.c_void_p()
+            self._buf = None
+
+    def __del__(self):
+        try:
+            if self.handle and torch.cuda.is_available():
+                self.free()
+        except Exception:
+            pass
+
+
+def unpack_state(buf: np.ndarray, n_lanes: int, variant: int) -> dict:
+    """Splits an exported state into its documented fields."""
+    P = int(n_lanes)
+    u32 = buf[512:512 + 36 * P].view(np.uint32).reshape(9, P)
+    out = {"table": buf[:512].reshape(16, 32), "a": u32[0], "b": u32[1], "c": u32[2], "d": u32[3],
+           "x": u32[4], "slot": u32[5], "sel": u32[6], "p": u32[7], "q": u32[8]}
+    if variant == _lib.CI_VAR_BBS:
+        u64 = buf[512 + 36 * P:512 + 36 * P + 32 * P].view(np.uint64).reshape(4, P)
+        out.update({"y": u64[0], "M": u64[1], "Mp": u64[2], "r2": u64[3]})
+    return out

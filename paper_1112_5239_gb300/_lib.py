@@ -1,0 +1,103 @@
+"""ctypes declarations of the C ABI in include/ci_prng.h.
+
+Loads the in-tree libci_prng.so; raises loudly when it is missing (there is no
+CPU fallback).  Names match the C entry points one to one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libci_prng.so")
+
+CI_OK, CI_PENDING = 0, 1
+CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE = -1, -2, -3, -4, -5, -6
+CI_VAR_XOR, CI_VAR_BBS = 0, 1
+CI_XL_XOR128, CI_XL_XORSHIFT32 = 0, 1
+
+STATUS_NAMES = {0: "CI_OK", 1: "CI_PENDING", -1: "CI_E_INVAL", -2: "CI_E_NOMEM", -3: "CI_E_CUDA",
+                -4: "CI_E_BUSY", -5: "CI_E_TIMEOUT", -6: "CI_E_STATE"}
+
+
+class ci_params(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int32),
+        ("xl", ctypes.c_int32),
+        ("comb_size", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64),
+        ("comb_seed", ctypes.c_uint64),
+        ("first_stream", ctypes.c_uint64),
+        ("comb", ctypes.c_void_p),
+    ]
+
+
+class ci_states_desc(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int32),
+        ("xl", ctypes.c_int32),
+        ("comb_size", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("n_streams", ctypes.c_uint64),
+        ("n_lanes", ctypes.c_uint64),
+        ("state_bytes", ctypes.c_uint64),
+        ("state_dev", ctypes.c_void_p),
+        ("comb", ctypes.c_uint8 * 512),
+    ]
+
+
+class CIError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__("%s failed with %s: %s" % (where, STATUS_NAMES.get(status, status), message))
+
+
+_lib = None
+
+_VP, _U32, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+_SIGNATURES = {
+    "ci_state_bytes": [_VP, _U64, _VP],
+    "ci_init_states": [_VP, _U64, _VP, _VP],
+    "ci_init_states_at": [_VP, _U64, _VP, _U64, _VP, _VP],
+    "ci_free_states": [_VP],
+    "ci_states_query": [_VP, _VP],
+    "ci_generate": [_VP, _U64, _VP, _U64, _VP],
+    "ci_generate_bbs": [_VP, _U64, _VP, _U64, _VP],
+    "ci_generate_fused_qc": [_VP, _U64, _VP, _VP],
+    "ci_export_state": [_VP, _VP, _U64, _VP],
+    "ci_import_state": [_VP, _VP, _U64, _VP],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libci_prng.so is not built (run `python -c 'import __graft_entry__ as g; "
+                              "g.build()'` or `python paper_1112_5239_gb300/build.py`); there is no CPU "
+                              "fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _I32
+        L.ci_last_error.argtypes = []
+        L.ci_last_error.restype = ctypes.c_char_p
+        L.ci_version.argtypes = []
+        L.ci_version.restype = _U32
+        _lib = L
+    return _lib
+
+
+def check(status: int, where: str) -> int:
+    if status < 0:
+        msg = lib().ci_last_error()
+        raise CIError(status, where, msg.decode() if msg else "")
+    return status
+
+
+def call(name: str, *args) -> int:
+    """Calls C entry point `name` and raises CIError on a negative status."""
+    return check(getattr(lib(), name)(*args), name)

@@ -1,0 +1,274 @@
+// ci_api.cu -- the C ABI (include/ci_prng.h): argument checks, state handles,
+// combination arrays, checkpoint export/import.  Every entry point returns a
+// ci_status and records a message for ci_last_error() on failure.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ci_internal.h"
+
+namespace ci {
+
+static thread_local std::string g_err;
+
+ci_status fail(ci_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+ci_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return CI_E_CUDA;
+}
+
+bool valid_handle(const ci_states s) { return s != nullptr && s->magic == kMagic; }
+
+uint64_t state_bytes_for(int variant, uint64_t P) {
+    return (uint64_t)kTableBytes + 4ull * kU32Fields * P +
+           (variant == CI_VAR_BBS ? 8ull * kU64Fields * P : 0ull);
+}
+
+// splitmix64 (Steele, Lea & Flood 2014) on the host, for the combination
+// arrays: draw i of seed s is mix(s + (i + 1) * golden gamma).
+static uint64_t host_draw(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Fisher-Yates shuffle of 0..C-1, consuming draws ctr, ctr+1, ...
+static void shuffle(uint32_t C, uint64_t seed, uint64_t &ctr, uint8_t *a) {
+    for (uint32_t i = 0; i < C; ++i) a[i] = (uint8_t)i;
+    for (uint32_t i = C; i-- > 1;) {
+        const uint32_t j = (uint32_t)(host_draw(seed, ctr++) % (uint64_t)(i + 1));
+        const uint8_t t = a[i];
+        a[i] = a[j];
+        a[j] = t;
+    }
+}
+
+// Combination arrays (Alg. 4: two, Alg. 5: sixteen permutations of [0, C)).
+// For the xor variant the second array is redrawn until it differs from the
+// first at every position (an equal pair of partners cancels in the XOR).
+static void derive_comb(int variant, uint32_t C, uint64_t seed, uint8_t *comb) {
+    uint64_t ctr = 0;
+    if (variant == CI_VAR_BBS) {
+        for (int a = 0; a < 16; ++a) shuffle(C, seed, ctr, comb + a * C);
+        return;
+    }
+    shuffle(C, seed, ctr, comb);
+    for (;;) {
+        shuffle(C, seed, ctr, comb + C);
+        if (C == 1) return;
+        bool distinct = true;
+        for (uint32_t j = 0; j < C; ++j) distinct = distinct && comb[j] != comb[C + j];
+        if (distinct) return;
+    }
+}
+
+// Partner table: lane j of a warp, array a -> lane (j - j % C) + comb[a][j % C].
+static void build_table(int variant, uint32_t C, const uint8_t *comb, uint8_t *table) {
+    std::memset(table, 0, kTableBytes);
+    const int arrays = variant == CI_VAR_BBS ? 16 : 2;
+    for (int a = 0; a < arrays; ++a)
+        for (uint32_t j = 0; j < 32; ++j) table[a * 32 + j] = (uint8_t)((j & ~(C - 1)) + comb[a * C + (j & (C - 1))]);
+}
+
+static ci_status check_params(const ci_params *p, uint64_t S) {
+    if (!p) return fail(CI_E_INVAL, "params is NULL");
+    if (p->variant != CI_VAR_XOR && p->variant != CI_VAR_BBS) return fail(CI_E_INVAL, "unknown variant");
+    if (p->variant == CI_VAR_XOR && p->xl != CI_XL_XOR128 && p->xl != CI_XL_XORSHIFT32)
+        return fail(CI_E_INVAL, "unknown xor-like generator");
+    const uint32_t C = p->comb_size;
+    if (C < 1 || C > 32 || (C & (C - 1)) != 0) return fail(CI_E_INVAL, "comb_size must be 1, 2, 4, 8, 16 or 32");
+    if (p->flags != 0) return fail(CI_E_INVAL, "flags must be 0");
+    if (S < 1 || S > (1ull << 32)) return fail(CI_E_INVAL, "n_streams must be in [1, 2^32]");
+    if ((p->first_stream & 31ull) != 0 || p->first_stream > (1ull << 32) - S)
+        return fail(CI_E_INVAL, "first_stream must be a multiple of 32 with first_stream + n_streams <= 2^32");
+    if (p->comb) {
+        const uint32_t n = (p->variant == CI_VAR_BBS ? 16u : 2u) * C;
+        for (uint32_t i = 0; i < n; ++i)
+            if (p->comb[i] >= C) return fail(CI_E_INVAL, "combination array entry >= comb_size");
+    }
+    return CI_OK;
+}
+
+static uint64_t lanes_for(uint64_t S) { return (S + 31ull) & ~31ull; }
+
+static ci_status make_handle(const ci_params *p, uint64_t S, void *dev, uint64_t bytes, bool owns,
+                             cudaStream_t stream, ci_states *out) {
+    ci_states_s *h = new (std::nothrow) ci_states_s();
+    if (!h) return fail(CI_E_NOMEM, "host allocation failed");
+    h->magic = kMagic;
+    h->variant = p->variant;
+    h->xl = p->variant == CI_VAR_XOR ? p->xl : 0;
+    h->C = p->comb_size;
+    h->S = S;
+    h->P = lanes_for(S);
+    h->bytes = bytes;
+    h->dev = dev;
+    h->owns = owns;
+    std::memset(h->comb, 0, sizeof h->comb);
+    const uint32_t ncomb = (p->variant == CI_VAR_BBS ? 16u : 2u) * h->C;
+    if (p->comb)
+        std::memcpy(h->comb, p->comb, ncomb);
+    else
+        derive_comb(p->variant, h->C, p->comb_seed, h->comb);
+    build_table(p->variant, h->C, h->comb, h->table);
+    cudaError_t e = cudaMemcpyAsync(dev, h->table, kTableBytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = launch_init(*h, p->seed, p->first_stream, stream);
+    if (e != cudaSuccess) {
+        h->magic = 0;
+        delete h;
+        return cuda_fail(e, "state initialisation");
+    }
+    *out = h;
+    return CI_OK;
+}
+
+}  // namespace ci
+
+ci::DevState ci_states_s::view() const {
+    ci::DevState s;
+    uint8_t *base = static_cast<uint8_t *>(dev);
+    s.table = base;
+    s.u32 = reinterpret_cast<uint32_t *>(base + ci::kTableBytes);
+    s.u64 = variant == CI_VAR_BBS ? reinterpret_cast<uint64_t *>(base + ci::kTableBytes + 4ull * ci::kU32Fields * P)
+                                  : nullptr;
+    s.P = P;
+    s.S = S;
+    return s;
+}
+
+using namespace ci;
+
+extern "C" {
+
+ci_status ci_state_bytes(const ci_params *params, uint64_t n_streams, uint64_t *bytes) {
+    ci_status st = check_params(params, n_streams);
+    if (st != CI_OK) return st;
+    if (!bytes) return fail(CI_E_INVAL, "bytes is NULL");
+    *bytes = state_bytes_for(params->variant, lanes_for(n_streams));
+    return CI_OK;
+}
+
+ci_status ci_init_states(const ci_params *params, uint64_t n_streams, void *cuda_stream, ci_states *out) {
+    if (!out) return fail(CI_E_INVAL, "out is NULL");
+    *out = nullptr;
+    ci_status st = check_params(params, n_streams);
+    if (st != CI_OK) return st;
+    const uint64_t bytes = state_bytes_for(params->variant, lanes_for(n_streams));
+    void *dev = nullptr;
+    cudaError_t e = cudaMalloc(&dev, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? CI_E_NOMEM : CI_E_CUDA,
+                    std::string("cudaMalloc of the state: ") + cudaGetErrorString(e));
+    }
+    st = make_handle(params, n_streams, dev, bytes, true, static_cast<cudaStream_t>(cuda_stream), out);
+    if (st != CI_OK) cudaFree(dev);
+    return st;
+}
+
+ci_status ci_init_states_at(const ci_params *params, uint64_t n_streams, void *state_dev, uint64_t state_bytes,
+                            void *cuda_stream, ci_states *out) {
+    if (!out) return fail(CI_E_INVAL, "out is NULL");
+    *out = nullptr;
+    ci_status st = check_params(params, n_streams);
+    if (st != CI_OK) return st;
+    const uint64_t need = state_bytes_for(params->variant, lanes_for(n_streams));
+    if (!state_dev || (reinterpret_cast<uintptr_t>(state_dev) & 255u) != 0)
+        return fail(CI_E_INVAL, "state_dev must be a non-NULL 256-byte aligned device address");
+    if (state_bytes < need) return fail(CI_E_INVAL, "state_bytes smaller than ci_state_bytes()");
+    return make_handle(params, n_streams, state_dev, need, false, static_cast<cudaStream_t>(cuda_stream), out);
+}
+
+ci_status ci_free_states(ci_states s) {
+    if (!s) return CI_OK;
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    s->magic = 0;
+    cudaError_t e = cudaSuccess;
+    if (s->owns) e = cudaFree(s->dev);
+    delete s;
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "cudaFree of the state");
+}
+
+ci_status ci_states_query(ci_states s, ci_states_desc *out) {
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    if (!out) return fail(CI_E_INVAL, "out is NULL");
+    std::memset(out, 0, sizeof *out);
+    out->variant = s->variant;
+    out->xl = s->xl;
+    out->comb_size = s->C;
+    out->n_streams = s->S;
+    out->n_lanes = s->P;
+    out->state_bytes = s->bytes;
+    out->state_dev = s->dev;
+    std::memcpy(out->comb, s->comb, sizeof out->comb);
+    return CI_OK;
+}
+
+static ci_status check_out(ci_states s, uint64_t n, const void *out, uint64_t cap) {
+    if (!out) return fail(CI_E_INVAL, "out_dev is NULL");
+    if (n > 0 && s->S > UINT64_MAX / n) return fail(CI_E_INVAL, "n_streams * n_per_stream overflows");
+    if (cap < s->S * n) return fail(CI_E_INVAL, "out_capacity_u32 < n_streams * n_per_stream");
+    return CI_OK;
+}
+
+ci_status ci_generate(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void *stream) {
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    if (s->variant != CI_VAR_XOR) return fail(CI_E_STATE, "ci_generate needs an xor-variant state (use ci_generate_bbs)");
+    if (n == 0) return CI_OK;
+    ci_status st = check_out(s, n, out, cap);
+    if (st != CI_OK) return st;
+    cudaError_t e = launch_generate(*s, n, out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "generation kernel launch");
+}
+
+ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void *stream) {
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    if (s->variant != CI_VAR_BBS) return fail(CI_E_STATE, "ci_generate_bbs needs a BBS-variant state (use ci_generate)");
+    if (n == 0) return CI_OK;
+    ci_status st = check_out(s, n, out, cap);
+    if (st != CI_OK) return st;
+    cudaError_t e = launch_generate(*s, n, out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "BBS generation kernel launch");
+}
+
+ci_status ci_generate_fused_qc(ci_states s, uint64_t n, uint64_t *counts, void *stream) {
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    if (n & 1ull) return fail(CI_E_INVAL, "n_per_stream must be even (outputs are consumed in pairs)");
+    if (n == 0) return CI_OK;
+    if (!counts) return fail(CI_E_INVAL, "counts_dev is NULL");
+    cudaError_t e = launch_fused_qc(*s, n, counts, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "fused generation kernel launch");
+}
+
+ci_status ci_export_state(ci_states s, void *host_buf, uint64_t bytes, void *stream) {
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    if (!host_buf || bytes != s->bytes) return fail(CI_E_INVAL, "host_buf NULL or bytes != state_bytes");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(host_buf, s->dev, bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "state export");
+}
+
+ci_status ci_import_state(ci_states s, const void *host_buf, uint64_t bytes, void *stream) {
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    if (!host_buf || bytes != s->bytes) return fail(CI_E_INVAL, "host_buf NULL or bytes != state_bytes");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(s->dev, host_buf, bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "state import");
+    std::memcpy(s->table, host_buf, kTableBytes);
+    return CI_OK;
+}
+
+const char *ci_last_error(void) { return g_err.c_str(); }
+
+uint32_t ci_version(void) { return 10000u; }
+
+}  // extern "C"

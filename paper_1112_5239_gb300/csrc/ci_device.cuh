@@ -1,0 +1,291 @@
+// ci_device.cuh -- device building blocks of the chaotic-iterations PRNG for
+// sm_103a: seeding, strategy sources (Algorithm 2 XORshift, 32-bit xor128,
+// BBS with Montgomery reduction), and the per-warp generation loop that runs
+// Algorithm 4/5's mixing and the Eq. (Oplus) update with the lanes' state in
+// registers.
+//
+// Mapping of the paper's thread model onto a warp: one lane per stream; a group
+// of C <= 32 consecutive lanes mixes within itself, so a warp holds 32 / C
+// whole groups and the exchange of last strategies ("shmem[o1]",
+// "shmem[o2]") is two register shuffles.  All lanes of the warp execute each
+// shuffle before any lane updates its slot, which is the synchronous reading
+// of Algorithm 4's unsynchronised shared-memory read/write: iteration i reads
+// the partners' strategies of iteration i - 1.
+#pragma once
+
+#include <cstdint>
+
+#include "ci_internal.h"
+
+namespace ci {
+namespace dev {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ seeding
+// splitmix64 (Steele, Lea & Flood 2014) used counter-based: draw k of lane l
+// is the (l * 2^32 + k + 1)-th output of the generator started at `seed`.
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t lane_draw(uint64_t seed, uint64_t lane, uint64_t k) {
+    return sm64_mix(seed + ((lane << 32) + k + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+
+// ------------------------------------------------------- strategy sources
+// Each source: load/store of its words for lane l, the pair of combination
+// arrays the lane uses, and next() returning the lane's own strategy word.
+
+// 32-bit xor128 (Marsaglia), the xor-like the paper uses for Algorithm 4.
+struct SrcXor128 {
+    static constexpr bool kHeavy = false;
+    uint32_t a, b, c, d;
+    __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
+        a = s.u32[F_A * s.P + l];
+        b = s.u32[F_B * s.P + l];
+        c = s.u32[F_C * s.P + l];
+        d = s.u32[F_D * s.P + l];
+    }
+    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const {
+        s.u32[F_A * s.P + l] = a;
+        s.u32[F_B * s.P + l] = b;
+        s.u32[F_C * s.P + l] = c;
+        s.u32[F_D * s.P + l] = d;
+    }
+    __device__ __forceinline__ void arrays(const DevState &, uint64_t, int &a1, int &a2) const {
+        a1 = 0;
+        a2 = 1;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        const uint32_t s = a ^ (a << 11);
+        a = b;
+        b = c;
+        c = d;
+        d = d ^ (d >> 19) ^ (s ^ (s >> 8));
+        return d;
+    }
+};
+
+// Algorithm 2: z ^= z << 13; z ^= z >> 17; z ^= z << 5.
+struct SrcXorshift32 {
+    static constexpr bool kHeavy = false;
+    uint32_t z;
+    __device__ __forceinline__ void load(const DevState &s, uint64_t l) { z = s.u32[F_A * s.P + l]; }
+    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const { s.u32[F_A * s.P + l] = z; }
+    __device__ __forceinline__ void arrays(const DevState &, uint64_t, int &a1, int &a2) const {
+        a1 = 0;
+        a2 = 1;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        z ^= z << 13;
+        z ^= z >> 17;
+        z ^= z << 5;
+        return z;
+    }
+};
+
+// ------------------------------------------------ Montgomery arithmetic
+// R = 2^64, M odd with 2^32 <= M < 2^62, Mp = -M^-1 mod R.  Values are kept
+// "lazy" in [0, 2M): for a, b < 2M, a*b < 4M^2 < M R (as 4M < R), so
+// (a*b + m M) / R < 2M with m = (a*b mod R) Mp mod R -- no final subtraction.
+__device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t M, uint64_t Mp) {
+    const uint64_t tlo = a * b;
+    const uint64_t thi = __umul64hi(a, b);
+    const uint64_t m = tlo * Mp;
+    // tlo + lo(m M) = 0 mod R: it wraps (carry 1) exactly when tlo != 0
+    return thi + __umul64hi(m, M) + (tlo != 0 ? 1ull : 0ull);
+}
+
+// Canonical residue of a lazy value a < 2M: (a + m M) / R with m = a Mp.
+// The quotient is < M + 2M/R, i.e. <= M, and equals M only if a = 0 mod M,
+// which for a in [0, 2M) with a != M means a = 0 (giving 0): the result is
+// already in [0, M).  (a = M cannot arise: 0 stays 0 under squaring.)
+__device__ __forceinline__ uint64_t mont_out(uint64_t a, uint64_t M, uint64_t Mp) {
+    const uint64_t m = a * Mp;
+    return __umul64hi(m, M) + (a != 0 ? 1ull : 0ull);
+}
+
+// -M^-1 mod 2^64 by Newton's iteration (each step doubles the correct bits;
+// M * M = 1 mod 8 gives 3 bits to start).
+__device__ __forceinline__ uint64_t neg_inv64(uint64_t M) {
+    uint64_t inv = M;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) inv *= 2ull - M * inv;
+    return 0ull - inv;
+}
+
+// 2^128 mod M: 2^64 mod M, then 64 modular doublings (values < 2^62).
+__device__ __forceinline__ uint64_t r2_mod(uint64_t M) {
+    uint64_t r = (0ull - M) % M;
+    for (int i = 0; i < 64; ++i) {
+        r <<= 1;
+        if (r >= M) r -= M;
+    }
+    return r;
+}
+
+// Blum Blum Shub strategy source (Algorithm 5 generalised to w = 5 bits per
+// squaring for 62-bit moduli): 7 chunks of 5 bits, then two shift steps.
+struct SrcBbs {
+    static constexpr bool kHeavy = true;
+    uint64_t Y, M, Mp;  // Y: Montgomery form of the BBS state, lazy in [0, 2M)
+    uint32_t sel;
+    __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
+        const uint64_t y = s.u64[G_Y * s.P + l];
+        M = s.u64[G_M * s.P + l];
+        Mp = s.u64[G_MP * s.P + l];
+        const uint64_t r2 = s.u64[G_R2 * s.P + l];
+        Y = mont_mul(y, r2, M, Mp);  // y R mod M (y < 2^64, r2 < M: product < M R)
+        sel = s.u32[F_SEL * s.P + l];
+    }
+    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const {
+        s.u64[G_Y * s.P + l] = mont_out(Y, M, Mp);
+    }
+    __device__ __forceinline__ void arrays(const DevState &, uint64_t, int &a1, int &a2) const {
+        a1 = (int)(sel & 7u);
+        a2 = 8 + (int)((sel >> 8) & 7u);
+    }
+    // One BBS output: x <- x^2 mod M, returned canonical (its low bits are the
+    // secure ones).
+    __device__ __forceinline__ uint32_t bbs() {
+        Y = mont_mul(Y, Y, M, Mp);
+        return (uint32_t)mont_out(Y, M, Mp);
+    }
+    __device__ __forceinline__ uint32_t next() {
+        uint32_t t = 0;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) t = (t << 5) | (bbs() & 31u);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const uint32_t shift = bbs() & 3u;
+            t <<= shift;
+            t |= bbs() & ((1u << shift) - 1u);  // array_shift = {0, 1, 3, 7}
+        }
+        return t;
+    }
+};
+
+// ----------------------------------------------------- generation loop
+enum Sink { SINK_V4 = 0, SINK_SCALAR = 1, SINK_QC = 2 };
+
+// Algorithm 4/5 inner step for one lane: t = own ^ slot[o1] ^ slot[o2];
+// slot = t; x ^= t (Eq. Oplus); returns the output x.
+template <class Src>
+__device__ __forceinline__ uint32_t ci_step(Src &src, uint32_t &x, uint32_t &slot, int p1, int p2) {
+    const uint32_t own = src.next();
+    const uint32_t s1 = __shfl_sync(kFull, slot, p1);
+    const uint32_t s2 = __shfl_sync(kFull, slot, p2);
+    const uint32_t t = own ^ s1 ^ s2;
+    slot = t;
+    x ^= t;
+    return x;
+}
+
+// Quarter-circle test of one output pair in 24-bit fixed point.
+__device__ __forceinline__ uint32_t qc_hit(uint32_t o0, uint32_t o1) {
+    const uint64_t a = o0 >> 8, b = o1 >> 8;
+    return (a * a + b * b < (1ull << 48)) ? 1u : 0u;
+}
+
+// Index of word `col` of row `row` in a warp's 32x32 staging tile: 16-byte
+// chunks XOR-swizzled by row so that both the per-lane 16-byte row writes and
+// the per-row 128-byte reads are free of bank conflicts.
+__device__ __forceinline__ int tile_word(int row, int col) {
+    return row * 32 + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
+}
+
+// Runs n iterations of warp group g (lanes 32g .. 32g+31) of state `st`.
+// Written sinks store stream r's outputs at out[r * ld + col0 + i]
+// (r = 32g + lane < st.S only); SINK_QC adds the lane's quarter-circle hits
+// to counts[r].  `tile` is this warp's 4 KB of shared memory (written sinks).
+// SINK_V4 needs out, ld and col0 aligned to 4 words.
+template <class Src, int SINK>
+__device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64_t n, uint32_t *out,
+                                          uint64_t ld, uint64_t col0, uint64_t *counts,
+                                          uint4 *tile) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t l = g * 32 + lane;
+    Src src;
+    src.load(st, l);
+    uint32_t x = st.u32[F_X * st.P + l];
+    uint32_t slot = st.u32[F_SLOT * st.P + l];
+    int a1, a2;
+    src.arrays(st, l, a1, a2);
+    const int p1 = st.table[a1 * 32 + lane];
+    const int p2 = st.table[a2 * 32 + lane];
+    const uint64_t row0 = g * 32;
+    const uint64_t nfull = n & ~31ull;
+    uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
+    uint64_t hits = 0;
+
+    for (uint64_t i0 = 0; i0 < nfull; i0 += 32) {
+        if (SINK == SINK_QC) {
+            uint32_t h = 0;
+#pragma unroll(Src::kHeavy ? 1 : 16)
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t o0 = ci_step(src, x, slot, p1, p2);
+                const uint32_t o1 = ci_step(src, x, slot, p1, p2);
+                h += qc_hit(o0, o1);
+            }
+            hits += h;
+        } else {
+#pragma unroll(Src::kHeavy ? 1 : 8)
+            for (int q = 0; q < 8; ++q) {
+                uint4 v;
+                v.x = ci_step(src, x, slot, p1, p2);
+                v.y = ci_step(src, x, slot, p1, p2);
+                v.z = ci_step(src, x, slot, p1, p2);
+                v.w = ci_step(src, x, slot, p1, p2);
+                tile[lane * 8 + (q ^ (lane & 7))] = v;
+            }
+            __syncwarp();
+            if (SINK == SINK_V4) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int r = 4 * k + (lane >> 3), c = lane & 7;
+                    const uint4 v = tile[r * 8 + (c ^ (r & 7))];
+                    if (row0 + r < st.S)
+                        __stcs(reinterpret_cast<uint4 *>(out + (row0 + r) * ld + col0 + i0 + 4 * c), v);
+                }
+            } else {
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const uint32_t v = tw[tile_word(r, lane)];
+                    if (row0 + r < st.S) out[(row0 + r) * ld + col0 + i0 + lane] = v;
+                }
+            }
+            __syncwarp();
+        }
+    }
+
+    const int rem = (int)(n - nfull);
+    if (rem) {
+        if (SINK == SINK_QC) {
+            uint32_t h = 0;
+            for (int k = 0; k < rem / 2; ++k) {
+                const uint32_t o0 = ci_step(src, x, slot, p1, p2);
+                const uint32_t o1 = ci_step(src, x, slot, p1, p2);
+                h += qc_hit(o0, o1);
+            }
+            hits += h;
+        } else {
+            for (int k = 0; k < rem; ++k) tw[tile_word(lane, k)] = ci_step(src, x, slot, p1, p2);
+            __syncwarp();
+            for (int r = 0; r < 32; ++r) {
+                if (lane < rem && row0 + r < st.S)
+                    out[(row0 + r) * ld + col0 + nfull + lane] = tw[tile_word(r, lane)];
+            }
+            __syncwarp();
+        }
+    }
+
+    src.store(st, l);
+    st.u32[F_X * st.P + l] = x;
+    st.u32[F_SLOT * st.P + l] = slot;
+    if (SINK == SINK_QC && l < st.S) counts[l] += hits;
+}
+
+}  // namespace dev
+}  // namespace ci

@@ -1,0 +1,64 @@
+// ci_internal.h -- host-side structures shared by the library's translation
+// units (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "ci_prng.h"
+
+namespace ci {
+
+// Device state layout (see ci_export_state in ci_prng.h).
+constexpr int kTableBytes = 512;     // partner table u8[16][32]
+constexpr int kU32Fields = 9;        // a b c d x slot sel p q
+constexpr int kU64Fields = 4;        // y M Mp r2 (BBS only)
+enum U32Field { F_A = 0, F_B = 1, F_C = 2, F_D = 3, F_X = 4, F_SLOT = 5, F_SEL = 6, F_P = 7, F_Q = 8 };
+enum U64Field { G_Y = 0, G_M = 1, G_MP = 2, G_R2 = 3 };
+
+// Device view of one handle's state, passed to kernels by value.
+struct DevState {
+    const uint8_t *table;  // [16][32]
+    uint32_t *u32;         // field f at u32 + f * P
+    uint64_t *u64;         // field g at u64 + g * P (BBS)
+    uint64_t P;            // lanes (multiple of 32)
+    uint64_t S;            // streams returned
+};
+
+uint64_t state_bytes_for(int variant, uint64_t P);
+
+}  // namespace ci
+
+struct ci_states_s {
+    uint32_t magic;
+    int32_t variant, xl;
+    uint32_t C;
+    uint64_t S, P;
+    uint64_t bytes;
+    void *dev;
+    bool owns;
+    uint8_t comb[16 * 32];
+    uint8_t table[ci::kTableBytes];
+    ci::DevState view() const;
+};
+
+namespace ci {
+
+constexpr uint32_t kMagic = 0xC1C1A05Eu;
+
+// Thread-local error message; returns `st` for tail calls.
+ci_status fail(ci_status st, const std::string &msg);
+ci_status cuda_fail(cudaError_t e, const char *what);
+bool valid_handle(const ci_states s);
+
+// Kernel launchers (ci_kernels.cu).  All asynchronous on `stream`.
+cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first_stream, cudaStream_t stream);
+cudaError_t launch_generate(const ci_states_s &h, uint64_t n, uint32_t *out, cudaStream_t stream);
+cudaError_t launch_fused_qc(const ci_states_s &h, uint64_t n, uint64_t *counts, cudaStream_t stream);
+
+int sm_count();
+
+}  // namespace ci

@@ -1,0 +1,212 @@
+// ci_kernels.cu -- seeding and generation kernels of the chaotic-iterations
+// PRNG (Algorithms 4 and 5 of the paper with Eq. (Oplus)), and their host
+// launchers.
+//
+// Work decomposition: one warp per group of 32 lanes ("warp group"), lanes'
+// state in registers for the whole call, a persistent grid sized from the
+// occupancy calculator (a multiple of the SM count) whose warps stride over
+// the warp groups.  Written outputs are staged per warp in a 4 KB swizzled
+// shared-memory tile of 32 streams x 32 iterations and leave as full 128-byte
+// row segments (16-byte streaming stores); the fused form keeps only a
+// per-lane hit count.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ci_device.cuh"
+
+namespace ci {
+
+using namespace dev;
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlockThreads = kWarpsPerBlock * 32;
+
+// ------------------------------------------------------------- seeding
+__global__ void __launch_bounds__(256) k_init_xor(DevState st, uint64_t seed, uint64_t first, int xl) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < st.P; l += stride) {
+        const uint64_t d0 = lane_draw(seed, first + l, 0);
+        const uint64_t d1 = lane_draw(seed, first + l, 1);
+        const uint64_t d2 = lane_draw(seed, first + l, 2);
+        uint32_t a, b = 0, c = 0, d = 0;
+        if (xl == CI_XL_XOR128) {
+            a = (uint32_t)d0;
+            b = (uint32_t)(d0 >> 32);
+            c = (uint32_t)d1;
+            d = (uint32_t)(d1 >> 32);
+            if ((a | b | c | d) == 0u) a = 1u;
+        } else {
+            a = (uint32_t)d0;
+            if (a == 0u) a = 1u;
+        }
+        st.u32[F_A * st.P + l] = a;
+        st.u32[F_B * st.P + l] = b;
+        st.u32[F_C * st.P + l] = c;
+        st.u32[F_D * st.P + l] = d;
+        st.u32[F_X * st.P + l] = (uint32_t)d2;
+        st.u32[F_SLOT * st.P + l] = (uint32_t)(d2 >> 32);
+        st.u32[F_SEL * st.P + l] = 0u;
+        st.u32[F_P * st.P + l] = 0u;
+        st.u32[F_Q * st.P + l] = 0u;
+    }
+}
+
+__device__ __forceinline__ uint32_t mulmod32(uint32_t a, uint32_t b, uint32_t n) {
+    return (uint32_t)(((uint64_t)a * b) % n);
+}
+
+__device__ uint32_t powmod32(uint32_t a, uint32_t e, uint32_t n) {
+    uint32_t r = 1u;
+    while (e) {
+        if (e & 1u) r = mulmod32(r, a, n);
+        a = mulmod32(a, a, n);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Miller-Rabin with bases 2, 7, 61: exact for odd n < 4,759,123,141
+// (Jaeschke 1993); here n is an odd number in [2^30, 2^31).
+__device__ bool is_prime_mr(uint32_t n) {
+    uint32_t d = n - 1u;
+    int s = 0;
+    while ((d & 1u) == 0u) {
+        d >>= 1;
+        ++s;
+    }
+    const uint32_t bases[3] = {2u, 7u, 61u};
+    for (int i = 0; i < 3; ++i) {
+        uint32_t x = powmod32(bases[i], d, n);
+        if (x == 1u || x == n - 1u) continue;
+        bool composite = true;
+        for (int r = 1; r < s; ++r) {
+            x = mulmod32(x, x, n);
+            if (x == n - 1u) {
+                composite = false;
+                break;
+            }
+        }
+        if (composite) return false;
+    }
+    return true;
+}
+
+// Blum prime candidate from a draw: 2^30 + (d >> 34), forced to 3 mod 4.
+__device__ __forceinline__ uint32_t blum_candidate(uint64_t d) {
+    return (uint32_t)((1ull << 30) + (d >> 34)) | 3u;
+}
+
+__global__ void __launch_bounds__(256) k_init_bbs(DevState st, uint64_t seed, uint64_t first) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < st.P; l += stride) {
+        uint64_t k = 0, d;
+        uint32_t p, q;
+        do {
+            d = lane_draw(seed, first + l, k++);
+            p = blum_candidate(d);
+        } while (!is_prime_mr(p));
+        do {
+            d = lane_draw(seed, first + l, k++);
+            q = blum_candidate(d);
+        } while (q == p || !is_prime_mr(q));
+        const uint64_t M = (uint64_t)p * q;
+        uint64_t v;
+        do {
+            d = lane_draw(seed, first + l, k++);
+            v = 2ull + d % (M - 2ull);
+        } while (v % p == 0ull || v % q == 0ull);  // gcd(v, p q) = 1
+        d = lane_draw(seed, first + l, k++);
+        for (int f = F_A; f <= F_D; ++f) st.u32[f * st.P + l] = 0u;
+        st.u32[F_X * st.P + l] = (uint32_t)d;
+        st.u32[F_SLOT * st.P + l] = (uint32_t)(d >> 32);
+        st.u32[F_SEL * st.P + l] = (uint32_t)(v & 7u) | ((uint32_t)((v >> 3) & 7u) << 8);
+        st.u32[F_P * st.P + l] = p;
+        st.u32[F_Q * st.P + l] = q;
+        st.u64[G_Y * st.P + l] = v;
+        st.u64[G_M * st.P + l] = M;
+        st.u64[G_MP * st.P + l] = neg_inv64(M);
+        st.u64[G_R2 * st.P + l] = r2_mod(M);
+    }
+}
+
+// ----------------------------------------------------------- generation
+template <class Src, int SINK>
+__global__ void __launch_bounds__(kBlockThreads) k_generate(DevState st, uint64_t n, uint32_t *out,
+                                                            uint64_t *counts) {
+    __shared__ uint4 tiles[SINK == SINK_QC ? 1 : kWarpsPerBlock][256];
+    const int w = threadIdx.x >> 5;
+    const uint64_t ngroups = st.P / 32;
+    const uint64_t gstride = (uint64_t)gridDim.x * kWarpsPerBlock;
+    for (uint64_t g = (uint64_t)blockIdx.x * kWarpsPerBlock + w; g < ngroups; g += gstride)
+        warp_task<Src, SINK>(st, g, n, out, n, 0, counts, tiles[SINK == SINK_QC ? 0 : w]);
+}
+
+// ------------------------------------------------------------ launchers
+int sm_count() {
+    static int count = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+        if (count <= 0) count = 1;
+    });
+    return count;
+}
+
+// Persistent grid: SMs x resident blocks per SM, but no more blocks than
+// there are warp groups to cover.
+template <class K>
+static unsigned grid_for(K kernel, uint64_t ngroups) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlockThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const uint64_t cap = (uint64_t)sm_count() * per_sm;
+    const uint64_t need = (ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+template <class Src, int SINK>
+static cudaError_t launch_gen(const DevState &st, uint64_t n, uint32_t *out, uint64_t *counts,
+                              cudaStream_t stream) {
+    auto kern = k_generate<Src, SINK>;
+    const unsigned grid = grid_for(kern, st.P / 32);
+    if (grid == 0) return cudaSuccess;
+    kern<<<grid, kBlockThreads, 0, stream>>>(st, n, out, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first, cudaStream_t stream) {
+    const DevState st = h.view();
+    const uint64_t blocks = (h.P + kBlockThreads - 1) / kBlockThreads;
+    const unsigned grid = (unsigned)(blocks < 65535 ? blocks : 65535);
+    if (h.variant == CI_VAR_BBS)
+        k_init_bbs<<<grid, kBlockThreads, 0, stream>>>(st, seed, first);
+    else
+        k_init_xor<<<grid, kBlockThreads, 0, stream>>>(st, seed, first, h.xl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generate(const ci_states_s &h, uint64_t n, uint32_t *out, cudaStream_t stream) {
+    const DevState st = h.view();
+    const bool v4 = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) && (n % 4 == 0);
+    if (h.variant == CI_VAR_BBS)
+        return v4 ? launch_gen<SrcBbs, SINK_V4>(st, n, out, nullptr, stream)
+                  : launch_gen<SrcBbs, SINK_SCALAR>(st, n, out, nullptr, stream);
+    if (h.xl == CI_XL_XORSHIFT32)
+        return v4 ? launch_gen<SrcXorshift32, SINK_V4>(st, n, out, nullptr, stream)
+                  : launch_gen<SrcXorshift32, SINK_SCALAR>(st, n, out, nullptr, stream);
+    return v4 ? launch_gen<SrcXor128, SINK_V4>(st, n, out, nullptr, stream)
+              : launch_gen<SrcXor128, SINK_SCALAR>(st, n, out, nullptr, stream);
+}
+
+cudaError_t launch_fused_qc(const ci_states_s &h, uint64_t n, uint64_t *counts, cudaStream_t stream) {
+    const DevState st = h.view();
+    if (h.variant == CI_VAR_BBS) return launch_gen<SrcBbs, SINK_QC>(st, n, nullptr, counts, stream);
+    if (h.xl == CI_XL_XORSHIFT32) return launch_gen<SrcXorshift32, SINK_QC>(st, n, nullptr, counts, stream);
+    return launch_gen<SrcXor128, SINK_QC>(st, n, nullptr, counts, stream);
+}
+
+}  // namespace ci

@@ -1,0 +1,30 @@
+"""Helpers shared by the GPU tests: build/load the CUDA library, run the
+oracle on the same parameters, and move outputs to numpy uint32."""
+import numpy as np
+import pytest
+
+import oracle
+
+VAR = {"xor": 0, "bbs": 1}
+XL = {"xor128": 0, "xorshift32": 1}
+
+
+def cuda_or_skip():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1112_5239_gb300 import build
+
+    build.build()
+    import paper_1112_5239_gb300 as ci
+
+    return torch, ci
+
+
+def u32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def oracle_gen(variant, xl, C, seed, comb_seed, S, comb=None, lane0=0, n_lanes=None):
+    return oracle.Generator(VAR[variant], XL.get(xl, 0), C, seed, comb_seed, S, comb=comb, lane0=lane0,
+                            n_lanes=n_lanes)

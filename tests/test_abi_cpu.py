@@ -1,0 +1,93 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, exports
+every function include/*.h declares, and its host-side argument checks
+return the documented statuses (no compute is launched: no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1112_5239_gb300 import build, _lib
+
+    build.build()
+    return _lib
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ci_[a-z0-9_]+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_core_calls():
+    names = _declared_functions()
+    for n in ["ci_init_states", "ci_generate", "ci_generate_bbs", "ci_generate_fused_qc", "ci_free_states",
+              "ci_export_state", "ci_import_state", "ci_last_error"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    lib = L.lib()
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_errors_without_gpu(L):
+    lib = L.lib()
+    assert lib.ci_version() >= 10000
+    p = L.ci_params()
+    p.variant, p.xl, p.comb_size, p.seed = 0, 0, 32, 1
+    nbytes = ctypes.c_uint64()
+    assert lib.ci_state_bytes(ctypes.byref(p), 4096, ctypes.byref(nbytes)) == 0
+    assert nbytes.value == 512 + 9 * 4 * 4096
+    p.variant = 1
+    assert lib.ci_state_bytes(ctypes.byref(p), 33, ctypes.byref(nbytes)) == 0
+    assert nbytes.value == 512 + 9 * 4 * 64 + 4 * 8 * 64
+    bad = []
+    for field, value in [("comb_size", 3), ("comb_size", 64), ("variant", 7), ("flags", 1),
+                         ("first_stream", 5)]:
+        q = L.ci_params()
+        q.variant, q.xl, q.comb_size = 0, 0, 32
+        setattr(q, field, value)
+        bad.append(lib.ci_state_bytes(ctypes.byref(q), 10, ctypes.byref(nbytes)))
+    assert bad == [-1] * 5
+    assert b"first_stream" in lib.ci_last_error()
+    q = L.ci_params()
+    q.variant, q.xl, q.comb_size = 0, 0, 32
+    assert lib.ci_state_bytes(ctypes.byref(q), 0, ctypes.byref(nbytes)) == -1
+    assert lib.ci_state_bytes(ctypes.byref(q), 2**32 + 1, ctypes.byref(nbytes)) == -1
+    h = ctypes.c_void_p()
+    q.comb_size = 5
+    assert lib.ci_init_states(ctypes.byref(q), 10, None, ctypes.byref(h)) == -1 and not h.value
+    assert lib.ci_generate(None, 4, None, 0, None) == -6
+    assert lib.ci_free_states(None) == 0
+
+
+def test_workload_generators_are_deterministic():
+    from paper_1112_5239_gb300 import workloads as W
+
+    a = W.batched_requests(count=500)
+    b = W.batched_requests(count=500)
+    assert a == b
+    assert all(1 <= r.n_streams <= 2**16 and 2**6 <= r.n_per_stream <= 2**20 for r in a)
+    frac_xor = sum(r.variant == "xor" for r in a) / len(a)
+    assert 0.7 < frac_xor < 0.9
+    s = W.serving_requests(count=300)
+    assert s == W.serving_requests(count=300)
+    assert all(s[i].arrival <= s[i + 1].arrival for i in range(len(s) - 1))
+    for r in s:
+        if r.continues >= 0:
+            base = s[r.continues]
+            assert base.continues < 0 and base.n_streams == r.n_streams and base.seed == r.seed

@@ -1,0 +1,74 @@
+"""GPU parity at the full workload sizes, in the launch configuration the
+benchmark times: the GPU runs every stream; the oracle recomputes a prefix or
+sampled groups (groups are independent, so a sampled group is exact)."""
+import numpy as np
+import pytest
+
+from gpu_util import cuda_or_skip, oracle_gen, u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return cuda_or_skip()
+
+
+def test_plain_2e20x4096_written_chunks_prefix(env):
+    """2^20 streams x 4096 outputs, seed 2, written as 16 chunks of 256
+    outputs per stream (1 GiB each): the 2^14-stream prefix of every chunk and
+    the last group's rows equal the oracle's."""
+    torch, ci = env
+    from paper_1112_5239_gb300.workloads import PLAIN_2E20x4096 as W
+
+    S, chunk = W.n_streams, W.chunk
+    st = ci.States(S, variant=W.variant, xl=W.xl, comb_size=W.comb_size, seed=W.seed, comb_seed=W.comb_seed)
+    out = torch.empty((S, chunk), dtype=torch.int32, device="cuda")
+    pre = oracle_gen(W.variant, W.xl, W.comb_size, W.seed, W.comb_seed, S, n_lanes=1 << 14)
+    last = oracle_gen(W.variant, W.xl, W.comb_size, W.seed, W.comb_seed, S, lane0=S - 32, n_lanes=32)
+    for c in range(W.n_per_stream // chunk):
+        st.generate(chunk, out=out)
+        got_pre = u32(out[: 1 << 14])
+        got_last = u32(out[S - 32:])
+        assert np.array_equal(got_pre, pre.generate(chunk)), c
+        assert np.array_equal(got_last, last.generate(chunk)), c
+
+
+def test_plain_2e20x4096_fused_prefix(env):
+    torch, ci = env
+    from paper_1112_5239_gb300.workloads import PLAIN_2E20x4096 as W
+
+    S = W.n_streams
+    st = ci.States(S, variant=W.variant, xl=W.xl, comb_size=W.comb_size, seed=W.seed, comb_seed=W.comb_seed)
+    counts = st.generate_fused_qc(W.n_per_stream).cpu().numpy().view(np.uint64)
+    pre = oracle_gen(W.variant, W.xl, W.comb_size, W.seed, W.comb_seed, S, n_lanes=1 << 14)
+    assert np.array_equal(counts[: 1 << 14], pre.fused_qc(W.n_per_stream))
+    # every stream's count is a valid number of hits among 2048 pairs, and the
+    # total estimates pi/4 (2^31 pairs: 6 sigma ~ 5.4e-5)
+    assert counts.max() <= W.n_per_stream // 2
+    frac = counts.sum() / (S * W.n_per_stream / 2)
+    assert abs(frac - np.pi / 4) < 6 * np.sqrt(np.pi / 4 * (1 - np.pi / 4) / (S * W.n_per_stream / 2))
+
+
+def test_bbs_2e16x16384_sampled_groups(env):
+    torch, ci = env
+    from paper_1112_5239_gb300.workloads import BBS_2E16x16384 as W
+
+    S, L = W.n_streams, W.n_per_stream
+    st = ci.States(S, variant="bbs", comb_size=W.comb_size, seed=W.seed, comb_seed=W.comb_seed)
+    out = st.generate(L)
+    torch.cuda.synchronize()
+    for g in [0, 1, 777, S // 32 - 1]:
+        ref = oracle_gen("bbs", "xor128", W.comb_size, W.seed, W.comb_seed, S, lane0=32 * g, n_lanes=32)
+        assert np.array_equal(u32(out[32 * g: 32 * g + 32]), ref.generate(L)), g
+
+
+def test_sharded_handles_reproduce_one_range(env):
+    """Handles over consecutive slices (first_stream) of one stream range
+    produce exactly the rows of the single handle (how the work shards over
+    GPUs: no exchange between slices)."""
+    torch, ci = env
+    S, L = 4096, 96
+    whole = u32(ci.States(S, seed=12, comb_size=16).generate(L))
+    parts = [u32(ci.States(1024, seed=12, comb_size=16, first_stream=r * 1024).generate(L)) for r in range(4)]
+    assert np.array_equal(np.concatenate(parts), whole)

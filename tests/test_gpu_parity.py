@@ -1,0 +1,177 @@
+"""GPU parity: every output of the CUDA path equals the oracle's, bit for bit
+(integer work, nothing relaxed), called through the C ABI via the binding."""
+import itertools
+
+import numpy as np
+import pytest
+
+from gpu_util import cuda_or_skip, oracle_gen, u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return cuda_or_skip()
+
+
+def _states(ci, variant, xl, C, seed, comb_seed, S, **kw):
+    return ci.States(S, variant=variant, xl=xl, comb_size=C, seed=seed, comb_seed=comb_seed, **kw)
+
+
+def test_plain_4096x1024_full(env):
+    """4096 streams x 1024 outputs, xor128, C = 32, seed 1: all 4 Mi outputs
+    and the final state equal the oracle's."""
+    torch, ci = env
+    st = _states(ci, "xor", "xor128", 32, 1, 0, 4096)
+    out = u32(st.generate(1024))
+    torch.cuda.synchronize()
+    orc = oracle_gen("xor", "xor128", 32, 1, 0, 4096)
+    ref = orc.streams(1024)
+    assert np.array_equal(out, ref)
+    s = ci.unpack_state(st.export_state(), 4096, 0)
+    for f, k in [("a", 0), ("b", 1), ("c", 2), ("d", 3)]:
+        assert np.array_equal(s[f], orc.lanes["w"][:, k])
+    assert np.array_equal(s["x"], orc.lanes["x"]) and np.array_equal(s["slot"], orc.lanes["tprev"])
+
+
+SHAPES = [(1, 1), (5, 3), (31, 32), (32, 33), (33, 64), (100, 31), (257, 129), (64, 100), (40, 4)]
+
+
+@pytest.mark.parametrize("xl", ["xor128", "xorshift32"])
+@pytest.mark.parametrize("C", [1, 2, 4, 8, 16, 32])
+def test_small_shapes_xor(env, xl, C):
+    torch, ci = env
+    for S, L in SHAPES:
+        st = _states(ci, "xor", xl, C, 77 + S, 5, S)
+        out = u32(st.generate(L))
+        ref = oracle_gen("xor", xl, C, 77 + S, 5, S).streams(L)
+        assert np.array_equal(out, ref), (S, L)
+
+
+def test_misaligned_output_uses_scalar_path(env):
+    """Output base not 16-byte aligned (and L a multiple of 4): still exact,
+    and nothing outside the requested range is written."""
+    torch, ci = env
+    S, L = 70, 64
+    st = _states(ci, "xor", "xor128", 8, 3, 1, S)
+    buf = torch.full((S * L + 9,), -7, dtype=torch.int32, device="cuda")
+    view = buf[1:1 + S * L].view(S, L)
+    st.generate(L, out=view)
+    b = u32(buf)
+    assert np.array_equal(b[1:1 + S * L].reshape(S, L), oracle_gen("xor", "xor128", 8, 3, 1, S).streams(L))
+    assert (b[0] == np.uint32(2**32 - 7)) and np.all(b[1 + S * L:] == np.uint32(2**32 - 7))
+
+
+def test_guard_words_untouched(env):
+    torch, ci = env
+    S, L = 45, 96
+    st = _states(ci, "xor", "xor128", 32, 9, 0, S)
+    buf = torch.full((S * L + 64,), 12345, dtype=torch.int32, device="cuda")
+    st.generate(L, out=buf[:S * L].view(S, L))
+    assert np.all(u32(buf[S * L:]) == 12345)
+
+
+@pytest.mark.parametrize("variant,xl", [("xor", "xor128"), ("xor", "xorshift32"), ("bbs", "xor128")])
+def test_continuation_any_split(env, variant, xl):
+    torch, ci = env
+    S = 96
+    total = 200
+    ref = oracle_gen(variant, xl, 16, 11, 2, S).streams(total)
+    for split in [(200,), (1, 199), (32, 32, 136), (7, 0, 64, 129), (100, 100)]:
+        st = _states(ci, variant, xl, 16, 11, 2, S)
+        parts = [u32(st.generate(n)) if n else np.zeros((S, 0), np.uint32) for n in split]
+        assert np.array_equal(np.concatenate(parts, axis=1), ref), split
+
+
+def test_export_import_resume(env):
+    torch, ci = env
+    S = 64
+    a = _states(ci, "xor", "xor128", 32, 4, 0, S)
+    a.generate(50)
+    snap = a.export_state()
+    tail_a = u32(a.generate(70))
+    b = _states(ci, "xor", "xor128", 32, 4, 0, S)
+    b.import_state(snap)
+    assert np.array_equal(u32(b.generate(70)), tail_a)
+
+
+@pytest.mark.parametrize("variant", ["xor", "bbs"])
+def test_fused_qc_matches_oracle_and_written_state(env, variant):
+    torch, ci = env
+    S, L = 130, 2 * 75
+    st = _states(ci, variant, "xor128", 32, 21, 0, S)
+    counts = u32(st.generate_fused_qc(L).view(torch.int32)).view(np.uint64)
+    orc = oracle_gen(variant, "xor128", 32, 21, 0, S)
+    ref = orc.fused_qc(L)[:S]
+    assert np.array_equal(counts, ref)
+    # accumulation across calls, and the state moved as the written form would
+    more = st.generate_fused_qc(L, counts=torch.from_numpy(counts.view(np.int64).copy()).cuda())
+    ref2 = ref + orc.fused_qc(L)[:S]
+    assert np.array_equal(u32(more.view(torch.int32)).view(np.uint64), ref2)
+    assert np.array_equal(u32(st.generate(8)), orc.streams(8))
+
+
+def test_explicit_combination_arrays(env):
+    torch, ci = env
+    C, S, L = 8, 48, 40
+    rng = np.random.default_rng(0)
+    comb = np.concatenate([rng.permutation(C), rng.permutation(C)]).astype(np.uint8)
+    comb[C:] = comb[:C]  # equal arrays: the mixing cancels
+    st = _states(ci, "xor", "xor128", C, 6, 0, S, comb=comb)
+    ref = oracle_gen("xor", "xor128", C, 6, 0, S, comb=comb).streams(L)
+    assert np.array_equal(u32(st.generate(L)), ref)
+    bcomb = np.stack([rng.permutation(C) for _ in range(16)]).astype(np.uint8).reshape(-1)
+    st = _states(ci, "bbs", "xor128", C, 6, 0, S, comb=bcomb)
+    ref = oracle_gen("bbs", "xor128", C, 6, 0, S, comb=bcomb).streams(L)
+    assert np.array_equal(u32(st.generate(L)), ref)
+
+
+def test_state_in_torch_memory(env):
+    torch, ci = env
+    st = _states(ci, "xor", "xor128", 32, 8, 0, 200, memory="torch")
+    assert np.array_equal(u32(st.generate(64)), oracle_gen("xor", "xor128", 32, 8, 0, 200).streams(64))
+
+
+@pytest.mark.parametrize("C", [1, 4, 32])
+def test_bbs_small(env, C):
+    torch, ci = env
+    for S, L in [(1, 5), (33, 33), (100, 64)]:
+        st = _states(ci, "bbs", "xor128", C, 3 + S, 1, S)
+        out = u32(st.generate(L))
+        orc = oracle_gen("bbs", "xor128", C, 3 + S, 1, S)
+        assert np.array_equal(out, orc.streams(L)), (S, L)
+        s = ci.unpack_state(st.export_state(), st.query().n_lanes, 1)
+        P = orc.lanes.shape[0]
+        assert np.array_equal(s["p"][:P], orc.lanes["p"]) and np.array_equal(s["q"][:P], orc.lanes["q"])
+        assert np.array_equal(s["M"][:P], orc.lanes["M"]) and np.array_equal(s["y"][:P], orc.lanes["y"])
+        assert np.array_equal(s["sel"][:P] & 0xFF, orc.lanes["sel1"])
+        assert np.array_equal(s["sel"][:P] >> 8, orc.lanes["sel2"])
+
+
+def test_bbs_montgomery_constants(env):
+    torch, ci = env
+    st = _states(ci, "bbs", "xor128", 32, 3, 0, 256)
+    s = ci.unpack_state(st.export_state(), 256, 1)
+    for M, Mp, r2 in zip(s["M"].tolist(), s["Mp"].tolist(), s["r2"].tolist()):
+        assert (M * Mp) % 2**64 == 2**64 - 1
+        assert r2 == pow(2, 128, M)
+
+
+def test_error_statuses(env):
+    torch, ci = env
+    st = _states(ci, "xor", "xor128", 32, 1, 0, 10)
+    bb = _states(ci, "bbs", "xor128", 32, 1, 0, 10)
+    small = torch.empty(10 * 8 - 1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ci.CIError) as e:
+        st.generate(8, out=small)
+    assert e.value.status == -1
+    with pytest.raises(ci.CIError) as e:
+        st.generate_fused_qc(7)
+    assert e.value.status == -1
+    from paper_1112_5239_gb300 import _lib
+
+    out = torch.empty(100, dtype=torch.int32, device="cuda")
+    assert _lib.lib().ci_generate_bbs(st.handle, 2, out.data_ptr(), 100, None) == -6
+    assert _lib.lib().ci_generate(bb.handle, 2, out.data_ptr(), 100, None) == -6
+    assert _lib.lib().ci_generate(st.handle, 0, None, 0, None) == 0  # empty call is a no-op
