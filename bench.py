@@ -47,8 +47,41 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="main written-mode line only")
-    ap.add_argument("--cpu-sample-streams", type=int, default=1 << 17)
+    ap.add_argument("--cpu-sample-streams", type=int, default=1 << 19)
+    ap.add_argument("--profile", choices=["written", "fused", "bbs"], default=None,
+                    help="small case for ncu: 2 warm-up launches then 1 launch of one kernel, no timing")
     return ap.parse_args()
+
+
+def run_profile_case(kind: str) -> None:
+    """Small case for profiler captures: 2^19 streams x 256 written (512 MiB,
+    larger than L2), 2^19 x 4096 fused, or 2^16 x 1024 BBS written (256 MiB);
+    two warm-up launches and one more of the same kernel."""
+    import torch
+
+    from paper_1112_5239_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1112_5239_gb300 as ci
+
+    torch.cuda.set_device(0)
+    if kind == "written":
+        st = ci.States(1 << 19, seed=SEED_MAIN)
+        out = torch.empty((1 << 19, CHUNK), dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            st.generate(CHUNK, out=out)
+    elif kind == "fused":
+        st = ci.States(1 << 19, seed=SEED_MAIN)
+        counts = torch.zeros(1 << 19, dtype=torch.int64, device="cuda")
+        for _ in range(3):
+            st.generate_fused_qc(L_MAIN, counts=counts)
+    else:
+        st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
+        out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            st.generate(1024, out=out)
+    torch.cuda.synchronize()
+    print("profile case %s done" % kind)
 
 
 # ------------------------------------------------------------------ clocks
@@ -225,6 +258,9 @@ def run_reference(args, world, rank):
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
+    if args.profile:
+        run_profile_case(args.profile)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
