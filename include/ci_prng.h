@@ -160,6 +160,61 @@ ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out
 ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t *counts_dev,
                                void *cuda_stream);
 
+/* Generation fused with a verification consumer: digest_dev[s] (uint64,
+ * caller-owned, n_streams elements) is SET to the Horner digest of stream s's
+ * outputs o_0 .. o_{n-1} of this call, D = sum_i o_i K^(n-1-i) mod 2^64 with
+ * K = 0xD1342543DE82EF95 (D <- D * K + o_i from D = 0).  No outputs are
+ * stored; the state advances as in the written form.  Not a construct of the
+ * paper: it lets very large runs be compared without holding their outputs.
+ * n_per_stream == 0 is a no-op.
+ * Errors: CI_E_STATE, CI_E_INVAL (digest_dev NULL with n > 0), CI_E_CUDA. */
+ci_status ci_generate_digest(ci_states states, uint64_t n_per_stream, uint64_t *digest_dev,
+                             void *cuda_stream);
+
+/* --------------------------------------------------- batched launches */
+
+/* Where a batch item's outputs go. */
+enum {
+    CI_SINK_WRITTEN = 0,  /* out_dev[s * n_per_stream + i], as ci_generate        */
+    CI_SINK_QC = 1,       /* aux_dev[s] += quarter-circle hits, as the fused call  */
+    CI_SINK_DIGEST = 2    /* aux_dev[s] = digest, as ci_generate_digest            */
+};
+
+typedef struct {
+    ci_states states;           /* handle to advance (xor or BBS: its own variant) */
+    uint64_t n_per_stream;      /* outputs per stream (0: item skipped)            */
+    int32_t sink;               /* CI_SINK_*                                        */
+    int32_t reserved;           /* must be 0                                        */
+    uint32_t *out_dev;          /* CI_SINK_WRITTEN: caller-owned device output      */
+    uint64_t out_capacity_u32;  /* elements available at out_dev                   */
+    uint64_t *aux_dev;          /* CI_SINK_QC / CI_SINK_DIGEST: n_streams uint64    */
+} ci_batch_item;
+
+/* A reusable batch launcher: a device work queue with room for max_items
+ * requests, pinned host staging, and two instantiated CUDA graphs (queue
+ * upload -> one persistent kernel) used alternately, so the host can prepare
+ * one batch while the previous one runs.  Allocates device and pinned host
+ * memory (cudaMalloc, cudaHostAlloc).  Errors: CI_E_INVAL, CI_E_NOMEM,
+ * CI_E_CUDA. */
+typedef struct ci_batch_s *ci_batch;
+ci_status ci_batch_create(uint32_t max_items, ci_batch *out);
+
+/* Runs every item in ONE launch of the persistent kernel, asynchronously on
+ * cuda_stream: each item is the same computation as the single-request call
+ * for its variant and sink (identical outputs and final state), requests of
+ * uneven stream counts, lengths and variants sharing the GPU.  The work queue
+ * holds one entry per item; a unit is (item, warp group of 32 streams, whole
+ * length); warps claim units through an atomic cursor, longest-first.
+ * A handle may appear at most once per batch.  The call may wait for the
+ * batch-before-last on this ci_batch to finish (its staging buffer is reused).
+ * Errors: CI_E_STATE (dead batch or handle), CI_E_INVAL (item checks as for
+ * the single-request calls, duplicate handle, n_items > max_items),
+ * CI_E_CUDA. */
+ci_status ci_batch_run(ci_batch batch, const ci_batch_item *items, uint32_t n_items, void *cuda_stream);
+
+/* Waits for the batch's launches to finish and frees it.  NULL is a no-op. */
+ci_status ci_batch_destroy(ci_batch batch);
+
 /* -------------------------------------------------- checkpoint / resume */
 
 /* Copies the whole device state (bytes == state_bytes) to host_buf /

@@ -19,7 +19,10 @@ from ._lib import CIError, ci_params, ci_states_desc
 VARIANTS = {"xor": _lib.CI_VAR_XOR, "bbs": _lib.CI_VAR_BBS}
 XORLIKES = {"xor128": _lib.CI_XL_XOR128, "xorshift32": _lib.CI_XL_XORSHIFT32}
 
-__all__ = ["States", "CIError", "make_params", "stream_ptr", "VARIANTS", "XORLIKES"]
+SINKS = {"written": _lib.CI_SINK_WRITTEN, "qc": _lib.CI_SINK_QC, "digest": _lib.CI_SINK_DIGEST}
+DIGEST_MUL = 0xD1342543DE82EF95
+
+__all__ = ["States", "Batch", "CIError", "make_params", "stream_ptr", "VARIANTS", "XORLIKES", "SINKS"]
 
 
 def stream_ptr(stream=None) -> int:
@@ -101,6 +104,14 @@ class States:
                   stream_ptr(stream))
         return counts
 
+    def generate_digest(self, n_per_stream, digest=None, stream=None) -> torch.Tensor:
+        """Per-stream Horner digest (int64 [n_streams]) of the next n outputs,
+        without storing them."""
+        if digest is None:
+            digest = torch.zeros(self.n_streams, dtype=torch.int64, device="cuda")
+        _lib.call("ci_generate_digest", self.handle, int(n_per_stream), digest.data_ptr(), stream_ptr(stream))
+        return digest
+
     # ------------------------------------------------- checkpoint/resume
     def export_state(self, stream=None) -> np.ndarray:
         buf = np.zeros(self.state_bytes, dtype=np.uint8)
@@ -123,6 +134,49 @@ class States:
         try:
             if self.handle and torch.cuda.is_available():
                 self.free()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A ``ci_batch``: runs many requests in one persistent-kernel launch.
+
+    ``run`` takes items ``(states, n_per_stream, sink, tensor)`` where sink is
+    "written" (tensor: int32 output with n_streams * n elements), "qc" (int64
+    counts, incremented) or "digest" (int64 digests, overwritten)."""
+
+    def __init__(self, max_items: int):
+        self.handle = ctypes.c_void_p()
+        self.max_items = int(max_items)
+        _lib.call("ci_batch_create", self.max_items, ctypes.byref(self.handle))
+
+    def run(self, items, stream=None) -> None:
+        arr = (_lib.ci_batch_item * max(1, len(items)))()
+        for i, (st, n, sink, t) in enumerate(items):
+            it = arr[i]
+            it.states = st.handle.value if isinstance(st, States) else st
+            it.n_per_stream = int(n)
+            it.sink = SINKS[sink] if isinstance(sink, str) else int(sink)
+            it.reserved = 0
+            if it.sink == _lib.CI_SINK_WRITTEN:
+                it.out_dev = t.data_ptr() if t is not None else None
+                it.out_capacity_u32 = t.numel() if t is not None else 0
+                it.aux_dev = None
+            else:
+                it.out_dev = None
+                it.out_capacity_u32 = 0
+                it.aux_dev = t.data_ptr() if t is not None else None
+        _lib.call("ci_batch_run", self.handle, ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
+
+    def close(self) -> None:
+        if self.handle:
+            _lib.call("ci_batch_destroy", self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self.handle and torch.cuda.is_available():
+                self.close()
         except Exception:
             pass
 

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(PKG, "libci_prng.so")
 CI_OK, CI_PENDING = 0, 1
 CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE = -1, -2, -3, -4, -5, -6
 CI_VAR_XOR, CI_VAR_BBS = 0, 1
+CI_SINK_WRITTEN, CI_SINK_QC, CI_SINK_DIGEST = 0, 1, 2
 CI_XL_XOR128, CI_XL_XORSHIFT32 = 0, 1
 
 STATUS_NAMES = {0: "CI_OK", 1: "CI_PENDING", -1: "CI_E_INVAL", -2: "CI_E_NOMEM", -3: "CI_E_CUDA",
@@ -47,6 +48,18 @@ class ci_states_desc(ctypes.Structure):
     ]
 
 
+class ci_batch_item(ctypes.Structure):
+    _fields_ = [
+        ("states", ctypes.c_void_p),
+        ("n_per_stream", ctypes.c_uint64),
+        ("sink", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("out_dev", ctypes.c_void_p),
+        ("out_capacity_u32", ctypes.c_uint64),
+        ("aux_dev", ctypes.c_void_p),
+    ]
+
+
 class CIError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -65,6 +78,10 @@ _SIGNATURES = {
     "ci_generate": [_VP, _U64, _VP, _U64, _VP],
     "ci_generate_bbs": [_VP, _U64, _VP, _U64, _VP],
     "ci_generate_fused_qc": [_VP, _U64, _VP, _VP],
+    "ci_generate_digest": [_VP, _U64, _VP, _VP],
+    "ci_batch_create": [_U32, _VP],
+    "ci_batch_run": [_VP, _VP, _U32, _VP],
+    "ci_batch_destroy": [_VP],
     "ci_export_state": [_VP, _VP, _U64, _VP],
     "ci_import_state": [_VP, _VP, _U64, _VP],
 }

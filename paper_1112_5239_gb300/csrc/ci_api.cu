@@ -247,6 +247,14 @@ ci_status ci_generate_fused_qc(ci_states s, uint64_t n, uint64_t *counts, void *
     return e == cudaSuccess ? CI_OK : cuda_fail(e, "fused generation kernel launch");
 }
 
+ci_status ci_generate_digest(ci_states s, uint64_t n, uint64_t *digest, void *stream) {
+    if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
+    if (n == 0) return CI_OK;
+    if (!digest) return fail(CI_E_INVAL, "digest_dev is NULL");
+    cudaError_t e = launch_digest(*s, n, digest, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "digest kernel launch");
+}
+
 ci_status ci_export_state(ci_states s, void *host_buf, uint64_t bytes, void *stream) {
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (!host_buf || bytes != s->bytes) return fail(CI_E_INVAL, "host_buf NULL or bytes != state_bytes");

@@ -168,7 +168,11 @@ struct SrcBbs {
 };
 
 // ----------------------------------------------------- generation loop
-enum Sink { SINK_V4 = 0, SINK_SCALAR = 1, SINK_QC = 2 };
+enum Sink { SINK_V4 = 0, SINK_SCALAR = 1, SINK_QC = 2, SINK_DIGEST = 3 };
+
+// Multiplier of the per-stream output digest D <- D * K + x (mod 2^64),
+// an odd 64-bit constant.
+constexpr uint64_t kDigestMul = 0xD1342543DE82EF95ull;
 
 // Algorithm 4/5 inner step for one lane: t = own ^ slot[o1] ^ slot[o2];
 // slot = t; x ^= t (Eq. Oplus); returns the output x.
@@ -199,8 +203,10 @@ __device__ __forceinline__ int tile_word(int row, int col) {
 // Runs n iterations of warp group g (lanes 32g .. 32g+31) of state `st`.
 // Written sinks store stream r's outputs at out[r * ld + col0 + i]
 // (r = 32g + lane < st.S only); SINK_QC adds the lane's quarter-circle hits
-// to counts[r].  `tile` is this warp's 4 KB of shared memory (written sinks).
-// SINK_V4 needs out, ld and col0 aligned to 4 words.
+// to counts[r]; SINK_DIGEST stores the Horner digest of the call's outputs,
+// D = sum_i x_i K^(n-1-i) mod 2^64, to counts[r].  `tile` is this warp's 4 KB
+// of shared memory (written sinks).  SINK_V4 needs out, ld and col0 aligned
+// to 4 words.
 template <class Src, int SINK>
 __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64_t n, uint32_t *out,
                                           uint64_t ld, uint64_t col0, uint64_t *counts,
@@ -221,7 +227,10 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
     uint64_t hits = 0;
 
     for (uint64_t i0 = 0; i0 < nfull; i0 += 32) {
-        if (SINK == SINK_QC) {
+        if (SINK == SINK_DIGEST) {
+#pragma unroll(Src::kHeavy ? 1 : 32)
+            for (int k = 0; k < 32; ++k) hits = hits * kDigestMul + ci_step(src, x, slot, p1, p2);
+        } else if (SINK == SINK_QC) {
             uint32_t h = 0;
 #pragma unroll(Src::kHeavy ? 1 : 16)
             for (int k = 0; k < 16; ++k) {
@@ -262,7 +271,9 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
 
     const int rem = (int)(n - nfull);
     if (rem) {
-        if (SINK == SINK_QC) {
+        if (SINK == SINK_DIGEST) {
+            for (int k = 0; k < rem; ++k) hits = hits * kDigestMul + ci_step(src, x, slot, p1, p2);
+        } else if (SINK == SINK_QC) {
             uint32_t h = 0;
             for (int k = 0; k < rem / 2; ++k) {
                 const uint32_t o0 = ci_step(src, x, slot, p1, p2);
@@ -285,6 +296,7 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
     st.u32[F_X * st.P + l] = x;
     st.u32[F_SLOT * st.P + l] = slot;
     if (SINK == SINK_QC && l < st.S) counts[l] += hits;
+    if (SINK == SINK_DIGEST && l < st.S) counts[l] = hits;
 }
 
 }  // namespace dev

@@ -58,6 +58,7 @@ bool valid_handle(const ci_states s);
 cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first_stream, cudaStream_t stream);
 cudaError_t launch_generate(const ci_states_s &h, uint64_t n, uint32_t *out, cudaStream_t stream);
 cudaError_t launch_fused_qc(const ci_states_s &h, uint64_t n, uint64_t *counts, cudaStream_t stream);
+cudaError_t launch_digest(const ci_states_s &h, uint64_t n, uint64_t *digest, cudaStream_t stream);
 
 int sm_count();
 

@@ -134,12 +134,12 @@ __global__ void __launch_bounds__(256) k_init_bbs(DevState st, uint64_t seed, ui
 template <class Src, int SINK>
 __global__ void __launch_bounds__(kBlockThreads) k_generate(DevState st, uint64_t n, uint32_t *out,
                                                             uint64_t *counts) {
-    __shared__ uint4 tiles[SINK == SINK_QC ? 1 : kWarpsPerBlock][256];
+    __shared__ uint4 tiles[SINK >= SINK_QC ? 1 : kWarpsPerBlock][256];
     const int w = threadIdx.x >> 5;
     const uint64_t ngroups = st.P / 32;
     const uint64_t gstride = (uint64_t)gridDim.x * kWarpsPerBlock;
     for (uint64_t g = (uint64_t)blockIdx.x * kWarpsPerBlock + w; g < ngroups; g += gstride)
-        warp_task<Src, SINK>(st, g, n, out, n, 0, counts, tiles[SINK == SINK_QC ? 0 : w]);
+        warp_task<Src, SINK>(st, g, n, out, n, 0, counts, tiles[SINK >= SINK_QC ? 0 : w]);
 }
 
 // ------------------------------------------------------------ launchers
@@ -207,6 +207,13 @@ cudaError_t launch_fused_qc(const ci_states_s &h, uint64_t n, uint64_t *counts, 
     if (h.variant == CI_VAR_BBS) return launch_gen<SrcBbs, SINK_QC>(st, n, nullptr, counts, stream);
     if (h.xl == CI_XL_XORSHIFT32) return launch_gen<SrcXorshift32, SINK_QC>(st, n, nullptr, counts, stream);
     return launch_gen<SrcXor128, SINK_QC>(st, n, nullptr, counts, stream);
+}
+
+cudaError_t launch_digest(const ci_states_s &h, uint64_t n, uint64_t *digest, cudaStream_t stream) {
+    const DevState st = h.view();
+    if (h.variant == CI_VAR_BBS) return launch_gen<SrcBbs, SINK_DIGEST>(st, n, nullptr, digest, stream);
+    if (h.xl == CI_XL_XORSHIFT32) return launch_gen<SrcXorshift32, SINK_DIGEST>(st, n, nullptr, digest, stream);
+    return launch_gen<SrcXor128, SINK_DIGEST>(st, n, nullptr, digest, stream);
 }
 
 }  // namespace ci

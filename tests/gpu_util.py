@@ -28,3 +28,17 @@ def u32(t):
 def oracle_gen(variant, xl, C, seed, comb_seed, S, comb=None, lane0=0, n_lanes=None):
     return oracle.Generator(VAR[variant], XL.get(xl, 0), C, seed, comb_seed, S, comb=comb, lane0=lane0,
                             n_lanes=n_lanes)
+
+
+DIGEST_MUL = 0xD1342543DE82EF95
+
+
+def digest_rows(outs: np.ndarray) -> np.ndarray:
+    """Horner digest D = sum_i o_i K^(n-1-i) mod 2^64 of each row of a uint32
+    [S, n] array: the definition the digest sink is documented to compute."""
+    d = np.zeros(outs.shape[0], dtype=np.uint64)
+    k = np.uint64(DIGEST_MUL)
+    with np.errstate(over="ignore"):
+        for i in range(outs.shape[1]):
+            d = d * k + outs[:, i].astype(np.uint64)
+    return d
