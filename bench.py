@@ -48,6 +48,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="main written-mode line only")
     ap.add_argument("--cpu-sample-streams", type=int, default=1 << 19)
+    ap.add_argument("--suite", choices=["main", "batched", "serving"], default="main",
+                    help="main: the 2^20 x 4096 line; batched: 10,000 uneven requests, one persistent launch vs "
+                         "one launch per request; serving: Poisson arrivals through the serving loop")
+    ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--profile", choices=["written", "fused", "bbs"], default=None,
                     help="small case for ncu: 2 warm-up launches then 1 launch of one kernel, no timing")
     return ap.parse_args()
@@ -264,6 +268,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
+    if args.suite == "batched":
+        bench_batched(args)
+        return
 
     import torch
 
@@ -469,6 +476,106 @@ def bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks,
     return {"value": value, "unit": "uint32/s", "ms_per_step": 1e3 * sec / steps, "steps": steps,
             "h2d_bytes_per_step": 512 + 64, "d2h_bytes_per_step": S_MAIN * L_MAIN * 4,
             "path": "ci_init_states (host params -> device) + 16 x ci_generate + D2H to pinned host"}
+
+
+def bench_batched(args):
+    """10,000 requests (stream counts log-uniform in [1, 2^16], lengths
+    log-uniform in [2^6, 2^20], 80 % xor128 / 20 % BBS, seed 4).  Their
+    6e12 outputs (about 25 TB) cannot be held in HBM, so both forms consume
+    them in-kernel through the per-stream digest sink: (a) ONE launch of the
+    persistent batched kernel over all requests (ci_batch_run, CUDA graph),
+    (b) one ci_generate_digest launch per request, back to back on one
+    stream.  Every digest of (a) must equal (b); a sample is checked against
+    the oracle."""
+    import numpy as np
+    import torch
+
+    from paper_1112_5239_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1112_5239_gb300 as ci
+    from paper_1112_5239_gb300.workloads import batched_requests
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    reqs = batched_requests(seed=4, count=args.requests)
+    t_init = time.perf_counter()
+    A, B, dA, dB = [], [], [], []
+    for r in reqs:
+        A.append(ci.States(r.n_streams, variant=r.variant, seed=r.seed))
+        B.append(ci.States(r.n_streams, variant=r.variant, seed=r.seed))
+        dA.append(torch.zeros(r.n_streams, dtype=torch.int64, device="cuda"))
+        dB.append(torch.zeros(r.n_streams, dtype=torch.int64, device="cuda"))
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t_init
+    # warm-up on a separate tiny batch (loads the kernels, instantiates the graph)
+    b = ci.Batch(len(reqs))
+    w = ci.States(64, seed=99)
+    wd = torch.zeros(64, dtype=torch.int64, device="cuda")
+    b.run([(w, 64, "digest", wd)])
+    w.generate_digest(64, digest=wd)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    b.run([(st, r.n_per_stream, "digest", d) for st, r, d in zip(A, reqs, dA)])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk_batched = clocks.stop()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t_host = time.perf_counter()
+    e1b = torch.cuda.Event(enable_timing=True)
+    e1b.record(stream)
+    for st, r, d in zip(B, reqs, dB):
+        st.generate_digest(r.n_per_stream, digest=d)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    t_host = time.perf_counter() - t_host
+    clk_single = clocks.stop()
+    sec_batched = e0.elapsed_time(e1) / 1e3
+    sec_single = e1b.elapsed_time(e2) / 1e3
+    identical = all(torch.equal(x, y) for x, y in zip(dA, dB))
+    n_out = sum(r.n_streams * r.n_per_stream for r in reqs)
+    n_bbs = sum(r.n_streams * r.n_per_stream for r in reqs if r.variant == "bbs")
+
+    # oracle on a seeded sample of the small requests
+    import oracle
+
+    rng = np.random.default_rng(4)
+    small = [i for i, r in enumerate(reqs) if r.n_streams * r.n_per_stream <= 1 << 20]
+    sample = sorted(rng.choice(small, size=min(16, len(small)), replace=False).tolist())
+    K = np.uint64(0xD1342543DE82EF95)
+    oracle_ok = True
+    for i in sample:
+        r = reqs[i]
+        g = oracle.Generator(1 if r.variant == "bbs" else 0, 0, 32, r.seed, 0, r.n_streams)
+        out = g.streams(r.n_per_stream)
+        d = np.zeros(out.shape[0], dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            for k in range(out.shape[1]):
+                d = d * K + out[:, k].astype(np.uint64)
+        oracle_ok = oracle_ok and np.array_equal(d, dA[i].cpu().numpy().view(np.uint64))
+    res = {
+        "metric": METRIC, "suite": "batched", "unit": "uint32/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "%d requests, seed 4: streams log-uniform [1, 2^16], length log-uniform "
+                               "[2^6, 2^20], 80%% xor128 / 20%% BBS; outputs consumed by the per-stream digest sink"
+                               % len(reqs),
+                   "outputs": n_out, "bbs_outputs": n_bbs, "work_units": sum(-(-r.n_streams // 32) for r in reqs)},
+        "batched": {"value": n_out / sec_batched, "seconds": sec_batched, "launches": 1, "clocks": clk_batched},
+        "per_request": {"value": n_out / sec_single, "seconds": sec_single, "launches": len(reqs),
+                        "host_seconds": t_host, "clocks": clk_single},
+        "batched_over_per_request": sec_single / sec_batched,
+        "identical_digests": bool(identical),
+        "oracle_sample": {"requests": sample, "equal": bool(oracle_ok)},
+        "init_seconds_both_forms": t_init,
+    }
+    res["value"] = res["batched"]["value"]
+    print(json.dumps(res), flush=True)
+    b.close()
 
 
 if __name__ == "__main__":
