@@ -215,6 +215,32 @@ ci_status ci_batch_run(ci_batch batch, const ci_batch_item *items, uint32_t n_it
 /* Waits for the batch's launches to finish and frees it.  NULL is a no-op. */
 ci_status ci_batch_destroy(ci_batch batch);
 
+/* Allocation-free batched launch.  The paper has no counterpart: this is a
+ * library convenience.  Some callers may not allocate device memory: code
+ * that runs while its host framework owns all device memory through its own
+ * allocator, real-time paths where an allocation's latency or failure is not
+ * acceptable, or code that must not touch the allocator (e.g. inside callbacks
+ * of another library).  With their states placed in their own memory
+ * (ci_init_states_at) they can run a batch through this call, which calls no
+ * cudaMalloc, cudaFree, cudaHostAlloc or any other allocating routine.
+ *
+ * Same computation and results as ci_batch_run on the same items, in one
+ * launch of the same persistent kernel on cuda_stream.  Its work queue (header
+ * with the claim cursor, then up to CI_NOALLOC_MAX_ITEMS task entries, about
+ * 112 KiB) is a fixed device array inside the library: every GPU that loads
+ * the library holds it until the process exits.  Every call shares that
+ * array and overwrites it (the upload also resets the cursor the previous call
+ * left), so calls that overlap on the GPU race: order them, e.g. issue them on
+ * one stream.  The queue is copied from the library's own host memory, so the
+ * call waits until work already queued on cuda_stream has started the copy;
+ * host-side calls are serialised by a lock.  The first call on a device, made
+ * with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Errors: CI_E_INVAL (n_items > CI_NOALLOC_MAX_ITEMS, or the item checks of
+ * ci_batch_run), CI_E_STATE, CI_E_CUDA. */
+#define CI_NOALLOC_MAX_ITEMS 1024
+ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, void *cuda_stream);
+
 /* -------------------------------------------------- checkpoint / resume */
 
 /* Copies the whole device state (bytes == state_bytes) to host_buf /

@@ -181,6 +181,25 @@ class Batch:
             pass
 
 
+def batch_run_noalloc(items, stream=None) -> None:
+    """Runs items (as ``Batch.run`` takes them) through the allocation-free
+    entry point ``ci_batch_run_noalloc``: no device memory is allocated, the
+    work queue is a fixed array inside the library (at most
+    CI_NOALLOC_MAX_ITEMS items; calls that overlap on the GPU race)."""
+    arr = (_lib.ci_batch_item * max(1, len(items)))()
+    for i, (st, n, sink, t) in enumerate(items):
+        it = arr[i]
+        it.states = st.handle.value if isinstance(st, States) else st
+        it.n_per_stream = int(n)
+        it.sink = SINKS[sink] if isinstance(sink, str) else int(sink)
+        it.reserved = 0
+        written = it.sink == _lib.CI_SINK_WRITTEN
+        it.out_dev = t.data_ptr() if (written and t is not None) else None
+        it.out_capacity_u32 = t.numel() if (written and t is not None) else 0
+        it.aux_dev = t.data_ptr() if (not written and t is not None) else None
+    _lib.call("ci_batch_run_noalloc", ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
+
+
 def unpack_state(buf: np.ndarray, n_lanes: int, variant: int) -> dict:
     """Splits an exported state into its documented fields."""
     P = int(n_lanes)

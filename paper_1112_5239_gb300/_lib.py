@@ -15,6 +15,7 @@ CI_OK, CI_PENDING = 0, 1
 CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE = -1, -2, -3, -4, -5, -6
 CI_VAR_XOR, CI_VAR_BBS = 0, 1
 CI_SINK_WRITTEN, CI_SINK_QC, CI_SINK_DIGEST = 0, 1, 2
+CI_NOALLOC_MAX_ITEMS = 1024
 CI_XL_XOR128, CI_XL_XORSHIFT32 = 0, 1
 
 STATUS_NAMES = {0: "CI_OK", 1: "CI_PENDING", -1: "CI_E_INVAL", -2: "CI_E_NOMEM", -3: "CI_E_CUDA",
@@ -82,6 +83,7 @@ _SIGNATURES = {
     "ci_batch_create": [_U32, _VP],
     "ci_batch_run": [_VP, _VP, _U32, _VP],
     "ci_batch_destroy": [_VP],
+    "ci_batch_run_noalloc": [_VP, _U32, _VP],
     "ci_export_state": [_VP, _VP, _U64, _VP],
     "ci_import_state": [_VP, _VP, _U64, _VP],
 }

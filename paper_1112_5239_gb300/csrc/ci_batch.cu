@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <unordered_set>
 #include <vector>
@@ -283,3 +284,109 @@ ci_status ci_batch_destroy(ci_batch b) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------- allocation-free batched launch
+// For callers that must not allocate device memory (see ci_batch_run_noalloc
+// in ci_prng.h).  The work queue lives in a fixed, file-scope device array;
+// the host stages it in fixed, file-scope host arrays.
+
+namespace {
+
+constexpr uint32_t kNoAllocMaxItems = CI_NOALLOC_MAX_ITEMS;
+constexpr size_t kNoAllocBytes = sizeof(BatchHeader) + sizeof(BatchTask) * kNoAllocMaxItems;
+constexpr int kNoAllocMaxDevices = 64;
+
+// Per-device state of the set-up: the device address of the queue array and
+// the launch geometry, found on the first call made with that device current.
+struct NoAllocDevice {
+    void *queue;
+    BatchGeometry geo;
+};
+
+std::mutex g_noalloc_mu;                                   // serialises host-side staging
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];           // zero-initialised
+alignas(64) unsigned char g_noalloc_host[kNoAllocBytes];    // header + tasks, staged here
+BatchTask g_noalloc_tasks[kNoAllocMaxItems];
+const void *g_noalloc_seen[kNoAllocMaxItems];
+
+}  // namespace
+
+// The queue: header (with the cursor) followed by up to kNoAllocMaxItems tasks.
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_queue[kNoAllocBytes];
+
+extern "C" ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, void *cuda_stream) {
+    if (n_items > kNoAllocMaxItems)
+        return fail(CI_E_INVAL, "ci_batch_run_noalloc takes at most CI_NOALLOC_MAX_ITEMS (1024) items");
+    if (n_items > 0 && !items) return fail(CI_E_INVAL, "items is NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CI_E_INVAL, "device ordinal above 63");
+
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.queue) {  // set-up, once per device, with that device current
+        void *addr = nullptr;
+        e = cudaGetSymbolAddress(&addr, g_noalloc_queue);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc queue");
+        d.geo = batch_geometry(8);
+        d.queue = addr;
+    }
+
+    uint32_t n_tasks = 0;
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const ci_batch_item &it = items[i];
+        if (!valid_handle(it.states)) return fail(CI_E_STATE, "an item's handle is not live");
+        for (uint32_t j = 0; j < i; ++j)
+            if (g_noalloc_seen[j] == it.states) return fail(CI_E_INVAL, "a handle may appear once per batch");
+        g_noalloc_seen[i] = it.states;
+        const ci_states_s &h = *it.states;
+        const uint64_t n = it.n_per_stream;
+        if (it.sink == CI_SINK_WRITTEN) {
+            if (n > 0 && !it.out_dev) return fail(CI_E_INVAL, "an item's out_dev is NULL");
+            if (n > 0 && (h.S > UINT64_MAX / n || it.out_capacity_u32 < h.S * n))
+                return fail(CI_E_INVAL, "an item's out_capacity_u32 < n_streams * n");
+        } else if (it.sink == CI_SINK_QC || it.sink == CI_SINK_DIGEST) {
+            if (n > 0 && !it.aux_dev) return fail(CI_E_INVAL, "an item's aux_dev is NULL");
+            if (it.sink == CI_SINK_QC && (n & 1ull)) return fail(CI_E_INVAL, "quarter-circle sink needs an even length");
+        } else {
+            return fail(CI_E_INVAL, "an item has an unknown sink");
+        }
+        if (n == 0) continue;
+        g_noalloc_tasks[n_tasks++] = make_task(h, n, it.sink, it.out_dev, it.aux_dev, n, 0);
+    }
+    if (n_tasks == 0) return CI_OK;
+
+    // Longest first (ties by position, so the order is deterministic); an
+    // in-place sort, no temporary buffer.
+    for (uint32_t i = 0; i < n_tasks; ++i) g_noalloc_tasks[i].prefix = i;
+    std::sort(g_noalloc_tasks, g_noalloc_tasks + n_tasks, [](const BatchTask &a, const BatchTask &b) {
+        const double ca = (double)a.n * kind_cost(a.kind), cb = (double)b.n * kind_cost(b.kind);
+        return ca != cb ? ca > cb : a.prefix < b.prefix;
+    });
+    uint64_t units = 0;
+    for (uint32_t i = 0; i < n_tasks; ++i) {
+        g_noalloc_tasks[i].prefix = units;
+        units += g_noalloc_tasks[i].ngroups;
+    }
+    BatchHeader hdr;
+    std::memset(&hdr, 0, sizeof hdr);
+    hdr.total_units = units;
+    hdr.cursor = 0;  // the upload clears the cursor the previous call left behind
+    hdr.n_tasks = n_tasks;
+    std::memcpy(g_noalloc_host, &hdr, sizeof hdr);
+    std::memcpy(g_noalloc_host + sizeof hdr, g_noalloc_tasks, sizeof(BatchTask) * n_tasks);
+    const size_t bytes = sizeof hdr + sizeof(BatchTask) * n_tasks;
+
+    cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    // From pageable memory: returns once the bytes are staged, so the host
+    // arrays may be reused by the next call.
+    e = cudaMemcpyAsync(d.queue, g_noalloc_host, bytes, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "no-alloc queue upload");
+    BatchHeader *dhdr = static_cast<BatchHeader *>(d.queue);
+    const BatchTask *dtasks = reinterpret_cast<const BatchTask *>(static_cast<unsigned char *>(d.queue) + sizeof hdr);
+    k_batched<8><<<d.geo.grid, d.geo.block, 0, cs>>>(dhdr, dtasks);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "no-alloc batched kernel launch");
+}
