@@ -241,6 +241,103 @@ ci_status ci_batch_destroy(ci_batch batch);
 #define CI_NOALLOC_MAX_ITEMS 1024
 ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, void *cuda_stream);
 
+/* ------------------------------------------------------------ serving */
+
+/* A serving loop with continuous batching.  A worker thread owns one CUDA
+ * stream.  Requests queue on submission; at every wave the worker:
+ *  - admits pending requests in arrival order while a slot and arena memory
+ *    for the request's output (and, for new streams, its state) are free;
+ *  - takes the next time slice of every admitted request (slice_xor or
+ *    slice_bbs outputs per stream) into one launch of the batched persistent
+ *    kernel (a CUDA graph replay);
+ *  - keeps up to two waves in flight, so requests that arrive while others
+ *    are on the GPU join the next wave.
+ * Slicing a stream over waves is exact: each result equals the one-call
+ * result whether the request runs alone or in any mix.  Stream state stays
+ * resident in the arena between requests; a request may continue the streams
+ * of an earlier request. */
+typedef struct ci_server_s *ci_server;
+
+typedef struct {
+    uint32_t max_slots;     /* requests admitted at once (0: 4096)               */
+    uint32_t max_inflight;  /* waves queued on the GPU at once, 1 or 2 (0: 2)    */
+    uint64_t slice_xor;     /* outputs per stream per wave, xor (0: 16384)       */
+    uint64_t slice_bbs;     /* outputs per stream per wave, BBS (0: 512)         */
+} ci_server_config;
+
+typedef struct {
+    ci_params params;          /* parameters of NEW streams (ignored when continuing) */
+    uint64_t n_streams;        /* new streams (ignored when continuing)               */
+    uint64_t n_per_stream;     /* outputs per stream, >= 1                             */
+    uint64_t continue_ticket;  /* 0: new streams; else continue the streams of that
+                                  earlier ticket (they must not be released)         */
+} ci_request;
+
+typedef struct {
+    ci_status status;         /* CI_OK once done; an error status if it failed      */
+    int32_t reserved;
+    uint32_t *out_dev;        /* [n_streams][n_per_stream] uint32 in the arena, valid
+                                 until ci_release                                    */
+    uint64_t n_streams;
+    uint64_t n_per_stream;
+    ci_states states;         /* server-owned state of the streams (query/export)   */
+    uint64_t submit_ns;       /* CLOCK_MONOTONIC times: submission,                 */
+    uint64_t admit_ns;        /*   admission,                                        */
+    uint64_t done_ns;         /*   last wave observed complete                       */
+} ci_result;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, released;
+    uint64_t waves, units;            /* launches of the batched kernel, work units  */
+    uint64_t arena_bytes, arena_used, arena_peak;
+    uint64_t pending, active;
+} ci_server_stats;
+
+/* Creates a server over caller-owned device memory `arena_dev` of arena_bytes
+ * bytes (outputs and stream states are sub-allocated from it; it must outlive
+ * the server), on the current device.  cfg may be NULL (defaults).  Starts the
+ * worker thread.  Errors: CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA. */
+ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_server_config *cfg, ci_server *out);
+
+/* Queues a request (thread-safe) and returns its ticket (> 0).  Errors:
+ * CI_E_INVAL (bad parameters, sizes, unknown or released continue_ticket),
+ * CI_E_NOMEM (output plus state can never fit the arena), CI_E_STATE. */
+ci_status ci_submit(ci_server server, const ci_request *req, uint64_t *ticket);
+
+/* Non-blocking: CI_PENDING while queued or running; CI_OK and *result once
+ * done; the request's error status if it failed; CI_E_INVAL for an unknown
+ * ticket. */
+ci_status ci_poll(ci_server server, uint64_t ticket, ci_result *result);
+
+/* Blocks until the ticket is done (or timeout_ms passes: CI_E_TIMEOUT), then
+ * behaves as ci_poll. */
+ci_status ci_wait(ci_server server, uint64_t ticket, uint32_t timeout_ms, ci_result *result);
+
+/* Frees a done request's output bytes in the arena. */
+ci_status ci_release(ci_server server, uint64_t ticket);
+
+/* Frees the stream state created by `ticket` (a request that did not
+ * continue another); later continuations of it are rejected.  The state must
+ * not be in use by a queued or running request (CI_E_BUSY). */
+ci_status ci_release_states(ci_server server, uint64_t ticket);
+
+ci_status ci_server_get_stats(ci_server server, ci_server_stats *out);
+
+/* Load generator for measurement: submits reqs[i] when arrival_s[i] seconds
+ * have passed since the call started (continues[i] >= 0: continue the streams
+ * of request continues[i] of this list, which must come earlier), collects
+ * every result into results[i] (tickets[i] gets the ticket) and releases each
+ * output as soon as it is done unless hold[i] != 0 (hold may be NULL).
+ * Returns when all are done or failed.  Errors: as ci_submit. */
+ci_status ci_server_drive(ci_server server, const ci_request *reqs, const double *arrival_s,
+                          const int64_t *continues, const uint8_t *hold, uint32_t n, ci_result *results,
+                          uint64_t *tickets);
+
+/* Stops the server: requests already admitted finish, requests still queued
+ * fail with CI_E_STATE; then frees every stream state and the server.
+ * Outputs not yet released are abandoned (the arena is the caller's). */
+ci_status ci_server_destroy(ci_server server);
+
 /* -------------------------------------------------- checkpoint / resume */
 
 /* Copies the whole device state (bytes == state_bytes) to host_buf /

@@ -22,7 +22,7 @@ XORLIKES = {"xor128": _lib.CI_XL_XOR128, "xorshift32": _lib.CI_XL_XORSHIFT32}
 SINKS = {"written": _lib.CI_SINK_WRITTEN, "qc": _lib.CI_SINK_QC, "digest": _lib.CI_SINK_DIGEST}
 DIGEST_MUL = 0xD1342543DE82EF95
 
-__all__ = ["States", "Batch", "CIError", "make_params", "stream_ptr", "VARIANTS", "XORLIKES", "SINKS"]
+__all__ = ["States", "Batch", "Server", "CIError", "make_params", "stream_ptr", "VARIANTS", "XORLIKES", "SINKS"]
 
 
 def stream_ptr(stream=None) -> int:
@@ -171,6 +171,99 @@ class Batch:
     def close(self) -> None:
         if self.handle:
             _lib.call("ci_batch_destroy", self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self.handle and torch.cuda.is_available():
+                self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A ``ci_server``: continuous-batching serving loop over a device arena
+    (a torch uint8 tensor the server sub-allocates for outputs and states)."""
+
+    def __init__(self, arena_bytes: int, max_slots=0, max_inflight=0, slice_xor=0, slice_bbs=0):
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        cfg = _lib.ci_server_config(int(max_slots), int(max_inflight), int(slice_xor), int(slice_bbs))
+        self.handle = ctypes.c_void_p()
+        torch.cuda.synchronize()
+        _lib.call("ci_server_create", self.arena.data_ptr(), self.arena.numel(), ctypes.byref(cfg),
+                  ctypes.byref(self.handle))
+
+    @staticmethod
+    def request(n_per_stream, n_streams=1, variant="xor", xl="xor128", comb_size=32, seed=0, comb_seed=0,
+                continue_ticket=0):
+        r = _lib.ci_request()
+        p, _ = make_params(variant, xl, comb_size, seed, comb_seed)
+        r.params = p
+        r.n_streams = int(n_streams)
+        r.n_per_stream = int(n_per_stream)
+        r.continue_ticket = int(continue_ticket)
+        return r
+
+    def submit(self, n_per_stream, n_streams=1, **kw) -> int:
+        r = self.request(n_per_stream, n_streams, **kw)
+        t = ctypes.c_uint64()
+        _lib.call("ci_submit", self.handle, ctypes.byref(r), ctypes.byref(t))
+        return int(t.value)
+
+    def poll(self, ticket):
+        res = _lib.ci_result()
+        rc = _lib.lib().ci_poll(self.handle, int(ticket), ctypes.byref(res))
+        if rc < 0:
+            _lib.check(rc, "ci_poll")
+        return rc, res
+
+    def wait(self, ticket, timeout_ms=120000):
+        res = _lib.ci_result()
+        _lib.call("ci_wait", self.handle, int(ticket), int(timeout_ms), ctypes.byref(res))
+        return res
+
+    def output(self, res) -> torch.Tensor:
+        """int32 [n_streams, n_per_stream] view of a done request's output."""
+        off = int(res.out_dev) - self.arena.data_ptr()
+        n = int(res.n_streams) * int(res.n_per_stream)
+        return self.arena[off:off + 4 * n].view(torch.int32).view(int(res.n_streams), int(res.n_per_stream))
+
+    def release(self, ticket) -> None:
+        _lib.call("ci_release", self.handle, int(ticket))
+
+    def release_states(self, ticket) -> None:
+        _lib.call("ci_release_states", self.handle, int(ticket))
+
+    def stats(self) -> dict:
+        st = _lib.ci_server_stats()
+        _lib.call("ci_server_get_stats", self.handle, ctypes.byref(st))
+        return {f: int(getattr(st, f)) for f, _ in _lib.ci_server_stats._fields_}
+
+    def drive(self, requests, hold=None):
+        """Open-loop load: requests is a list of workloads.Request (arrival in
+        seconds, continues = index of an earlier request or -1).  Returns the
+        ci_result array and the tickets."""
+        n = len(requests)
+        reqs = (_lib.ci_request * max(1, n))()
+        arr = np.zeros(max(1, n), dtype=np.float64)
+        cont = np.full(max(1, n), -1, dtype=np.int64)
+        hd = np.zeros(max(1, n), dtype=np.uint8)
+        for i, q in enumerate(requests):
+            reqs[i] = self.request(q.n_per_stream, q.n_streams, variant=q.variant, seed=q.seed,
+                                   comb_seed=q.comb_seed)
+            arr[i] = q.arrival
+            cont[i] = q.continues
+            if hold is not None and hold[i]:
+                hd[i] = 1
+        results = (_lib.ci_result * max(1, n))()
+        tickets = np.zeros(max(1, n), dtype=np.uint64)
+        _lib.call("ci_server_drive", self.handle, ctypes.cast(reqs, ctypes.c_void_p), arr.ctypes.data,
+                  cont.ctypes.data, hd.ctypes.data, n, ctypes.cast(results, ctypes.c_void_p), tickets.ctypes.data)
+        return results, tickets
+
+    def close(self) -> None:
+        if self.handle:
+            _lib.call("ci_server_destroy", self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

@@ -61,6 +61,43 @@ class ci_batch_item(ctypes.Structure):
     ]
 
 
+class ci_server_config(ctypes.Structure):
+    _fields_ = [
+        ("max_slots", ctypes.c_uint32),
+        ("max_inflight", ctypes.c_uint32),
+        ("slice_xor", ctypes.c_uint64),
+        ("slice_bbs", ctypes.c_uint64),
+    ]
+
+
+class ci_request(ctypes.Structure):
+    _fields_ = [
+        ("params", ci_params),
+        ("n_streams", ctypes.c_uint64),
+        ("n_per_stream", ctypes.c_uint64),
+        ("continue_ticket", ctypes.c_uint64),
+    ]
+
+
+class ci_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("out_dev", ctypes.c_void_p),
+        ("n_streams", ctypes.c_uint64),
+        ("n_per_stream", ctypes.c_uint64),
+        ("states", ctypes.c_void_p),
+        ("submit_ns", ctypes.c_uint64),
+        ("admit_ns", ctypes.c_uint64),
+        ("done_ns", ctypes.c_uint64),
+    ]
+
+
+class ci_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "released", "waves", "units",
+                                                "arena_bytes", "arena_used", "arena_peak", "pending", "active")]
+
+
 class CIError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -84,6 +121,15 @@ _SIGNATURES = {
     "ci_batch_run": [_VP, _VP, _U32, _VP],
     "ci_batch_destroy": [_VP],
     "ci_batch_run_noalloc": [_VP, _U32, _VP],
+    "ci_server_create": [_VP, _U64, _VP, _VP],
+    "ci_submit": [_VP, _VP, _VP],
+    "ci_poll": [_VP, _U64, _VP],
+    "ci_wait": [_VP, _U64, _U32, _VP],
+    "ci_release": [_VP, _U64],
+    "ci_release_states": [_VP, _U64],
+    "ci_server_get_stats": [_VP, _VP],
+    "ci_server_drive": [_VP, _VP, _VP, _VP, _VP, _U32, _VP, _VP],
+    "ci_server_destroy": [_VP],
     "ci_export_state": [_VP, _VP, _U64, _VP],
     "ci_import_state": [_VP, _VP, _U64, _VP],
 }

@@ -123,10 +123,11 @@ BatchTask make_task(const ci_states_s &h, uint64_t n, int sink_abi, uint32_t *ou
     return t;
 }
 
-uint64_t pack_queue(BatchTask *tasks, uint32_t n_tasks, void *staging) {
-    std::stable_sort(tasks, tasks + n_tasks, [](const BatchTask &a, const BatchTask &b) {
-        return (double)a.n * kind_cost(a.kind) > (double)b.n * kind_cost(b.kind);
-    });
+uint64_t pack_queue(BatchTask *tasks, uint32_t n_tasks, void *staging, bool sort) {
+    if (sort)
+        std::stable_sort(tasks, tasks + n_tasks, [](const BatchTask &a, const BatchTask &b) {
+            return (double)a.n * kind_cost(a.kind) > (double)b.n * kind_cost(b.kind);
+        });
     uint64_t prefix = 0;
     for (uint32_t i = 0; i < n_tasks; ++i) {
         tasks[i].prefix = prefix;
@@ -201,6 +202,30 @@ static cudaError_t build_graph(ci_batch_s *b, int i) {
     return cudaGraphInstantiate(&b->exec[i], b->graph[i], 0);
 }
 
+namespace ci {
+
+ci_status batch_launch_tasks(ci_batch_s *b, BatchTask *tasks, uint32_t n_tasks, cudaStream_t cs, bool sort) {
+    if (n_tasks == 0) return CI_OK;
+    if (n_tasks > b->max_items) return fail(CI_E_INVAL, "more tasks than the batch's max_items");
+    const int s = b->slot;
+    b->slot ^= 1;
+    if (b->pending[s]) {
+        cudaError_t e = cudaEventSynchronize(b->done[s]);
+        if (e != cudaSuccess) return cuda_fail(e, "waiting for the previous batch");
+        b->pending[s] = false;
+    }
+    const uint64_t bytes = pack_queue(tasks, n_tasks, b->host[s], sort);
+    cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(b->exec[s], b->copy_node[s], b->dev[s], b->host[s], bytes,
+                                                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[s], cs);
+    if (e == cudaSuccess) e = cudaEventRecord(b->done[s], cs);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    b->pending[s] = true;
+    return CI_OK;
+}
+
+}  // namespace ci
+
 extern "C" {
 
 ci_status ci_batch_create(uint32_t max_items, ci_batch *out) {
@@ -257,23 +282,7 @@ ci_status ci_batch_run(ci_batch b, const ci_batch_item *items, uint32_t n_items,
         if (n == 0) continue;
         b->tasks.push_back(make_task(h, n, it.sink, it.out_dev, it.aux_dev, n, 0));
     }
-    if (b->tasks.empty()) return CI_OK;
-    const int s = b->slot;
-    b->slot ^= 1;
-    if (b->pending[s]) {
-        cudaError_t e = cudaEventSynchronize(b->done[s]);
-        if (e != cudaSuccess) return cuda_fail(e, "waiting for the previous batch");
-        b->pending[s] = false;
-    }
-    const uint64_t bytes = pack_queue(b->tasks.data(), (uint32_t)b->tasks.size(), b->host[s]);
-    cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
-    cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(b->exec[s], b->copy_node[s], b->dev[s], b->host[s], bytes,
-                                                       cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[s], cs);
-    if (e == cudaSuccess) e = cudaEventRecord(b->done[s], cs);
-    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
-    b->pending[s] = true;
-    return CI_OK;
+    return batch_launch_tasks(b, b->tasks.data(), (uint32_t)b->tasks.size(), static_cast<cudaStream_t>(cuda_stream));
 }
 
 ci_status ci_batch_destroy(ci_batch b) {

@@ -55,8 +55,16 @@ double kind_cost(uint32_t kind);
 BatchTask make_task(const ci_states_s &h, uint64_t n, int sink_abi, uint32_t *out, uint64_t *aux,
                     uint64_t ld, uint64_t col0);
 
+// Uploads `tasks` (sorted and packed here) to one of b's two queue slots and
+// replays that slot's graph on `stream`; waits first for the launch that
+// last used the slot.
+// With sort == false the tasks keep their order (serving waves, whose slices
+// are already bounded in length).
+ci_status batch_launch_tasks(ci_batch_s *b, BatchTask *tasks, uint32_t n_tasks, cudaStream_t stream,
+                             bool sort = true);
+
 // Sorts tasks longest-first, assigns prefixes, writes header + tasks to
 // `staging` (capacity checked by the caller) and returns the bytes to upload.
-uint64_t pack_queue(BatchTask *tasks, uint32_t n_tasks, void *staging);
+uint64_t pack_queue(BatchTask *tasks, uint32_t n_tasks, void *staging, bool sort = true);
 
 }  // namespace ci

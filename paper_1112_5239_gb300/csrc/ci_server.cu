@@ -1,0 +1,618 @@
+// ci_server.cu -- serving loop with continuous batching over the batched
+// persistent kernel (ci_server_* in ci_prng.h).
+//
+// One worker thread per server owns a CUDA stream and an internal ci_batch
+// (two CUDA-graph slots).  Each iteration it retires finished waves, admits
+// pending requests (arrival order; slots and arena bytes permitting), and
+// launches a wave holding the next time slice of every admitted request.
+// Time slices continue each stream's state exactly, so a request's outputs
+// do not depend on which other requests share its waves.
+#include <cuda_runtime.h>
+#include <time.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ci_batch.h"
+
+namespace ci {
+
+static uint64_t now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+static uint64_t round256(uint64_t b) { return (b + 255ull) & ~255ull; }
+
+// Sub-allocator over the caller's arena (offsets, 256-byte units): first fit
+// from the bottom for outputs, highest fit for stream states; neighbours
+// coalesce on release.
+class Arena {
+   public:
+    void init(uint64_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+        size_ = size;
+        used_ = peak_ = 0;
+    }
+    bool alloc(uint64_t bytes, uint64_t *off) {
+        bytes = round256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const uint64_t o = it->first, rem = it->second - bytes;
+            free_.erase(it);
+            if (rem) free_[o + bytes] = rem;
+            *off = o;
+            used_ += bytes;
+            peak_ = std::max(peak_, used_);
+            return true;
+        }
+        return false;
+    }
+    // Highest-addressed fit, taken from the top end of its free block.  Stream
+    // states (small, long-lived) come from the top of the arena and outputs
+    // from the bottom, so states do not fragment the space outputs need.
+    bool alloc_high(uint64_t bytes, uint64_t *off) {
+        bytes = round256(bytes);
+        for (auto it = free_.rbegin(); it != free_.rend(); ++it) {
+            if (it->second < bytes) continue;
+            it->second -= bytes;
+            *off = it->first + it->second;
+            if (it->second == 0) free_.erase(std::next(it).base());
+            used_ += bytes;
+            peak_ = std::max(peak_, used_);
+            return true;
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t bytes) {
+        bytes = round256(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    uint64_t size() const { return size_; }
+    uint64_t used() const { return used_; }
+    uint64_t peak() const { return peak_; }
+
+   private:
+    std::map<uint64_t, uint64_t> free_;
+    uint64_t size_ = 0, used_ = 0, peak_ = 0;
+};
+
+enum ReqState { RQ_PENDING = 0, RQ_ACTIVE = 1, RQ_DONE = 2, RQ_FAILED = 3, RQ_RELEASED = 4 };
+
+struct Req {
+    ci_request r;
+    uint8_t comb[16 * 32];
+    bool has_comb;
+    uint64_t S, L;
+    int variant;
+    int state;
+    ci_status status;
+    uint64_t root;  // ticket whose stream state this request advances
+    ci_states h;
+    uint64_t out_off, out_bytes;
+    uint32_t *out;
+    uint64_t enq;  // outputs per stream already queued on the GPU
+    uint64_t t_submit, t_admit, t_done;
+};
+
+struct StatesRec {
+    ci_states h;
+    uint64_t off, bytes;
+    bool busy;
+    bool released;
+};
+
+struct Wave {
+    cudaEvent_t ev;
+    std::vector<uint64_t> finishing;
+    std::vector<uint64_t> members;
+};
+
+}  // namespace ci
+
+using namespace ci;
+
+struct ci_server_s {
+    uint32_t magic;
+    int device;
+    char *arena_base;
+    Arena arena;
+    ci_server_config cfg;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::unordered_map<uint64_t, Req> reqs;
+    std::unordered_map<uint64_t, StatesRec> states;
+    std::deque<uint64_t> pending;
+    std::vector<uint64_t> active;
+    std::deque<uint64_t> completed;  // feed of ci_server_drive
+    bool feed_completed = false;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    cudaStream_t stream = nullptr;
+    ci_batch batch = nullptr;
+    std::deque<Wave> inflight;       // worker thread only
+    std::vector<cudaEvent_t> spare;  // worker thread only
+    ci_server_stats st;
+};
+
+static constexpr uint32_t kServerMagic = 0x5E2BE200u;
+
+namespace {
+
+bool valid_server(const ci_server s) { return s && s->magic == kServerMagic; }
+
+void finish_request(ci_server_s *s, uint64_t t, ci_status status) {  // under lock
+    Req &q = s->reqs[t];
+    const bool held_states = q.state == RQ_ACTIVE;  // only an admitted request holds its streams
+    q.state = status == CI_OK ? RQ_DONE : RQ_FAILED;
+    q.status = status;
+    q.t_done = now_ns();
+    auto sit = s->states.find(q.root);
+    if (held_states && sit != s->states.end()) sit->second.busy = false;
+    if (status != CI_OK && q.out) {
+        s->arena.release(q.out_off, q.out_bytes);
+        q.out = nullptr;
+    }
+    auto a = std::find(s->active.begin(), s->active.end(), t);
+    if (a != s->active.end()) {
+        *a = s->active.back();
+        s->active.pop_back();
+    }
+    if (status == CI_OK) s->st.completed++;
+    if (s->feed_completed) s->completed.push_back(t);
+}
+
+void retire_front(ci_server_s *s) {
+    Wave w = std::move(s->inflight.front());
+    s->inflight.pop_front();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (uint64_t t : w.finishing) finish_request(s, t, CI_OK);
+    }
+    s->cv_done.notify_all();
+    s->spare.push_back(w.ev);
+}
+
+// Admission in arrival order; a continuation whose streams are busy (or not
+// created yet) waits without blocking later requests; a request that does not
+// fit the arena stops admission (no overtaking by smaller requests).
+void admit(ci_server_s *s) {  // under lock
+    for (auto it = s->pending.begin(); it != s->pending.end();) {
+        if (s->active.size() >= s->cfg.max_slots) break;
+        const uint64_t t = *it;
+        Req &q = s->reqs[t];
+        const bool cont = q.r.continue_ticket != 0;
+        auto sit = s->states.find(q.root);
+        if (cont) {
+            if (sit == s->states.end()) {
+                const Req &root = s->reqs[q.root];
+                if (root.state == RQ_FAILED) {
+                    finish_request(s, t, CI_E_STATE);
+                    it = s->pending.erase(it);
+                    continue;
+                }
+                ++it;  // its streams are not created yet
+                continue;
+            }
+            if (sit->second.released) {
+                finish_request(s, t, CI_E_STATE);
+                it = s->pending.erase(it);
+                continue;
+            }
+            if (sit->second.busy) {
+                ++it;
+                continue;
+            }
+        }
+        uint64_t off_out = 0;
+        if (!s->arena.alloc(q.out_bytes, &off_out)) break;
+        if (!cont) {
+            uint64_t need = 0, off_st = 0;
+            ci_params p = q.r.params;
+            p.comb = q.has_comb ? q.comb : nullptr;
+            ci_state_bytes(&p, q.S, &need);
+            if (!s->arena.alloc_high(need, &off_st)) {
+                s->arena.release(off_out, q.out_bytes);
+                break;
+            }
+            ci_states h = nullptr;
+            const ci_status rc = ci_init_states_at(&p, q.S, s->arena_base + off_st, need, s->stream, &h);
+            if (rc != CI_OK) {
+                s->arena.release(off_out, q.out_bytes);
+                s->arena.release(off_st, need);
+                finish_request(s, t, rc);
+                it = s->pending.erase(it);
+                continue;
+            }
+            StatesRec r;
+            r.h = h;
+            r.off = off_st;
+            r.bytes = need;
+            r.busy = true;
+            r.released = false;
+            s->states[t] = r;
+            q.h = h;
+        } else {
+            sit->second.busy = true;
+            q.h = sit->second.h;
+        }
+        q.out_off = off_out;
+        q.out = reinterpret_cast<uint32_t *>(s->arena_base + off_out);
+        q.state = RQ_ACTIVE;
+        q.t_admit = now_ns();
+        q.enq = 0;
+        s->active.push_back(t);
+        s->st.admitted++;
+        it = s->pending.erase(it);
+    }
+}
+
+void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w) {  // under lock
+    for (uint64_t t : s->active) {
+        Req &q = s->reqs[t];
+        if (q.enq >= q.L) continue;
+        const uint64_t slice = q.variant == CI_VAR_BBS ? s->cfg.slice_bbs : s->cfg.slice_xor;
+        const uint64_t n = std::min(slice, q.L - q.enq);
+        tasks.push_back(make_task(*q.h, n, CI_SINK_WRITTEN, q.out, nullptr, q.L, q.enq));
+        s->st.units += q.h->P / 32;
+        q.enq += n;
+        w.members.push_back(t);
+        if (q.enq == q.L) w.finishing.push_back(t);
+    }
+}
+
+void worker_main(ci_server_s *s) {
+    cudaSetDevice(s->device);
+    std::vector<BatchTask> tasks;
+    for (;;) {
+        while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().ev) == cudaSuccess) retire_front(s);
+        tasks.clear();
+        Wave w;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->stop) {  // requests never admitted will not run
+                for (uint64_t t : s->pending) finish_request(s, t, CI_E_STATE);
+                if (!s->pending.empty()) s->cv_done.notify_all();
+                s->pending.clear();
+                if (s->active.empty() && s->inflight.empty()) break;
+            }
+            admit(s);
+            if (s->inflight.size() < s->cfg.max_inflight) build_wave(s, tasks, w);
+            if (tasks.empty()) {
+                if (s->inflight.empty())
+                    s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+                else
+                    s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+                continue;
+            }
+        }
+        ci_status rc = batch_launch_tasks(s->batch, tasks.data(), (uint32_t)tasks.size(), s->stream, false);
+        if (s->spare.empty()) {
+            cudaEvent_t ev;
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            s->spare.push_back(ev);
+        }
+        w.ev = s->spare.back();
+        s->spare.pop_back();
+        if (rc == CI_OK && cudaEventRecord(w.ev, s->stream) != cudaSuccess) rc = CI_E_CUDA;
+        if (rc != CI_OK) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (uint64_t t : w.members) finish_request(s, t, rc);
+            s->spare.push_back(w.ev);
+            s->cv_done.notify_all();
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->st.waves++;
+        }
+        s->inflight.push_back(std::move(w));
+    }
+}
+
+void fill_result(const Req &q, ci_result *r) {
+    std::memset(r, 0, sizeof *r);
+    r->status = q.state == RQ_DONE || q.state == RQ_RELEASED ? CI_OK : q.status;
+    r->out_dev = q.state == RQ_DONE ? q.out : nullptr;
+    r->n_streams = q.S;
+    r->n_per_stream = q.L;
+    r->states = q.h;
+    r->submit_ns = q.t_submit;
+    r->admit_ns = q.t_admit;
+    r->done_ns = q.t_done;
+}
+
+ci_status poll_locked(ci_server_s *s, uint64_t ticket, ci_result *result) {
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(CI_E_INVAL, "unknown ticket");
+    const Req &q = it->second;
+    if (result) fill_result(q, result);
+    if (q.state == RQ_PENDING || q.state == RQ_ACTIVE) return CI_PENDING;
+    if (q.state == RQ_FAILED) return q.status;
+    return CI_OK;
+}
+
+ci_status release_locked(ci_server_s *s, uint64_t ticket) {
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(CI_E_INVAL, "unknown ticket");
+    Req &q = it->second;
+    if (q.state != RQ_DONE) return fail(CI_E_BUSY, "request not done (or already released)");
+    s->arena.release(q.out_off, q.out_bytes);
+    q.out = nullptr;
+    q.state = RQ_RELEASED;
+    s->st.released++;
+    return CI_OK;
+}
+
+ci_status submit_locked(ci_server_s *s, const ci_request *req, uint64_t *ticket) {
+    Req q;
+    std::memset(&q, 0, sizeof q);
+    q.r = *req;
+    q.L = req->n_per_stream;
+    if (q.L == 0) return fail(CI_E_INVAL, "n_per_stream must be >= 1");
+    if (req->continue_ticket) {
+        auto it = s->reqs.find(req->continue_ticket);
+        if (it == s->reqs.end()) return fail(CI_E_INVAL, "unknown continue_ticket");
+        const Req &base = it->second;
+        if (base.state == RQ_FAILED) return fail(CI_E_STATE, "continue_ticket failed");
+        auto sit = s->states.find(base.root);
+        if (sit != s->states.end() && sit->second.released) return fail(CI_E_INVAL, "its streams were released");
+        q.root = base.root;
+        q.S = base.S;
+        q.variant = base.variant;
+    } else {
+        uint64_t need = 0;
+        ci_status rc = ci_state_bytes(&req->params, req->n_streams, &need);
+        if (rc != CI_OK) return rc;
+        q.S = req->n_streams;
+        q.variant = req->params.variant;
+        if (req->params.comb) {
+            const uint32_t n = (req->params.variant == CI_VAR_BBS ? 16u : 2u) * req->params.comb_size;
+            std::memcpy(q.comb, req->params.comb, n);
+            q.has_comb = true;
+        }
+    }
+    if (q.S > UINT64_MAX / 4 / q.L) return fail(CI_E_INVAL, "n_streams * n_per_stream overflows");
+    q.out_bytes = round256(q.S * q.L * 4ull);
+    uint64_t st_bytes = 0;
+    if (!req->continue_ticket) ci_state_bytes(&req->params, q.S, &st_bytes);
+    if (q.out_bytes + round256(st_bytes) > s->arena.size())
+        return fail(CI_E_NOMEM, "output plus state larger than the whole arena");
+    const uint64_t t = s->next_ticket++;
+    if (!req->continue_ticket) q.root = t;
+    q.state = RQ_PENDING;
+    q.status = CI_PENDING;
+    q.t_submit = now_ns();
+    q.h = nullptr;
+    s->reqs.emplace(t, q);
+    s->pending.push_back(t);
+    s->st.submitted++;
+    *ticket = t;
+    return CI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_server_config *cfg, ci_server *out) {
+    if (!out) return fail(CI_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!arena_dev || (reinterpret_cast<uintptr_t>(arena_dev) & 255u)) return fail(CI_E_INVAL, "arena_dev must be 256-byte aligned");
+    if (arena_bytes < 4096) return fail(CI_E_INVAL, "arena too small");
+    ci_server_s *s = new (std::nothrow) ci_server_s();
+    if (!s) return fail(CI_E_NOMEM, "host allocation failed");
+    s->magic = kServerMagic;
+    cudaGetDevice(&s->device);
+    s->arena_base = static_cast<char *>(arena_dev);
+    s->arena.init(arena_bytes & ~255ull);
+    ci_server_config c;
+    std::memset(&c, 0, sizeof c);
+    if (cfg) c = *cfg;
+    if (c.max_slots == 0) c.max_slots = 4096;
+    if (c.max_inflight == 0 || c.max_inflight > 2) c.max_inflight = 2;
+    if (c.slice_xor == 0) c.slice_xor = 16384;
+    if (c.slice_bbs == 0) c.slice_bbs = 512;
+    c.slice_xor = std::max<uint64_t>(4, c.slice_xor & ~3ull);  // keep 16-byte store alignment
+    c.slice_bbs = std::max<uint64_t>(4, c.slice_bbs & ~3ull);
+    s->cfg = c;
+    std::memset(&s->st, 0, sizeof s->st);
+    s->st.arena_bytes = s->arena.size();
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "server stream");
+    }
+    ci_status rc = ci_batch_create(c.max_slots, &s->batch);
+    if (rc != CI_OK) {
+        cudaStreamDestroy(s->stream);
+        delete s;
+        return rc;
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return CI_OK;
+}
+
+ci_status ci_submit(ci_server s, const ci_request *req, uint64_t *ticket) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    if (!req || !ticket) return fail(CI_E_INVAL, "req or ticket is NULL");
+    ci_status rc;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return fail(CI_E_STATE, "server is stopping");
+        rc = submit_locked(s, req, ticket);
+    }
+    if (rc == CI_OK) s->cv_work.notify_one();
+    return rc;
+}
+
+ci_status ci_poll(ci_server s, uint64_t ticket, ci_result *result) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    return poll_locked(s, ticket, result);
+}
+
+ci_status ci_wait(ci_server s, uint64_t ticket, uint32_t timeout_ms, ci_result *result) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(CI_E_INVAL, "unknown ticket");
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+        const int st = s->reqs[ticket].state;
+        return st != RQ_PENDING && st != RQ_ACTIVE;
+    });
+    if (!ok) return fail(CI_E_TIMEOUT, "request not done within timeout_ms");
+    return poll_locked(s, ticket, result);
+}
+
+ci_status ci_release(ci_server s, uint64_t ticket) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    return release_locked(s, ticket);
+}
+
+ci_status ci_release_states(ci_server s, uint64_t ticket) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->states.find(ticket);
+    if (it == s->states.end() || it->second.released) return fail(CI_E_INVAL, "ticket owns no live stream state");
+    if (it->second.busy) return fail(CI_E_BUSY, "stream state in use");
+    for (uint64_t t : s->pending)
+        if (s->reqs[t].root == ticket) return fail(CI_E_BUSY, "a queued request continues these streams");
+    s->arena.release(it->second.off, it->second.bytes);
+    ci_free_states(it->second.h);
+    it->second.h = nullptr;
+    it->second.released = true;
+    return CI_OK;
+}
+
+ci_status ci_server_get_stats(ci_server s, ci_server_stats *out) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    if (!out) return fail(CI_E_INVAL, "out is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->st;
+    out->arena_used = s->arena.used();
+    out->arena_peak = s->arena.peak();
+    out->pending = s->pending.size();
+    out->active = s->active.size();
+    return CI_OK;
+}
+
+ci_status ci_server_drive(ci_server s, const ci_request *reqs, const double *arrival_s, const int64_t *continues,
+                          const uint8_t *hold, uint32_t n, ci_result *results, uint64_t *tickets) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    if (n > 0 && (!reqs || !arrival_s || !results || !tickets)) return fail(CI_E_INVAL, "NULL argument");
+    std::unordered_map<uint64_t, uint32_t> index;
+    index.reserve(n * 2 + 1);
+    uint32_t done = 0;
+    ci_status first_err = CI_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->feed_completed = true;
+        s->completed.clear();
+    }
+    auto drain = [&](std::unique_lock<std::mutex> &lk) {
+        while (!s->completed.empty()) {
+            const uint64_t t = s->completed.front();
+            s->completed.pop_front();
+            auto ix = index.find(t);
+            if (ix == index.end()) continue;
+            Req &q = s->reqs[t];
+            fill_result(q, &results[ix->second]);
+            if (q.state == RQ_DONE && !(hold && hold[ix->second])) release_locked(s, t);
+            ++done;
+        }
+        (void)lk;
+    };
+    const uint64_t t0 = now_ns();
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint64_t due = t0 + (uint64_t)(arrival_s[i] * 1e9);
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(s->mu);
+                drain(lk);
+            }
+            if (now_ns() >= due) break;
+            std::this_thread::yield();
+        }
+        ci_request r = reqs[i];
+        if (continues && continues[i] >= 0) {
+            if ((uint64_t)continues[i] >= i) return fail(CI_E_INVAL, "continues[i] must refer to an earlier request");
+            r.continue_ticket = tickets[continues[i]];
+        }
+        uint64_t t = 0;
+        ci_status rc;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            rc = submit_locked(s, &r, &t);
+            if (rc == CI_OK) index[t] = i;
+        }
+        if (rc != CI_OK) {
+            tickets[i] = 0;
+            std::memset(&results[i], 0, sizeof results[i]);
+            results[i].status = rc;
+            if (first_err == CI_OK) first_err = rc;
+            ++done;
+            continue;
+        }
+        tickets[i] = t;
+        s->cv_work.notify_one();
+    }
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        while (done < n) {
+            drain(lk);
+            if (done < n) s->cv_done.wait_for(lk, std::chrono::milliseconds(1));
+        }
+        s->feed_completed = false;
+    }
+    return first_err;
+}
+
+ci_status ci_server_destroy(ci_server s) {
+    if (!s) return CI_OK;
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaStreamSynchronize(s->stream);
+    for (auto &kv : s->states)
+        if (!kv.second.released && kv.second.h) ci_free_states(kv.second.h);
+    for (cudaEvent_t ev : s->spare) cudaEventDestroy(ev);
+    ci_batch_destroy(s->batch);
+    cudaStreamDestroy(s->stream);
+    s->magic = 0;
+    delete s;
+    return CI_OK;
+}
+
+}  // extern "C"

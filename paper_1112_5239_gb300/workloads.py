@@ -83,10 +83,9 @@ def serving_requests(seed: int = 5, count: int = 2000, rate: float = 1000.0, con
         sd = int(rng.integers(0, 2**63))
         if cont:
             j = int(rng.integers(0, i))
+            while reqs[j].continues >= 0:  # continue the stream set a chain started with
+                j = reqs[j].continues
             base = reqs[j]
-            while base.continues >= 0:
-                base = reqs[base.continues]
-            j = reqs.index(base) if base is not reqs[j] else j
             S = base.n_streams
             reqs.append(Request(base.variant, S, max(1, -(-n // S)), base.seed, base.comb_seed, j, t))
         else:

@@ -1,0 +1,155 @@
+"""Serving loop (continuous batching): results are identical alone and in
+any mix, continuations equal the oracle's uninterrupted stream, admission
+respects the arena, and errors are reported."""
+import numpy as np
+import pytest
+
+from gpu_util import cuda_or_skip, oracle_gen, u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return cuda_or_skip()
+
+
+def _oracle_rows(variant, seed, S, L):
+    return oracle_gen(variant, "xor128", 32, seed, 0, S).streams(L)
+
+
+def test_single_request_equals_oracle(env):
+    torch, ci = env
+    srv = ci.Server(64 << 20)
+    t = srv.submit(300, 70, seed=5)
+    res = srv.wait(t)
+    assert res.status == 0
+    assert np.array_equal(u32(srv.output(res)), _oracle_rows("xor", 5, 70, 300))
+    srv.release(t)
+    srv.close()
+
+
+def test_alone_equals_in_mix(env):
+    """The same request, alone on a fresh server and submitted amid 60 others
+    of mixed variants, sizes and continuations, gives identical outputs
+    (tolerance 0), equal to the oracle's."""
+    torch, ci = env
+    spec = dict(n_per_stream=1000, n_streams=45, variant="bbs", seed=77)
+    alone = ci.Server(64 << 20, slice_bbs=64)
+    t = alone.submit(**spec)
+    out_alone = u32(alone.output(alone.wait(t)))
+    alone.close()
+    mix = ci.Server(4 << 30, slice_xor=128, slice_bbs=64)  # room for every output: none is released here
+    rng = np.random.default_rng(1)
+    tickets = []
+    mine = None
+    for i in range(61):
+        if i == 30:
+            mine = mix.submit(**spec)
+            continue
+        if tickets and rng.random() < 0.3:
+            base = tickets[int(rng.integers(0, len(tickets)))]
+            tickets.append(mix.submit(int(rng.integers(1, 700)), continue_ticket=base))
+        else:
+            v = "bbs" if rng.random() < 0.2 else "xor"
+            tickets.append(mix.submit(int(rng.integers(1, 3000)), int(rng.integers(1, 3000)), variant=v,
+                                      seed=int(rng.integers(0, 2**62))))
+    out_mix = u32(mix.output(mix.wait(mine)))
+    assert np.array_equal(out_alone, out_mix)
+    assert np.array_equal(out_mix, _oracle_rows("bbs", 77, 45, 1000))
+    for t in tickets:
+        assert mix.wait(t).status == 0
+    st = mix.stats()
+    assert st["completed"] == 61 and st["waves"] > 1
+    mix.close()
+
+
+def test_continuation_chain_equals_uninterrupted(env):
+    torch, ci = env
+    srv = ci.Server(64 << 20, slice_xor=100)
+    for variant in ["xor", "bbs"]:
+        t0 = srv.submit(123, 50, variant=variant, seed=9)
+        t1 = srv.submit(77, continue_ticket=t0)
+        t2 = srv.submit(200, continue_ticket=t1)  # continuing a continuation continues the same streams
+        outs = [u32(srv.output(srv.wait(t))) for t in (t0, t1, t2)]
+        ref = _oracle_rows(variant, 9, 50, 400)
+        assert np.array_equal(np.concatenate(outs, axis=1), ref)
+        for t in (t0, t1, t2):
+            srv.release(t)
+        srv.release_states(t0)
+        with pytest.raises(ci.CIError):
+            srv.submit(5, continue_ticket=t0)
+    srv.close()
+
+
+def test_admission_bounded_by_arena(env):
+    """A 3 MiB arena and 1 MiB outputs: requests wait for memory released by
+    earlier ones; every request completes and the peak stays in the arena."""
+    torch, ci = env
+    from paper_1112_5239_gb300.workloads import Request
+
+    srv = ci.Server(3 << 20, slice_xor=64)
+    reqs = [Request("xor", 256, 1024, 1000 + i, arrival=0.0) for i in range(12)]
+    hold = [i in (3, 11) for i in range(12)]
+    results, tickets = srv.drive(reqs, hold=hold)
+    assert all(r.status == 0 for r in results)
+    st = srv.stats()
+    assert st["completed"] == 12 and st["arena_peak"] <= st["arena_bytes"]
+    for i in (3, 11):
+        assert np.array_equal(u32(srv.output(results[i])), _oracle_rows("xor", 1000 + i, 256, 1024))
+    srv.close()
+
+
+def test_server_errors(env):
+    torch, ci = env
+    srv = ci.Server(1 << 20)
+    with pytest.raises(ci.CIError) as e:
+        srv.submit(1 << 20, 1024)  # 4 GiB of output can never fit
+    assert e.value.status == -2
+    with pytest.raises(ci.CIError):
+        srv.submit(10, continue_ticket=999)
+    with pytest.raises(ci.CIError):
+        srv.submit(0, 4)
+    with pytest.raises(ci.CIError):
+        srv.poll(12345)
+    t = srv.submit(10, 4, seed=1)
+    srv.wait(t)
+    srv.release(t)
+    with pytest.raises(ci.CIError) as e:
+        srv.release(t)
+    assert e.value.status == -4
+    srv.close()
+
+
+def test_poisson_mix_with_continuations_against_oracle(env):
+    """400 requests of the serving mix (lognormal sizes, 30 % continuations,
+    80/20 xor128/BBS) at 2000 requests/s through the load generator; a sample
+    of held outputs, continuations included, equals the oracle's
+    uninterrupted streams."""
+    torch, ci = env
+    from paper_1112_5239_gb300.workloads import serving_requests
+
+    reqs = serving_requests(seed=5, count=400, rate=2000.0, cap_log2=20)
+    root = []
+    for i, r in enumerate(reqs):
+        root.append(i if r.continues < 0 else root[r.continues])
+    offset, seen = [], {}
+    for i, r in enumerate(reqs):
+        offset.append(seen.get(root[i], 0))
+        seen[root[i]] = offset[-1] + r.n_per_stream
+    rng = np.random.default_rng(2)
+    small = [i for i, r in enumerate(reqs) if r.n_streams * (offset[i] + r.n_per_stream) <= 1 << 18]
+    cont_small = [i for i in small if reqs[i].continues >= 0]
+    sample = set(rng.choice(small, size=min(10, len(small)), replace=False).tolist())
+    sample |= set(cont_small[:6])
+    srv = ci.Server(8 << 30)
+    results, tickets = srv.drive(reqs, hold=[i in sample for i in range(len(reqs))])
+    assert all(r.status == 0 for r in results)
+    for i in sorted(sample):
+        r = reqs[i]
+        base = reqs[root[i]]
+        ref = _oracle_rows(base.variant, base.seed, base.n_streams, offset[i] + r.n_per_stream)[:, offset[i]:]
+        assert np.array_equal(u32(srv.output(results[i])), ref), i
+    lat = np.array([(x.done_ns - x.submit_ns) / 1e6 for x in results])
+    assert np.all(lat > 0)
+    srv.close()
