@@ -52,6 +52,7 @@ def parse_args():
                     help="main: the 2^20 x 4096 line; batched: 10,000 uneven requests, one persistent launch vs "
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
+    ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
     ap.add_argument("--profile", choices=["written", "fused", "bbs"], default=None,
                     help="small case for ncu: 2 warm-up launches then 1 launch of one kernel, no timing")
     return ap.parse_args()
@@ -270,6 +271,9 @@ def main():
         return
     if args.suite == "batched":
         bench_batched(args)
+        return
+    if args.suite == "serving":
+        bench_serving(args)
         return
 
     import torch
@@ -500,14 +504,14 @@ def bench_batched(args):
     stream = torch.cuda.current_stream()
     reqs = batched_requests(seed=4, count=args.requests)
     t_init = time.perf_counter()
-    A, B, dA, dB = [], [], [], []
-    for r in reqs:
-        A.append(ci.States(r.n_streams, variant=r.variant, seed=r.seed))
-        B.append(ci.States(r.n_streams, variant=r.variant, seed=r.seed))
-        dA.append(torch.zeros(r.n_streams, dtype=torch.int64, device="cuda"))
-        dB.append(torch.zeros(r.n_streams, dtype=torch.int64, device="cuda"))
+    specs = [dict(n_streams=r.n_streams, variant=r.variant, seed=r.seed) for r in reqs]
+    A = ci.States.many(specs)  # one seeding launch for all requests
     torch.cuda.synchronize()
     t_init = time.perf_counter() - t_init
+    B = [ci.States(r.n_streams, variant=r.variant, seed=r.seed) for r in reqs]  # one seeding launch each
+    dA = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+    dB = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+    torch.cuda.synchronize()
     # warm-up on a separate tiny batch (loads the kernels, instantiates the graph)
     b = ci.Batch(len(reqs))
     w = ci.States(64, seed=99)
@@ -571,11 +575,151 @@ def bench_batched(args):
         "batched_over_per_request": sec_single / sec_batched,
         "identical_digests": bool(identical),
         "oracle_sample": {"requests": sample, "equal": bool(oracle_ok)},
-        "init_seconds_both_forms": t_init,
+        "init_seconds_batched_seeding": t_init,
     }
     res["value"] = res["batched"]["value"]
     print(json.dumps(res), flush=True)
     b.close()
+
+
+def _serving_run(ci, reqs, arena_gib, hold=None, **cfg):
+    import numpy as np
+
+    srv = ci.Server(arena_gib << 30, **cfg)
+    t0 = time.perf_counter()
+    results, tickets = srv.drive(reqs, hold=hold)
+    wall = time.perf_counter() - t0
+    ok = all(r.status == 0 for r in results)
+    submit = np.array([r.submit_ns for r in results], dtype=np.float64)
+    done = np.array([r.done_ns for r in results], dtype=np.float64)
+    lat_ms = (done - submit) / 1e6
+    span = (done.max() - submit.min()) / 1e9
+    n_out = sum(r.n_streams * r.n_per_stream for r in reqs)
+    stats = srv.stats()
+    # steady phase: between the 10 % and 90 % completion marks (excludes the
+    # start-up ramp and the tail of the longest serial chains)
+    order = np.argsort(done)
+    k10, k90 = int(0.1 * len(reqs)), int(0.9 * len(reqs))
+    t10, t90 = done[order[k10]], done[order[k90]]
+    mid_out = sum(reqs[i].n_streams * reqs[i].n_per_stream for i in order[k10 + 1:k90 + 1])
+    steady_s = max((t90 - t10) / 1e9, 1e-9)
+    return srv, results, {"ok": ok, "requests": len(reqs), "outputs": n_out, "seconds": span, "wall_s": wall,
+                          "value": n_out / span, "req_per_s": len(reqs) / span,
+                          "steady_value": mid_out / steady_s, "steady_req_per_s": (k90 - k10) / steady_s,
+                          "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                          "mean_ms": float(lat_ms.mean()), "waves": stats["waves"], "units": stats["units"],
+                          "gpu_busy_s": stats["gpu_ns"] / 1e9, "max_wave_units": stats["max_wave_units"],
+                          "arena_peak_gib": stats["arena_peak"] / 2**30}
+
+
+def _plain_per_request(torch, ci, reqs):
+    handles = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        if r.continues < 0:
+            st = ci.States(r.n_streams, variant=r.variant, seed=r.seed, comb_seed=r.comb_seed, memory="torch")
+            handles[i] = st
+        else:
+            st = handles[r.continues]
+        st.generate(r.n_per_stream)  # output tensor from torch's caching allocator, dropped after use
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    n_out = sum(r.n_streams * r.n_per_stream for r in reqs)
+    for h in handles.values():
+        h.free()
+    return {"requests": len(reqs), "outputs": n_out, "seconds": sec, "value": n_out / sec,
+            "req_per_s": len(reqs) / sec, "launches": len(reqs) + sum(r.continues < 0 for r in reqs)}
+
+
+def bench_serving(args):
+    """Serving loop under Poisson arrivals (seed 5): sizes lognormal with
+    median 2^16 numbers, sigma 2, capped at 2^28; 30 % of requests continue an
+    earlier request's streams; 80 % xor128 / 20 % BBS; 64 GiB arena for
+    outputs and states.  First the saturation throughput (all requests at
+    t = 0), then open-loop sweeps at fractions of it with p50/p99 latency
+    (submission to completion), beside the plain form (one launch per request,
+    one at a time: the same server with one slot and whole-request slices).
+    A sample of held outputs, continuations included, is checked against the
+    oracle's uninterrupted streams."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_1112_5239_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1112_5239_gb300 as ci
+    from paper_1112_5239_gb300.workloads import serving_requests
+
+    torch.cuda.set_device(0)
+    n = args.serving_requests
+    base = serving_requests(seed=5, count=n, rate=1.0)  # arrival times rescaled per rate below
+
+    def at_rate(rate):
+        return [dataclasses.replace(r, arrival=r.arrival / rate) for r in base]
+
+    def at_zero():
+        return [dataclasses.replace(r, arrival=0.0) for r in base]
+
+    # warm-up (kernels, graphs, arena first touch)
+    srv, _, _ = _serving_run(ci, at_zero()[:500], 64)
+    srv.close()
+    clocks = ClockSampler(0)
+    clocks.start()
+    srv, _, sat = _serving_run(ci, at_zero(), 64)
+    clk = clocks.stop()
+    srv.close()
+    sweep = []
+    for frac in [0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.25]:
+        rate = frac * sat["steady_req_per_s"]
+        srv, _, r = _serving_run(ci, at_rate(rate), 64)
+        srv.close()
+        r.update({"fraction_of_saturation": frac, "offered_req_per_s": rate})
+        sweep.append(r)
+    # plain form: a loop issuing, per request, the state initialisation (new
+    # streams, state in torch memory) and ONE generation launch, asynchronously
+    # on one stream; timed from the first issue to the end of the last launch
+    plain = _plain_per_request(torch, ci, base)
+    srv, _, single = _serving_run(ci, at_zero(), 64, max_slots=1, max_inflight=2, slice_xor=1 << 40,
+                                  slice_bbs=1 << 40)
+    srv.close()
+
+    # oracle check of held outputs at half saturation
+    root, offset, seen = [], [], {}
+    for i, r in enumerate(base):
+        root.append(i if r.continues < 0 else root[r.continues])
+        offset.append(seen.get(root[i], 0))
+        seen[root[i]] = offset[-1] + r.n_per_stream
+    rng = np.random.default_rng(5)
+    small = [i for i, r in enumerate(base) if r.n_streams * (offset[i] + r.n_per_stream) <= 1 << 18]
+    conts = [i for i in small if base[i].continues >= 0]
+    sample = set(rng.choice(small, size=min(12, len(small)), replace=False).tolist()) | set(conts[:12])
+    srv, results, _ = _serving_run(ci, at_rate(0.5 * sat["steady_req_per_s"]), 64,
+                                   hold=[i in sample for i in range(len(base))])
+    import oracle
+
+    equal = True
+    for i in sorted(sample):
+        r, b0 = base[i], base[root[i]]
+        g = oracle.Generator(1 if b0.variant == "bbs" else 0, 0, 32, b0.seed, 0, b0.n_streams)
+        ref = g.streams(offset[i] + r.n_per_stream)[:, offset[i]:]
+        equal = equal and np.array_equal(srv.output(results[i]).cpu().numpy().view(np.uint32), ref)
+    srv.close()
+    res = {
+        "metric": METRIC, "suite": "serving", "unit": "uint32/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "%d requests per rate, seed 5: lognormal sizes (median 2^16, sigma 2, cap 2^28), "
+                               "S = 2^clamp(floor(log2 n) - 10, 0, 16), 30%% continuations, 80%% xor128 / 20%% BBS, "
+                               "64 GiB arena" % n},
+        "saturation": sat, "sweep": sweep, "plain_per_request": plain, "single_slot_server": single,
+        "served_over_plain": sat["steady_value"] / plain["value"],
+        "oracle_sample": {"requests": sorted(sample), "continuations": len(set(conts[:12])), "equal": bool(equal)},
+        "clocks": clk,
+    }
+    res["value"] = sat["steady_value"]
+    print(json.dumps(res), flush=True)
 
 
 if __name__ == "__main__":

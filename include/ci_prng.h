@@ -118,6 +118,15 @@ ci_status ci_init_states(const ci_params *params, uint64_t n_streams, void *cuda
 ci_status ci_init_states_at(const ci_params *params, uint64_t n_streams, void *state_dev,
                             uint64_t state_bytes, void *cuda_stream, ci_states *out);
 
+/* Creates n states at once (params[i], n_streams[i]; library-allocated as in
+ * ci_init_states) and seeds all of them in ONE kernel launch on cuda_stream:
+ * results equal n separate ci_init_states calls.  Worth it for many small
+ * states, whose separate seeding launches would run one after another.  On
+ * failure no handle is left allocated (out[i] = NULL).  Errors: CI_E_INVAL
+ * (with the failing item's index in ci_last_error), CI_E_NOMEM, CI_E_CUDA. */
+ci_status ci_init_states_many(const ci_params *params, const uint64_t *n_streams, uint32_t n, void *cuda_stream,
+                              ci_states *out);
+
 /* Frees the handle (and its device memory if the library allocated it).
  * The caller must ensure no enqueued call still uses it.  NULL is a no-op. */
 ci_status ci_free_states(ci_states states);
@@ -291,6 +300,10 @@ typedef struct {
     uint64_t waves, units;            /* launches of the batched kernel, work units  */
     uint64_t arena_bytes, arena_used, arena_peak;
     uint64_t pending, active;
+    uint64_t gpu_ns;                  /* summed GPU time of retired waves            */
+    uint64_t max_wave_units;          /* largest wave, in work units                 */
+    uint64_t host_admit_ns;           /* worker time admitting and seeding           */
+    uint64_t host_launch_ns;          /* worker time building and launching waves    */
 } ci_server_stats;
 
 /* Creates a server over caller-owned device memory `arena_dev` of arena_bytes

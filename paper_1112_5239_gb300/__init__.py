@@ -75,6 +75,36 @@ class States:
             _lib.call("ci_init_states", ctypes.byref(p), self.n_streams, stream_ptr(stream),
                       ctypes.byref(self.handle))
 
+    @classmethod
+    def many(cls, specs, stream=None) -> list:
+        """Creates and seeds many states in one launch (``ci_init_states_many``).
+        specs: dicts of the constructor's keyword arguments (n_streams, variant,
+        xl, comb_size, seed, comb_seed, comb, first_stream)."""
+        n = len(specs)
+        if n == 0:
+            return []
+        params = (ci_params * n)()
+        counts = np.zeros(n, dtype=np.uint64)
+        keep = []
+        for i, sp in enumerate(specs):
+            p, k = make_params(sp.get("variant", "xor"), sp.get("xl", "xor128"), sp.get("comb_size", 32),
+                               sp.get("seed", 0), sp.get("comb_seed", 0), sp.get("comb"), sp.get("first_stream", 0))
+            params[i] = p
+            keep.append(k)
+            counts[i] = int(sp["n_streams"])
+        handles = (ctypes.c_void_p * n)()
+        _lib.call("ci_init_states_many", ctypes.cast(params, ctypes.c_void_p), counts.ctypes.data, n,
+                  stream_ptr(stream), ctypes.cast(handles, ctypes.c_void_p))
+        out = []
+        for i in range(n):
+            obj = cls.__new__(cls)
+            obj.handle = ctypes.c_void_p(handles[i])
+            obj.n_streams = int(counts[i])
+            obj.variant = params[i].variant
+            obj._buf = None
+            out.append(obj)
+        return out
+
     # ------------------------------------------------------------ queries
     def query(self) -> ci_states_desc:
         d = ci_states_desc()

@@ -95,7 +95,8 @@ class ci_result(ctypes.Structure):
 
 class ci_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "released", "waves", "units",
-                                                "arena_bytes", "arena_used", "arena_peak", "pending", "active")]
+                                                "arena_bytes", "arena_used", "arena_peak", "pending", "active", "gpu_ns",
+                                                "max_wave_units", "host_admit_ns", "host_launch_ns")]
 
 
 class CIError(RuntimeError):
@@ -111,6 +112,7 @@ _SIGNATURES = {
     "ci_state_bytes": [_VP, _U64, _VP],
     "ci_init_states": [_VP, _U64, _VP, _VP],
     "ci_init_states_at": [_VP, _U64, _VP, _U64, _VP, _VP],
+    "ci_init_states_many": [_VP, _VP, _U32, _VP, _VP],
     "ci_free_states": [_VP],
     "ci_states_query": [_VP, _VP],
     "ci_generate": [_VP, _U64, _VP, _U64, _VP],

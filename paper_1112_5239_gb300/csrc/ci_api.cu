@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "ci_internal.h"
 
@@ -98,8 +99,7 @@ static ci_status check_params(const ci_params *p, uint64_t S) {
 
 static uint64_t lanes_for(uint64_t S) { return (S + 31ull) & ~31ull; }
 
-static ci_status make_handle(const ci_params *p, uint64_t S, void *dev, uint64_t bytes, bool owns,
-                             cudaStream_t stream, ci_states *out) {
+ci_status prepare_handle(const ci_params *p, uint64_t S, void *dev, uint64_t bytes, bool owns, ci_states *out) {
     ci_states_s *h = new (std::nothrow) ci_states_s();
     if (!h) return fail(CI_E_NOMEM, "host allocation failed");
     h->magic = kMagic;
@@ -118,8 +118,26 @@ static ci_status make_handle(const ci_params *p, uint64_t S, void *dev, uint64_t
     else
         derive_comb(p->variant, h->C, p->comb_seed, h->comb);
     build_table(p->variant, h->C, h->comb, h->table);
-    cudaError_t e = cudaMemcpyAsync(dev, h->table, kTableBytes, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = launch_init(*h, p->seed, p->first_stream, stream);
+    *out = h;
+    return CI_OK;
+}
+
+void fill_init_task(const ci_states_s &h, uint64_t seed, uint64_t first, uint64_t prefix, InitTask *t) {
+    t->st = h.view();
+    t->seed = seed;
+    t->first = first;
+    t->prefix = prefix;
+    t->variant = h.variant;
+    t->xl = h.xl;
+    std::memcpy(t->table, h.table, kTableBytes);
+}
+
+static ci_status make_handle(const ci_params *p, uint64_t S, void *dev, uint64_t bytes, bool owns,
+                             cudaStream_t stream, ci_states *out) {
+    ci_states h = nullptr;
+    ci_status st = prepare_handle(p, S, dev, bytes, owns, &h);
+    if (st != CI_OK) return st;
+    cudaError_t e = launch_init(*h, p->seed, p->first_stream, stream);  // also writes the partner table
     if (e != cudaSuccess) {
         h->magic = 0;
         delete h;
@@ -184,6 +202,54 @@ ci_status ci_init_states_at(const ci_params *params, uint64_t n_streams, void *s
         return fail(CI_E_INVAL, "state_dev must be a non-NULL 256-byte aligned device address");
     if (state_bytes < need) return fail(CI_E_INVAL, "state_bytes smaller than ci_state_bytes()");
     return make_handle(params, n_streams, state_dev, need, false, static_cast<cudaStream_t>(cuda_stream), out);
+}
+
+ci_status ci_init_states_many(const ci_params *params, const uint64_t *n_streams, uint32_t n, void *cuda_stream,
+                              ci_states *out) {
+    if (n == 0) return CI_OK;
+    if (!params || !n_streams || !out) return fail(CI_E_INVAL, "NULL argument");
+    for (uint32_t i = 0; i < n; ++i) out[i] = nullptr;
+    for (uint32_t i = 0; i < n; ++i) {
+        ci_status st = check_params(&params[i], n_streams[i]);
+        if (st != CI_OK) return fail(st, "item " + std::to_string(i) + ": " + g_err);
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<InitTask> tasks(n);
+    uint64_t lanes = 0;
+    ci_status rc = CI_OK;
+    for (uint32_t i = 0; i < n && rc == CI_OK; ++i) {
+        const uint64_t bytes = state_bytes_for(params[i].variant, lanes_for(n_streams[i]));
+        void *dev = nullptr;
+        cudaError_t e = cudaMalloc(&dev, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(e == cudaErrorMemoryAllocation ? CI_E_NOMEM : CI_E_CUDA, "cudaMalloc of a state");
+            break;
+        }
+        rc = prepare_handle(&params[i], n_streams[i], dev, bytes, true, &out[i]);
+        if (rc != CI_OK) {
+            cudaFree(dev);
+            break;
+        }
+        fill_init_task(*out[i], params[i].seed, params[i].first_stream, lanes, &tasks[i]);
+        lanes += out[i]->P;
+    }
+    InitTask *dtasks = nullptr;
+    if (rc == CI_OK) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&dtasks), sizeof(InitTask) * n, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dtasks, tasks.data(), sizeof(InitTask) * n, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = launch_init_batched(dtasks, n, lanes, cs);
+        if (dtasks) cudaFreeAsync(dtasks, cs);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batched state initialisation");
+    }
+    if (rc != CI_OK) {
+        for (uint32_t i = 0; i < n; ++i) {
+            if (out[i]) ci_free_states(out[i]);
+            out[i] = nullptr;
+        }
+    }
+    return rc;
 }
 
 ci_status ci_free_states(ci_states s) {

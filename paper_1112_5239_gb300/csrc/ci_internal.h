@@ -30,6 +30,15 @@ struct DevState {
 
 uint64_t state_bytes_for(int variant, uint64_t P);
 
+// One state to seed in a batched initialisation launch; lanes of all tasks
+// form one index space (task t owns [prefix, prefix + st.P)).
+struct InitTask {
+    DevState st;
+    uint64_t seed, first, prefix;
+    int32_t variant, xl;
+    uint32_t table[kTableBytes / 4];
+};
+
 }  // namespace ci
 
 struct ci_states_s {
@@ -59,6 +68,14 @@ cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first_stre
 cudaError_t launch_generate(const ci_states_s &h, uint64_t n, uint32_t *out, cudaStream_t stream);
 cudaError_t launch_fused_qc(const ci_states_s &h, uint64_t n, uint64_t *counts, cudaStream_t stream);
 cudaError_t launch_digest(const ci_states_s &h, uint64_t n, uint64_t *digest, cudaStream_t stream);
+cudaError_t launch_init_batched(const InitTask *dev_tasks, uint32_t n_tasks, uint64_t total_lanes,
+                                cudaStream_t stream);
+
+// Validates params and builds a handle over `dev` (which must hold
+// state_bytes_for(...) bytes) without seeding it; fill_init_task describes the
+// seeding for a batched launch.
+ci_status prepare_handle(const ci_params *p, uint64_t S, void *dev, uint64_t bytes, bool owns, ci_states *out);
+void fill_init_task(const ci_states_s &h, uint64_t seed, uint64_t first, uint64_t prefix, InitTask *t);
 
 int sm_count();
 

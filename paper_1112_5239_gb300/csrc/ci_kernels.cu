@@ -11,6 +11,7 @@
 // per-lane hit count.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "ci_device.cuh"
@@ -23,33 +24,49 @@ constexpr int kWarpsPerBlock = 8;
 constexpr int kBlockThreads = kWarpsPerBlock * 32;
 
 // ------------------------------------------------------------- seeding
-__global__ void __launch_bounds__(256) k_init_xor(DevState st, uint64_t seed, uint64_t first, int xl) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < st.P; l += stride) {
-        const uint64_t d0 = lane_draw(seed, first + l, 0);
-        const uint64_t d1 = lane_draw(seed, first + l, 1);
-        const uint64_t d2 = lane_draw(seed, first + l, 2);
-        uint32_t a, b = 0, c = 0, d = 0;
-        if (xl == CI_XL_XOR128) {
-            a = (uint32_t)d0;
-            b = (uint32_t)(d0 >> 32);
-            c = (uint32_t)d1;
-            d = (uint32_t)(d1 >> 32);
-            if ((a | b | c | d) == 0u) a = 1u;
-        } else {
-            a = (uint32_t)d0;
-            if (a == 0u) a = 1u;
-        }
-        st.u32[F_A * st.P + l] = a;
-        st.u32[F_B * st.P + l] = b;
-        st.u32[F_C * st.P + l] = c;
-        st.u32[F_D * st.P + l] = d;
-        st.u32[F_X * st.P + l] = (uint32_t)d2;
-        st.u32[F_SLOT * st.P + l] = (uint32_t)(d2 >> 32);
-        st.u32[F_SEL * st.P + l] = 0u;
-        st.u32[F_P * st.P + l] = 0u;
-        st.u32[F_Q * st.P + l] = 0u;
+// The partner table travels as a kernel parameter (no host-to-device copy
+// from pageable memory, which would synchronise the caller's stream).
+struct TableParam {
+    uint32_t w[kTableBytes / 4];
+};
+
+__device__ __forceinline__ void write_table(const DevState &st, const TableParam &tp) {
+    if (blockIdx.x == 0 && threadIdx.x < kTableBytes / 4)
+        reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(st.table))[threadIdx.x] = tp.w[threadIdx.x];
+}
+
+__device__ __forceinline__ void init_xor_lane(const DevState &st, uint64_t seed, uint64_t first, int xl,
+                                              uint64_t l) {
+    const uint64_t d0 = lane_draw(seed, first + l, 0);
+    const uint64_t d1 = lane_draw(seed, first + l, 1);
+    const uint64_t d2 = lane_draw(seed, first + l, 2);
+    uint32_t a, b = 0, c = 0, d = 0;
+    if (xl == CI_XL_XOR128) {
+        a = (uint32_t)d0;
+        b = (uint32_t)(d0 >> 32);
+        c = (uint32_t)d1;
+        d = (uint32_t)(d1 >> 32);
+        if ((a | b | c | d) == 0u) a = 1u;
+    } else {
+        a = (uint32_t)d0;
+        if (a == 0u) a = 1u;
     }
+    st.u32[F_A * st.P + l] = a;
+    st.u32[F_B * st.P + l] = b;
+    st.u32[F_C * st.P + l] = c;
+    st.u32[F_D * st.P + l] = d;
+    st.u32[F_X * st.P + l] = (uint32_t)d2;
+    st.u32[F_SLOT * st.P + l] = (uint32_t)(d2 >> 32);
+    st.u32[F_SEL * st.P + l] = 0u;
+    st.u32[F_P * st.P + l] = 0u;
+    st.u32[F_Q * st.P + l] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_init_xor(DevState st, TableParam tp, uint64_t seed, uint64_t first, int xl) {
+    write_table(st, tp);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < st.P; l += stride)
+        init_xor_lane(st, seed, first, xl, l);
 }
 
 __device__ __forceinline__ uint32_t mulmod32(uint32_t a, uint32_t b, uint32_t n) {
@@ -97,37 +114,75 @@ __device__ __forceinline__ uint32_t blum_candidate(uint64_t d) {
     return (uint32_t)((1ull << 30) + (d >> 34)) | 3u;
 }
 
-__global__ void __launch_bounds__(256) k_init_bbs(DevState st, uint64_t seed, uint64_t first) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < st.P; l += stride) {
-        uint64_t k = 0, d;
-        uint32_t p, q;
-        do {
-            d = lane_draw(seed, first + l, k++);
-            p = blum_candidate(d);
-        } while (!is_prime_mr(p));
-        do {
-            d = lane_draw(seed, first + l, k++);
-            q = blum_candidate(d);
-        } while (q == p || !is_prime_mr(q));
-        const uint64_t M = (uint64_t)p * q;
-        uint64_t v;
-        do {
-            d = lane_draw(seed, first + l, k++);
-            v = 2ull + d % (M - 2ull);
-        } while (v % p == 0ull || v % q == 0ull);  // gcd(v, p q) = 1
+__device__ void init_bbs_lane(const DevState &st, uint64_t seed, uint64_t first, uint64_t l) {
+    uint64_t k = 0, d;
+    uint32_t p, q;
+    do {
         d = lane_draw(seed, first + l, k++);
-        for (int f = F_A; f <= F_D; ++f) st.u32[f * st.P + l] = 0u;
-        st.u32[F_X * st.P + l] = (uint32_t)d;
-        st.u32[F_SLOT * st.P + l] = (uint32_t)(d >> 32);
-        st.u32[F_SEL * st.P + l] = (uint32_t)(v & 7u) | ((uint32_t)((v >> 3) & 7u) << 8);
-        st.u32[F_P * st.P + l] = p;
-        st.u32[F_Q * st.P + l] = q;
-        st.u64[G_Y * st.P + l] = v;
-        st.u64[G_M * st.P + l] = M;
-        st.u64[G_MP * st.P + l] = neg_inv64(M);
-        st.u64[G_R2 * st.P + l] = r2_mod(M);
+        p = blum_candidate(d);
+    } while (!is_prime_mr(p));
+    do {
+        d = lane_draw(seed, first + l, k++);
+        q = blum_candidate(d);
+    } while (q == p || !is_prime_mr(q));
+    const uint64_t M = (uint64_t)p * q;
+    uint64_t v;
+    do {
+        d = lane_draw(seed, first + l, k++);
+        v = 2ull + d % (M - 2ull);
+    } while (v % p == 0ull || v % q == 0ull);  // gcd(v, p q) = 1
+    d = lane_draw(seed, first + l, k++);
+    for (int f = F_A; f <= F_D; ++f) st.u32[f * st.P + l] = 0u;
+    st.u32[F_X * st.P + l] = (uint32_t)d;
+    st.u32[F_SLOT * st.P + l] = (uint32_t)(d >> 32);
+    st.u32[F_SEL * st.P + l] = (uint32_t)(v & 7u) | ((uint32_t)((v >> 3) & 7u) << 8);
+    st.u32[F_P * st.P + l] = p;
+    st.u32[F_Q * st.P + l] = q;
+    st.u64[G_Y * st.P + l] = v;
+    st.u64[G_M * st.P + l] = M;
+    st.u64[G_MP * st.P + l] = neg_inv64(M);
+    st.u64[G_R2 * st.P + l] = r2_mod(M);
+}
+
+__global__ void __launch_bounds__(256) k_init_bbs(DevState st, TableParam tp, uint64_t seed, uint64_t first) {
+    write_table(st, tp);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < st.P; l += stride)
+        init_bbs_lane(st, seed, first, l);
+}
+
+// Seeding of many states in one launch: thread g takes global lane g, finds
+// its task (largest lane prefix <= g) and seeds that lane; the first lanes of
+// each task also write its partner table.
+__global__ void __launch_bounds__(256) k_init_batched(const InitTask *tasks, uint32_t n_tasks, uint64_t total) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        uint32_t lo = 0, hi = n_tasks;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (tasks[mid].prefix <= g)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const InitTask &T = tasks[lo];
+        const uint64_t l = g - T.prefix;
+        for (uint64_t w = l; w < kTableBytes / 4; w += T.st.P)
+            reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(T.st.table))[w] = T.table[w];
+        if (T.variant == CI_VAR_BBS)
+            init_bbs_lane(T.st, T.seed, T.first, l);
+        else
+            init_xor_lane(T.st, T.seed, T.first, T.xl, l);
     }
+}
+
+cudaError_t launch_init_batched(const InitTask *dev_tasks, uint32_t n_tasks, uint64_t total_lanes,
+                                cudaStream_t stream) {
+    if (n_tasks == 0 || total_lanes == 0) return cudaSuccess;
+    const uint64_t blocks = (total_lanes + kBlockThreads - 1) / kBlockThreads;
+    const unsigned grid = (unsigned)(blocks < 65535 ? blocks : 65535);
+    k_init_batched<<<grid, kBlockThreads, 0, stream>>>(dev_tasks, n_tasks, total_lanes);
+    return cudaGetLastError();
 }
 
 // ----------------------------------------------------------- generation
@@ -182,10 +237,12 @@ cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first, cud
     const DevState st = h.view();
     const uint64_t blocks = (h.P + kBlockThreads - 1) / kBlockThreads;
     const unsigned grid = (unsigned)(blocks < 65535 ? blocks : 65535);
+    TableParam tp;
+    std::memcpy(tp.w, h.table, kTableBytes);
     if (h.variant == CI_VAR_BBS)
-        k_init_bbs<<<grid, kBlockThreads, 0, stream>>>(st, seed, first);
+        k_init_bbs<<<grid, kBlockThreads, 0, stream>>>(st, tp, seed, first);
     else
-        k_init_xor<<<grid, kBlockThreads, 0, stream>>>(st, seed, first, h.xl);
+        k_init_xor<<<grid, kBlockThreads, 0, stream>>>(st, tp, seed, first, h.xl);
     return cudaGetLastError();
 }
 

@@ -117,6 +117,17 @@ struct Req {
     uint32_t *out;
     uint64_t enq;  // outputs per stream already queued on the GPU
     uint64_t t_submit, t_admit, t_done;
+    uint64_t ticket;
+    size_t active_idx;  // position in ci_server_s::active while admitted
+    BatchTask tmpl;     // this request's queue entry; each wave sets col0 and n
+};
+
+// Requests of one stream set (a root request and its continuations) run one
+// at a time, in submission order: the one queued or running is `busy`; later
+// ones wait here and move to the ready queue when it finishes.
+struct Chain {
+    bool busy = false;
+    std::deque<uint64_t> waiting;
 };
 
 struct StatesRec {
@@ -128,6 +139,7 @@ struct StatesRec {
 
 struct Wave {
     cudaEvent_t ev;
+    cudaEvent_t start;
     std::vector<uint64_t> finishing;
     std::vector<uint64_t> members;
 };
@@ -146,17 +158,31 @@ struct ci_server_s {
     std::condition_variable cv_work, cv_done;
     std::unordered_map<uint64_t, Req> reqs;
     std::unordered_map<uint64_t, StatesRec> states;
-    std::deque<uint64_t> pending;
-    std::vector<uint64_t> active;
+    std::deque<uint64_t> pending;    // new stream sets, arrival order
+    std::deque<uint64_t> ready;      // continuations whose stream set is idle, arrival order
+    std::unordered_map<uint64_t, Chain> chains;
+    std::vector<Req *> active;       // element pointers of `reqs` stay valid across rehashing
+    bool admit_dirty = true;         // something changed that may let a pending request in
     std::deque<uint64_t> completed;  // feed of ci_server_drive
     bool feed_completed = false;
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // waves
+    cudaStream_t init_stream = nullptr;  // seeding of admitted stream sets, runs beside the waves
     ci_batch batch = nullptr;
     std::deque<Wave> inflight;       // worker thread only
     std::vector<cudaEvent_t> spare;  // worker thread only
+    // batched seeding of the stream sets admitted in one pass: two slots of
+    // pinned staging + device task arrays, reused alternately
+    InitTask *init_host[2] = {nullptr, nullptr};
+    InitTask *init_dev[2] = {nullptr, nullptr};
+    cudaEvent_t init_done[2] = {nullptr, nullptr};
+    bool init_pending[2] = {false, false};
+    int init_slot = 0;
+    uint32_t init_n = 0;
+    uint64_t init_lanes = 0;
+    std::vector<uint64_t> init_tickets;
     ci_server_stats st;
 };
 
@@ -178,11 +204,20 @@ void finish_request(ci_server_s *s, uint64_t t, ci_status status) {  // under lo
         s->arena.release(q.out_off, q.out_bytes);
         q.out = nullptr;
     }
-    auto a = std::find(s->active.begin(), s->active.end(), t);
-    if (a != s->active.end()) {
-        *a = s->active.back();
+    if (held_states) {
+        Req *last = s->active.back();
+        s->active[q.active_idx] = last;
+        last->active_idx = q.active_idx;
         s->active.pop_back();
     }
+    Chain &ch = s->chains[q.root];
+    if (!ch.waiting.empty()) {
+        s->ready.push_back(ch.waiting.front());
+        ch.waiting.pop_front();
+    } else {
+        ch.busy = false;
+    }
+    s->admit_dirty = true;
     if (status == CI_OK) s->st.completed++;
     if (s->feed_completed) s->completed.push_back(t);
 }
@@ -190,99 +225,132 @@ void finish_request(ci_server_s *s, uint64_t t, ci_status status) {  // under lo
 void retire_front(ci_server_s *s) {
     Wave w = std::move(s->inflight.front());
     s->inflight.pop_front();
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, w.start, w.ev);
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        s->st.gpu_ns += (uint64_t)(ms * 1e6);
         for (uint64_t t : w.finishing) finish_request(s, t, CI_OK);
     }
     s->cv_done.notify_all();
     s->spare.push_back(w.ev);
+    s->spare.push_back(w.start);
 }
 
-// Admission in arrival order; a continuation whose streams are busy (or not
-// created yet) waits without blocking later requests; a request that does not
-// fit the arena stops admission (no overtaking by smaller requests).
-void admit(ci_server_s *s) {  // under lock
-    for (auto it = s->pending.begin(); it != s->pending.end();) {
-        if (s->active.size() >= s->cfg.max_slots) break;
-        const uint64_t t = *it;
-        Req &q = s->reqs[t];
-        const bool cont = q.r.continue_ticket != 0;
+// Admission: first continuations whose stream set became idle, then new
+// stream sets in arrival order; a request that does not fit the arena stops
+// its queue (no overtaking by smaller requests).
+bool admit_one(ci_server_s *s, uint64_t t) {  // under lock; false: no room now
+    Req &q = s->reqs[t];
+    const bool cont = q.r.continue_ticket != 0;
+    StatesRec *sr = nullptr;
+    if (cont) {
         auto sit = s->states.find(q.root);
-        if (cont) {
-            if (sit == s->states.end()) {
-                const Req &root = s->reqs[q.root];
-                if (root.state == RQ_FAILED) {
-                    finish_request(s, t, CI_E_STATE);
-                    it = s->pending.erase(it);
-                    continue;
-                }
-                ++it;  // its streams are not created yet
-                continue;
-            }
-            if (sit->second.released) {
-                finish_request(s, t, CI_E_STATE);
-                it = s->pending.erase(it);
-                continue;
-            }
-            if (sit->second.busy) {
-                ++it;
-                continue;
-            }
+        if (sit == s->states.end() || sit->second.released) {  // its stream set failed or was released
+            finish_request(s, t, CI_E_STATE);
+            return true;
         }
-        uint64_t off_out = 0;
-        if (!s->arena.alloc(q.out_bytes, &off_out)) break;
-        if (!cont) {
-            uint64_t need = 0, off_st = 0;
-            ci_params p = q.r.params;
-            p.comb = q.has_comb ? q.comb : nullptr;
-            ci_state_bytes(&p, q.S, &need);
-            if (!s->arena.alloc_high(need, &off_st)) {
-                s->arena.release(off_out, q.out_bytes);
-                break;
-            }
-            ci_states h = nullptr;
-            const ci_status rc = ci_init_states_at(&p, q.S, s->arena_base + off_st, need, s->stream, &h);
-            if (rc != CI_OK) {
-                s->arena.release(off_out, q.out_bytes);
-                s->arena.release(off_st, need);
-                finish_request(s, t, rc);
-                it = s->pending.erase(it);
-                continue;
-            }
-            StatesRec r;
-            r.h = h;
-            r.off = off_st;
-            r.bytes = need;
-            r.busy = true;
-            r.released = false;
-            s->states[t] = r;
-            q.h = h;
-        } else {
-            sit->second.busy = true;
-            q.h = sit->second.h;
-        }
-        q.out_off = off_out;
-        q.out = reinterpret_cast<uint32_t *>(s->arena_base + off_out);
-        q.state = RQ_ACTIVE;
-        q.t_admit = now_ns();
-        q.enq = 0;
-        s->active.push_back(t);
-        s->st.admitted++;
-        it = s->pending.erase(it);
+        sr = &sit->second;
     }
+    uint64_t off_out = 0;
+    if (!s->arena.alloc(q.out_bytes, &off_out)) return false;
+    if (!cont) {
+        uint64_t need = 0, off_st = 0;
+        ci_params p = q.r.params;
+        p.comb = q.has_comb ? q.comb : nullptr;
+        ci_state_bytes(&p, q.S, &need);
+        if (!s->arena.alloc_high(need, &off_st)) {
+            s->arena.release(off_out, q.out_bytes);
+            return false;
+        }
+        ci_states h = nullptr;
+        const ci_status rc = prepare_handle(&p, q.S, s->arena_base + off_st, need, false, &h);
+        if (rc != CI_OK) {
+            s->arena.release(off_out, q.out_bytes);
+            s->arena.release(off_st, need);
+            finish_request(s, t, rc);
+            return true;
+        }
+        fill_init_task(*h, p.seed, p.first_stream, s->init_lanes, &s->init_host[s->init_slot][s->init_n++]);
+        s->init_lanes += h->P;
+        s->init_tickets.push_back(t);
+        StatesRec r;
+        r.h = h;
+        r.off = off_st;
+        r.bytes = need;
+        r.busy = true;
+        r.released = false;
+        s->states[t] = r;
+        q.h = h;
+    } else {
+        sr->busy = true;
+        q.h = sr->h;
+    }
+    q.out_off = off_out;
+    q.out = reinterpret_cast<uint32_t *>(s->arena_base + off_out);
+    q.state = RQ_ACTIVE;
+    q.t_admit = now_ns();
+    q.enq = 0;
+    q.tmpl = make_task(*q.h, 1, CI_SINK_WRITTEN, q.out, nullptr, q.L, 0);
+    q.active_idx = s->active.size();
+    s->active.push_back(&q);
+    s->st.admitted++;
+    return true;
+}
+
+void admit(ci_server_s *s) {  // under lock
+    if (!s->admit_dirty) return;
+    const int slot = s->init_slot;
+    if (s->init_pending[slot]) {  // its staging may still be in an upload: try again later
+        if (cudaEventQuery(s->init_done[slot]) != cudaSuccess) return;
+        s->init_pending[slot] = false;
+    }
+    s->admit_dirty = false;
+    s->init_n = 0;
+    s->init_lanes = 0;
+    s->init_tickets.clear();
+    for (std::deque<uint64_t> *queue : {&s->ready, &s->pending}) {
+        while (!queue->empty() && s->active.size() < s->cfg.max_slots) {
+            if (!admit_one(s, queue->front())) break;
+            queue->pop_front();
+        }
+    }
+    if (s->init_n == 0) return;
+    // one upload and one launch seed every stream set admitted in this pass,
+    // on the seeding stream, concurrently with the waves in flight; the next
+    // wave (the first to use them) waits for it
+    cudaError_t e = cudaMemcpyAsync(s->init_dev[slot], s->init_host[slot], sizeof(InitTask) * s->init_n,
+                                    cudaMemcpyHostToDevice, s->init_stream);
+    if (e == cudaSuccess) e = launch_init_batched(s->init_dev[slot], s->init_n, s->init_lanes, s->init_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->init_done[slot], s->init_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->init_done[slot], 0);  // next wave waits
+    if (e != cudaSuccess) {  // the new stream sets of this pass were not seeded: fail them
+        cuda_fail(e, "batched state initialisation");
+        for (uint64_t t : s->init_tickets) {
+            auto sit = s->states.find(t);
+            if (sit != s->states.end()) sit->second.released = true;  // continuations of it fail too
+            finish_request(s, t, CI_E_CUDA);
+        }
+        return;
+    }
+    s->init_pending[slot] = true;
+    s->init_slot ^= 1;
 }
 
 void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w) {  // under lock
-    for (uint64_t t : s->active) {
-        Req &q = s->reqs[t];
+    for (Req *qp : s->active) {
+        Req &q = *qp;
         if (q.enq >= q.L) continue;
         const uint64_t slice = q.variant == CI_VAR_BBS ? s->cfg.slice_bbs : s->cfg.slice_xor;
         const uint64_t n = std::min(slice, q.L - q.enq);
-        tasks.push_back(make_task(*q.h, n, CI_SINK_WRITTEN, q.out, nullptr, q.L, q.enq));
-        s->st.units += q.h->P / 32;
+        tasks.push_back(q.tmpl);
+        BatchTask &tk = tasks.back();
+        tk.col0 = q.enq;
+        tk.n = n;
+        s->st.units += tk.ngroups;
         q.enq += n;
-        w.members.push_back(t);
-        if (q.enq == q.L) w.finishing.push_back(t);
+        w.members.push_back(q.ticket);
+        if (q.enq == q.L) w.finishing.push_back(q.ticket);
     }
 }
 
@@ -296,13 +364,23 @@ void worker_main(ci_server_s *s) {
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->stop) {  // requests never admitted will not run
-                for (uint64_t t : s->pending) finish_request(s, t, CI_E_STATE);
-                if (!s->pending.empty()) s->cv_done.notify_all();
-                s->pending.clear();
+                bool any = false;
+                while (!s->pending.empty() || !s->ready.empty()) {
+                    std::deque<uint64_t> &qq = s->ready.empty() ? s->pending : s->ready;
+                    const uint64_t t = qq.front();
+                    qq.pop_front();
+                    finish_request(s, t, CI_E_STATE);  // may move a waiting continuation to ready
+                    any = true;
+                }
+                if (any) s->cv_done.notify_all();
                 if (s->active.empty() && s->inflight.empty()) break;
             }
+            const uint64_t ta = now_ns();
             admit(s);
+            const uint64_t tb = now_ns();
+            s->st.host_admit_ns += tb - ta;
             if (s->inflight.size() < s->cfg.max_inflight) build_wave(s, tasks, w);
+            s->st.host_launch_ns += now_ns() - tb;
             if (tasks.empty()) {
                 if (s->inflight.empty())
                     s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
@@ -311,25 +389,35 @@ void worker_main(ci_server_s *s) {
                 continue;
             }
         }
-        ci_status rc = batch_launch_tasks(s->batch, tasks.data(), (uint32_t)tasks.size(), s->stream, false);
-        if (s->spare.empty()) {
+        while (s->spare.size() < 2) {
             cudaEvent_t ev;
-            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            cudaEventCreate(&ev);
             s->spare.push_back(ev);
         }
+        w.start = s->spare.back();
+        s->spare.pop_back();
         w.ev = s->spare.back();
         s->spare.pop_back();
+        cudaEventRecord(w.start, s->stream);
+        uint64_t wave_units = 0;
+        for (const BatchTask &tk : tasks) wave_units += tk.ngroups;
+        const uint64_t tl = now_ns();
+        ci_status rc = batch_launch_tasks(s->batch, tasks.data(), (uint32_t)tasks.size(), s->stream, false);
+        const uint64_t tl_end = now_ns();
         if (rc == CI_OK && cudaEventRecord(w.ev, s->stream) != cudaSuccess) rc = CI_E_CUDA;
         if (rc != CI_OK) {
             std::lock_guard<std::mutex> lk(s->mu);
             for (uint64_t t : w.members) finish_request(s, t, rc);
             s->spare.push_back(w.ev);
+            s->spare.push_back(w.start);
             s->cv_done.notify_all();
             continue;
         }
         {
             std::lock_guard<std::mutex> lk(s->mu);
+            s->st.host_launch_ns += tl_end - tl;
             s->st.waves++;
+            s->st.max_wave_units = std::max(s->st.max_wave_units, wave_units);
         }
         s->inflight.push_back(std::move(w));
     }
@@ -366,6 +454,7 @@ ci_status release_locked(ci_server_s *s, uint64_t ticket) {
     q.out = nullptr;
     q.state = RQ_RELEASED;
     s->st.released++;
+    s->admit_dirty = true;
     return CI_OK;
 }
 
@@ -409,8 +498,19 @@ ci_status submit_locked(ci_server_s *s, const ci_request *req, uint64_t *ticket)
     q.status = CI_PENDING;
     q.t_submit = now_ns();
     q.h = nullptr;
+    q.ticket = t;
     s->reqs.emplace(t, q);
-    s->pending.push_back(t);
+    Chain &ch = s->chains[q.root];
+    if (!req->continue_ticket) {
+        ch.busy = true;
+        s->pending.push_back(t);
+    } else if (!ch.busy) {
+        ch.busy = true;
+        s->ready.push_back(t);
+    } else {
+        ch.waiting.push_back(t);
+    }
+    s->admit_dirty = true;
     s->st.submitted++;
     *ticket = t;
     return CI_OK;
@@ -444,15 +544,37 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     std::memset(&s->st, 0, sizeof s->st);
     s->st.arena_bytes = s->arena.size();
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->init_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        if (s->stream) cudaStreamDestroy(s->stream);
         delete s;
-        return cuda_fail(e, "server stream");
+        return cuda_fail(e, "server streams");
     }
     ci_status rc = ci_batch_create(c.max_slots, &s->batch);
     if (rc != CI_OK) {
         cudaStreamDestroy(s->stream);
+        cudaStreamDestroy(s->init_stream);
         delete s;
         return rc;
+    }
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaHostAlloc(reinterpret_cast<void **>(&s->init_host[i]), sizeof(InitTask) * c.max_slots,
+                          cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s->init_dev[i]), sizeof(InitTask) * c.max_slots);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->init_done[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (int i = 0; i < 2; ++i) {
+            if (s->init_host[i]) cudaFreeHost(s->init_host[i]);
+            if (s->init_dev[i]) cudaFree(s->init_dev[i]);
+            if (s->init_done[i]) cudaEventDestroy(s->init_done[i]);
+        }
+        ci_batch_destroy(s->batch);
+        cudaStreamDestroy(s->stream);
+        cudaStreamDestroy(s->init_stream);
+        delete s;
+        return e == cudaErrorMemoryAllocation ? fail(CI_E_NOMEM, "server buffers") : cuda_fail(e, "server buffers");
     }
     s->worker = std::thread(worker_main, s);
     *out = s;
@@ -503,9 +625,11 @@ ci_status ci_release_states(ci_server s, uint64_t ticket) {
     auto it = s->states.find(ticket);
     if (it == s->states.end() || it->second.released) return fail(CI_E_INVAL, "ticket owns no live stream state");
     if (it->second.busy) return fail(CI_E_BUSY, "stream state in use");
-    for (uint64_t t : s->pending)
-        if (s->reqs[t].root == ticket) return fail(CI_E_BUSY, "a queued request continues these streams");
+    auto ch = s->chains.find(ticket);
+    if (ch != s->chains.end() && ch->second.busy)
+        return fail(CI_E_BUSY, "a queued request continues these streams");
     s->arena.release(it->second.off, it->second.bytes);
+    s->admit_dirty = true;
     ci_free_states(it->second.h);
     it->second.h = nullptr;
     it->second.released = true;
@@ -519,7 +643,9 @@ ci_status ci_server_get_stats(ci_server s, ci_server_stats *out) {
     *out = s->st;
     out->arena_used = s->arena.used();
     out->arena_peak = s->arena.peak();
-    out->pending = s->pending.size();
+    uint64_t waiting = 0;
+    for (const auto &kv : s->chains) waiting += kv.second.waiting.size();
+    out->pending = s->pending.size() + s->ready.size() + waiting;
     out->active = s->active.size();
     return CI_OK;
 }
@@ -604,11 +730,18 @@ ci_status ci_server_destroy(ci_server s) {
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    cudaStreamSynchronize(s->init_stream);
     cudaStreamSynchronize(s->stream);
     for (auto &kv : s->states)
         if (!kv.second.released && kv.second.h) ci_free_states(kv.second.h);
     for (cudaEvent_t ev : s->spare) cudaEventDestroy(ev);
+    for (int i = 0; i < 2; ++i) {
+        cudaFreeHost(s->init_host[i]);
+        cudaFree(s->init_dev[i]);
+        cudaEventDestroy(s->init_done[i]);
+    }
     ci_batch_destroy(s->batch);
+    cudaStreamDestroy(s->init_stream);
     cudaStreamDestroy(s->stream);
     s->magic = 0;
     delete s;

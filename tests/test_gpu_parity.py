@@ -175,3 +175,20 @@ def test_error_statuses(env):
     assert _lib.lib().ci_generate_bbs(st.handle, 2, out.data_ptr(), 100, None) == -6
     assert _lib.lib().ci_generate(bb.handle, 2, out.data_ptr(), 100, None) == -6
     assert _lib.lib().ci_generate(st.handle, 0, None, 0, None) == 0  # empty call is a no-op
+
+
+def test_init_states_many_equals_single_inits(env):
+    """ci_init_states_many seeds many states of mixed variants, sizes and
+    parameters in one launch; each equals the state ci_init_states makes."""
+    torch, ci = env
+    specs = [dict(n_streams=1 + 37 * i, variant="bbs" if i % 3 == 0 else "xor",
+                  xl="xorshift32" if i % 4 == 1 else "xor128", comb_size=[1, 4, 32][i % 3], seed=1000 + i,
+                  comb_seed=i, first_stream=32 * (i % 5)) for i in range(24)]
+    many = ci.States.many(specs)
+    for sp, m in zip(specs, many):
+        one = ci.States(**sp)
+        assert np.array_equal(m.export_state(), one.export_state()), sp
+    out = u32(many[5].generate(40))
+    sp = specs[5]
+    ref = oracle_gen(sp["variant"], sp["xl"], sp["comb_size"], sp["seed"], sp["comb_seed"], sp["n_streams"] + 32 * (5 % 5))
+    assert np.array_equal(out, ref.streams(40)[:sp["n_streams"]])
