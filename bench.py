@@ -293,6 +293,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     first = rank * S_MAIN
+    tuned = ci.autotune()  # launch shapes for this GPU (outside every timed region)
 
     def barrier_sync():
         torch.cuda.synchronize()
@@ -359,7 +360,8 @@ def main():
                                "per launch)",
                    "streams_per_gpu": S_MAIN, "n_per_stream": L_MAIN, "chunk": CHUNK,
                    "l2": "each launch writes 1 GiB (> 129 MB L2): no flush between steps",
-                   "parallelism": "dp%d (disjoint stream slices, no exchange)" % world},
+                   "parallelism": "dp%d (disjoint stream slices, no exchange)" % world,
+                   "autotuned": {k: tuned[k] for k in ("xor128/written", "xor128/qc", "bbs/written", "batch")}},
         "roofline": roofline, "gpu_launches": args.steps * nchunks, "clocks": clk,
     }
     del out
@@ -502,6 +504,7 @@ def bench_batched(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    tuned = ci.autotune()
     reqs = batched_requests(seed=4, count=args.requests)
     t_init = time.perf_counter()
     specs = [dict(n_streams=r.n_streams, variant=r.variant, seed=r.seed) for r in reqs]
@@ -576,6 +579,7 @@ def bench_batched(args):
         "identical_digests": bool(identical),
         "oracle_sample": {"requests": sample, "equal": bool(oracle_ok)},
         "init_seconds_batched_seeding": t_init,
+        "autotuned_batch": tuned["batch"],
     }
     res["value"] = res["batched"]["value"]
     print(json.dumps(res), flush=True)
@@ -654,6 +658,7 @@ def bench_serving(args):
     from paper_1112_5239_gb300.workloads import serving_requests
 
     torch.cuda.set_device(0)
+    tuned = ci.autotune()
     n = args.serving_requests
     base = serving_requests(seed=5, count=n, rate=1.0)  # arrival times rescaled per rate below
 
@@ -716,7 +721,7 @@ def bench_serving(args):
         "saturation": sat, "sweep": sweep, "plain_per_request": plain, "single_slot_server": single,
         "served_over_plain": sat["steady_value"] / plain["value"],
         "oracle_sample": {"requests": sorted(sample), "continuations": len(set(conts[:12])), "equal": bool(equal)},
-        "clocks": clk,
+        "clocks": clk, "autotuned_batch": tuned["batch"],
     }
     res["value"] = sat["steady_value"]
     print(json.dumps(res), flush=True)

@@ -370,6 +370,43 @@ ci_status ci_export_state(ci_states states, void *host_buf, uint64_t bytes, void
 ci_status ci_import_state(ci_states states, const void *host_buf, uint64_t bytes,
                           void *cuda_stream);
 
+/* ----------------------------------------------------------- autotuning */
+
+/* Launch shape of one generation kernel class.  Shapes change speed only,
+ * never results. */
+typedef struct {
+    uint32_t warps_per_block;  /* 4, 8 or 16 (block of 128, 256 or 512 threads)     */
+    uint32_t tile_depth;       /* written outputs: outputs per stream staged in
+                                  shared memory per flush, 32 or 64 (64 only for
+                                  16-byte-aligned xor-variant outputs)             */
+    uint32_t cache_policy;     /* 16-byte-aligned written outputs: 0 streaming
+                                  (evict-first) stores, 1 write-back stores        */
+    float ms;                  /* time of the tuning problem with this shape (0:
+                                  not measured)                                    */
+} ci_tune_choice;
+
+/* choice[source][sink]: source 0 xor128, 1 XORshift32, 2 BBS; sink 0 written
+ * 16-byte-aligned, 1 written unaligned, 2 quarter-circle, 3 digest. */
+typedef struct {
+    ci_tune_choice choice[3][4];
+    uint32_t batch_warps_per_block;  /* batched persistent kernel (read when a
+                                        ci_batch or ci_server is created)        */
+    float batch_ms;
+} ci_tune_table;
+
+/* Times every allowed shape of every class on representative problems (xor:
+ * 2^19 streams x 256 written / x 1024 consumed; BBS: 2^16 streams x 128; a
+ * 64-request mixed batch) on cuda_stream, installs the fastest for this
+ * process and returns the table.  Allocates and frees its own test states and
+ * buffers; takes well under a second.  flags must be 0.  Errors: CI_E_INVAL,
+ * CI_E_NOMEM, CI_E_CUDA. */
+ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out);
+
+/* Reads / installs the table (e.g. to cache tuning results across runs).
+ * ci_tune_set rejects shapes not allowed for their class (CI_E_INVAL). */
+ci_status ci_tune_get(ci_tune_table *out);
+ci_status ci_tune_set(const ci_tune_table *in);
+
 /* --------------------------------------------------------------- misc */
 
 /* Message for the last failing call on this thread ("" if none). */

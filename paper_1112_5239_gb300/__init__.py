@@ -304,6 +304,48 @@ class Server:
             pass
 
 
+SOURCES = ("xor128", "xorshift32", "bbs")
+SINK_CLASSES = ("written", "written_unaligned", "qc", "digest")
+
+
+def _table_to_dict(t) -> dict:
+    d = {}
+    for i, src in enumerate(SOURCES):
+        for k, snk in enumerate(SINK_CLASSES):
+            c = t.choice[i][k]
+            d["%s/%s" % (src, snk)] = {"warps_per_block": c.warps_per_block, "tile_depth": c.tile_depth,
+                                       "cache_policy": c.cache_policy, "ms": round(float(c.ms), 4)}
+    d["batch"] = {"warps_per_block": t.batch_warps_per_block, "ms": round(float(t.batch_ms), 4)}
+    return d
+
+
+def autotune(stream=None) -> dict:
+    """Times every allowed launch shape (``ci_autotune``), installs the
+    fastest for this process and returns the choices."""
+    t = _lib.ci_tune_table()
+    _lib.call("ci_autotune", 0, stream_ptr(stream), ctypes.byref(t))
+    return _table_to_dict(t)
+
+
+def tune_table() -> dict:
+    t = _lib.ci_tune_table()
+    _lib.call("ci_tune_get", ctypes.byref(t))
+    return _table_to_dict(t)
+
+
+def set_tune_table(d: dict) -> None:
+    """Installs choices in the form ``tune_table()`` returns."""
+    t = _lib.ci_tune_table()
+    for i, src in enumerate(SOURCES):
+        for k, snk in enumerate(SINK_CLASSES):
+            c = d["%s/%s" % (src, snk)]
+            t.choice[i][k].warps_per_block = c["warps_per_block"]
+            t.choice[i][k].tile_depth = c["tile_depth"]
+            t.choice[i][k].cache_policy = c["cache_policy"]
+    t.batch_warps_per_block = d["batch"]["warps_per_block"]
+    _lib.call("ci_tune_set", ctypes.byref(t))
+
+
 def batch_run_noalloc(items, stream=None) -> None:
     """Runs items (as ``Batch.run`` takes them) through the allocation-free
     entry point ``ci_batch_run_noalloc``: no device memory is allocated, the

@@ -99,6 +99,23 @@ class ci_server_stats(ctypes.Structure):
                                                 "max_wave_units", "host_admit_ns", "host_launch_ns")]
 
 
+class ci_tune_choice(ctypes.Structure):
+    _fields_ = [
+        ("warps_per_block", ctypes.c_uint32),
+        ("tile_depth", ctypes.c_uint32),
+        ("cache_policy", ctypes.c_uint32),
+        ("ms", ctypes.c_float),
+    ]
+
+
+class ci_tune_table(ctypes.Structure):
+    _fields_ = [
+        ("choice", (ci_tune_choice * 4) * 3),
+        ("batch_warps_per_block", ctypes.c_uint32),
+        ("batch_ms", ctypes.c_float),
+    ]
+
+
 class CIError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -132,6 +149,9 @@ _SIGNATURES = {
     "ci_server_get_stats": [_VP, _VP],
     "ci_server_drive": [_VP, _VP, _VP, _VP, _VP, _U32, _VP, _VP],
     "ci_server_destroy": [_VP],
+    "ci_autotune": [_U32, _VP, _VP],
+    "ci_tune_get": [_VP],
+    "ci_tune_set": [_VP],
     "ci_export_state": [_VP, _VP, _U64, _VP],
     "ci_import_state": [_VP, _VP, _U64, _VP],
 }

@@ -14,6 +14,7 @@
 
 #include "ci_batch.h"
 #include "ci_device.cuh"
+#include "ci_tune.h"
 
 namespace ci {
 
@@ -237,7 +238,7 @@ ci_status ci_batch_create(uint32_t max_items, ci_batch *out) {
     b->magic = kBatchMagic;
     b->max_items = max_items;
     b->bytes = sizeof(BatchHeader) + sizeof(BatchTask) * (uint64_t)max_items;
-    b->geo = batch_geometry(8);
+    b->geo = batch_geometry(tuned_batch_warps());
     b->tasks.reserve(max_items);
     for (int i = 0; i < 2; ++i) {
         cudaError_t e = cudaMalloc(&b->dev[i], b->bytes);

@@ -203,24 +203,55 @@ __device__ __forceinline__ uint32_t qc_hit(uint32_t o0, uint32_t o1) {
     return (a * a + b * b < (1ull << 48)) ? 1u : 0u;
 }
 
-// Index of word `col` of row `row` in a warp's 32x32 staging tile: 16-byte
+// Launch-shape choices of the written sinks, picked by the autotuner:
+// KT = outputs per stream staged per flush (tile depth: 32 or 64, i.e. 128- or
+// 256-byte row segments), CACHE = store policy (0: streaming st.global.cs,
+// evict-first; 1: default write-back st.global).
+template <int KT_, int CACHE_>
+struct TileCfg {
+    static constexpr int KT = KT_;
+    static constexpr int CH = KT_ / 4;  // 16-byte chunks per tile row
+    static constexpr int CACHE = CACHE_;
+};
+using TileDefault = TileCfg<32, 0>;
+
+// Index of word `col` of row `row` in a warp's 32 x KT staging tile: 16-byte
 // chunks XOR-swizzled by row so that both the per-lane 16-byte row writes and
-// the per-row 128-byte reads are free of bank conflicts.
+// the per-row reads are free of bank conflicts.
+template <int KT>
 __device__ __forceinline__ int tile_word(int row, int col) {
-    return row * 32 + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
+    return row * KT + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
+}
+
+template <int CACHE>
+__device__ __forceinline__ void store16(uint32_t *p, const uint4 &v) {
+    if (CACHE == 0)
+        __stcs(reinterpret_cast<uint4 *>(p), v);
+    else
+        *reinterpret_cast<uint4 *>(p) = v;
+}
+
+template <int CACHE>
+__device__ __forceinline__ void store4(uint32_t *p, uint32_t v) {
+    if (CACHE == 0)
+        __stcs(p, v);
+    else
+        *p = v;
 }
 
 // Runs n iterations of warp group g (lanes 32g .. 32g+31) of state `st`.
 // Written sinks store stream r's outputs at out[r * ld + col0 + i]
 // (r = 32g + lane < st.S only); SINK_QC adds the lane's quarter-circle hits
 // to counts[r]; SINK_DIGEST stores the Horner digest of the call's outputs,
-// D = sum_i x_i K^(n-1-i) mod 2^64, to counts[r].  `tile` is this warp's 4 KB
-// of shared memory (written sinks).  SINK_V4 needs out, ld and col0 aligned
-// to 4 words.
-template <class Src, int SINK>
+// D = sum_i x_i K^(n-1-i) mod 2^64, to counts[r].  `tile` is this warp's
+// 32 x TC::KT words of shared memory (written sinks).  SINK_V4 needs out, ld
+// and col0 aligned to 4 words.
+template <class Src, int SINK, class TC = TileDefault>
 __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64_t n, uint32_t *out,
                                           uint64_t ld, uint64_t col0, uint64_t *counts,
                                           uint4 *tile) {
+    constexpr int KT = (SINK == SINK_V4 || SINK == SINK_SCALAR) ? TC::KT : 32;
+    constexpr int CH = KT / 4;
     const int lane = threadIdx.x & 31;
     const uint64_t l = g * 32 + lane;
     Src src;
@@ -232,11 +263,11 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
     const int p1 = st.table[a1 * 32 + lane];
     const int p2 = st.table[a2 * 32 + lane];
     const uint64_t row0 = g * 32;
-    const uint64_t nfull = n & ~31ull;
+    const uint64_t nfull = n - n % KT;
     uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
     uint64_t hits = 0;
 
-    for (uint64_t i0 = 0; i0 < nfull; i0 += 32) {
+    for (uint64_t i0 = 0; i0 < nfull; i0 += KT) {
         if (SINK == SINK_DIGEST) {
 #pragma unroll(Src::kHeavy ? 1 : 32)
             for (int k = 0; k < 32; ++k) hits = hits * kDigestMul + ci_step(src, x, slot, p1, p2);
@@ -250,29 +281,33 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
             }
             hits += h;
         } else {
-#pragma unroll(Src::kHeavy ? 1 : 8)
-            for (int q = 0; q < 8; ++q) {
+#pragma unroll(Src::kHeavy ? 1 : CH)
+            for (int q = 0; q < CH; ++q) {
                 uint4 v;
                 v.x = ci_step(src, x, slot, p1, p2);
                 v.y = ci_step(src, x, slot, p1, p2);
                 v.z = ci_step(src, x, slot, p1, p2);
                 v.w = ci_step(src, x, slot, p1, p2);
-                tile[lane * 8 + (q ^ (lane & 7))] = v;
+                tile[lane * CH + (q ^ (lane & 7))] = v;
             }
             __syncwarp();
             if (SINK == SINK_V4) {
+                constexpr int RPI = 32 / CH;  // tile rows per warp-wide store
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int r = 4 * k + (lane >> 3), c = lane & 7;
-                    const uint4 v = tile[r * 8 + (c ^ (r & 7))];
-                    if (row0 + r < st.S)
-                        __stcs(reinterpret_cast<uint4 *>(out + (row0 + r) * ld + col0 + i0 + 4 * c), v);
+                for (int k = 0; k < CH; ++k) {
+                    const int r = RPI * k + lane / CH, c = lane % CH;
+                    const uint4 v = tile[r * CH + (c ^ (r & 7))];
+                    if (row0 + r < st.S) store16<TC::CACHE>(out + (row0 + r) * ld + col0 + i0 + 4 * c, v);
                 }
             } else {
 #pragma unroll 4
                 for (int r = 0; r < 32; ++r) {
-                    const uint32_t v = tw[tile_word(r, lane)];
-                    if (row0 + r < st.S) out[(row0 + r) * ld + col0 + i0 + lane] = v;
+#pragma unroll
+                    for (int h = 0; h < KT / 32; ++h) {
+                        const int c = 32 * h + lane;
+                        const uint32_t v = tw[tile_word<KT>(r, c)];
+                        if (row0 + r < st.S) store4<TC::CACHE>(out + (row0 + r) * ld + col0 + i0 + c, v);
+                    }
                 }
             }
             __syncwarp();
@@ -292,11 +327,11 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
             }
             hits += h;
         } else {
-            for (int k = 0; k < rem; ++k) tw[tile_word(lane, k)] = ci_step(src, x, slot, p1, p2);
+            for (int k = 0; k < rem; ++k) tw[tile_word<KT>(lane, k)] = ci_step(src, x, slot, p1, p2);
             __syncwarp();
             for (int r = 0; r < 32; ++r) {
-                if (lane < rem && row0 + r < st.S)
-                    out[(row0 + r) * ld + col0 + nfull + lane] = tw[tile_word(r, lane)];
+                for (int c = lane; c < rem; c += 32)
+                    if (row0 + r < st.S) out[(row0 + r) * ld + col0 + nfull + c] = tw[tile_word<KT>(r, c)];
             }
             __syncwarp();
         }

@@ -2,19 +2,16 @@
 // PRNG (Algorithms 4 and 5 of the paper with Eq. (Oplus)), and their host
 // launchers.
 //
-// Work decomposition: one warp per group of 32 lanes ("warp group"), lanes'
-// state in registers for the whole call, a persistent grid sized from the
-// occupancy calculator (a multiple of the SM count) whose warps stride over
-// the warp groups.  Written outputs are staged per warp in a 4 KB swizzled
-// shared-memory tile of 32 streams x 32 iterations and leave as full 128-byte
-// row segments (16-byte streaming stores); the fused form keeps only a
-// per-lane hit count.
+// The generation kernels themselves are in ci_gen.cuh (instantiated per
+// source in ci_gen_*.cu); this file holds seeding and the launch entry points,
+// which apply the autotuned launch shape.
 #include <cuda_runtime.h>
 
 #include <cstring>
 #include <mutex>
 
 #include "ci_device.cuh"
+#include "ci_tune.h"
 
 namespace ci {
 
@@ -185,18 +182,6 @@ cudaError_t launch_init_batched(const InitTask *dev_tasks, uint32_t n_tasks, uin
     return cudaGetLastError();
 }
 
-// ----------------------------------------------------------- generation
-template <class Src, int SINK>
-__global__ void __launch_bounds__(kBlockThreads) k_generate(DevState st, uint64_t n, uint32_t *out,
-                                                            uint64_t *counts) {
-    __shared__ uint4 tiles[SINK >= SINK_QC ? 1 : kWarpsPerBlock][256];
-    const int w = threadIdx.x >> 5;
-    const uint64_t ngroups = st.P / 32;
-    const uint64_t gstride = (uint64_t)gridDim.x * kWarpsPerBlock;
-    for (uint64_t g = (uint64_t)blockIdx.x * kWarpsPerBlock + w; g < ngroups; g += gstride)
-        warp_task<Src, SINK>(st, g, n, out, n, 0, counts, tiles[SINK >= SINK_QC ? 0 : w]);
-}
-
 // ------------------------------------------------------------ launchers
 int sm_count() {
     static int count = 0;
@@ -208,29 +193,6 @@ int sm_count() {
         if (count <= 0) count = 1;
     });
     return count;
-}
-
-// Persistent grid: SMs x resident blocks per SM, but no more blocks than
-// there are warp groups to cover.
-template <class K>
-static unsigned grid_for(K kernel, uint64_t ngroups) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlockThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    const uint64_t cap = (uint64_t)sm_count() * per_sm;
-    const uint64_t need = (ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    return (unsigned)(need < cap ? need : cap);
-}
-
-template <class Src, int SINK>
-static cudaError_t launch_gen(const DevState &st, uint64_t n, uint32_t *out, uint64_t *counts,
-                              cudaStream_t stream) {
-    auto kern = k_generate<Src, SINK>;
-    const unsigned grid = grid_for(kern, st.P / 32);
-    if (grid == 0) return cudaSuccess;
-    kern<<<grid, kBlockThreads, 0, stream>>>(st, n, out, counts);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first, cudaStream_t stream) {
@@ -246,31 +208,30 @@ cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_generate(const ci_states_s &h, uint64_t n, uint32_t *out, cudaStream_t stream) {
+cudaError_t launch_with(const ci_states_s &h, int sink, const TuneChoice &c, uint64_t n, uint32_t *out,
+                        uint64_t *counts, cudaStream_t stream) {
     const DevState st = h.view();
+    if (h.variant == CI_VAR_BBS) return gen_bbs(sink, c, st, n, out, counts, stream);
+    if (h.xl == CI_XL_XORSHIFT32) return gen_xs32(sink, c, st, n, out, counts, stream);
+    return gen_xor128(sink, c, st, n, out, counts, stream);
+}
+
+static int src_kind(const ci_states_s &h) {
+    return h.variant == CI_VAR_BBS ? SK_BBS : (h.xl == CI_XL_XORSHIFT32 ? SK_XS32 : SK_XOR128);
+}
+
+cudaError_t launch_generate(const ci_states_s &h, uint64_t n, uint32_t *out, cudaStream_t stream) {
     const bool v4 = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) && (n % 4 == 0);
-    if (h.variant == CI_VAR_BBS)
-        return v4 ? launch_gen<SrcBbs, SINK_V4>(st, n, out, nullptr, stream)
-                  : launch_gen<SrcBbs, SINK_SCALAR>(st, n, out, nullptr, stream);
-    if (h.xl == CI_XL_XORSHIFT32)
-        return v4 ? launch_gen<SrcXorshift32, SINK_V4>(st, n, out, nullptr, stream)
-                  : launch_gen<SrcXorshift32, SINK_SCALAR>(st, n, out, nullptr, stream);
-    return v4 ? launch_gen<SrcXor128, SINK_V4>(st, n, out, nullptr, stream)
-              : launch_gen<SrcXor128, SINK_SCALAR>(st, n, out, nullptr, stream);
+    const int sink = v4 ? SINK_V4 : SINK_SCALAR;
+    return launch_with(h, sink, tuned(src_kind(h), sink), n, out, nullptr, stream);
 }
 
 cudaError_t launch_fused_qc(const ci_states_s &h, uint64_t n, uint64_t *counts, cudaStream_t stream) {
-    const DevState st = h.view();
-    if (h.variant == CI_VAR_BBS) return launch_gen<SrcBbs, SINK_QC>(st, n, nullptr, counts, stream);
-    if (h.xl == CI_XL_XORSHIFT32) return launch_gen<SrcXorshift32, SINK_QC>(st, n, nullptr, counts, stream);
-    return launch_gen<SrcXor128, SINK_QC>(st, n, nullptr, counts, stream);
+    return launch_with(h, SINK_QC, tuned(src_kind(h), SINK_QC), n, nullptr, counts, stream);
 }
 
 cudaError_t launch_digest(const ci_states_s &h, uint64_t n, uint64_t *digest, cudaStream_t stream) {
-    const DevState st = h.view();
-    if (h.variant == CI_VAR_BBS) return launch_gen<SrcBbs, SINK_DIGEST>(st, n, nullptr, digest, stream);
-    if (h.xl == CI_XL_XORSHIFT32) return launch_gen<SrcXorshift32, SINK_DIGEST>(st, n, nullptr, digest, stream);
-    return launch_gen<SrcXor128, SINK_DIGEST>(st, n, nullptr, digest, stream);
+    return launch_with(h, SINK_DIGEST, tuned(src_kind(h), SINK_DIGEST), n, nullptr, digest, stream);
 }
 
 }  // namespace ci
