@@ -53,15 +53,17 @@ def parse_args():
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
-    ap.add_argument("--profile", choices=["written", "fused", "bbs"], default=None,
-                    help="small case for ncu: 2 warm-up launches then 1 launch of one kernel, no timing")
+    ap.add_argument("--profile", choices=["written", "fused", "bbs", "batched"], default=None,
+                    help="small case for ncu: autotune, 2 warm-up launches, then 1 launch of one kernel inside "
+                         "the NVTX range 'profile'; no timing")
     return ap.parse_args()
 
 
 def run_profile_case(kind: str) -> None:
     """Small case for profiler captures: 2^19 streams x 256 written (512 MiB,
-    larger than L2), 2^19 x 4096 fused, or 2^16 x 1024 BBS written (256 MiB);
-    two warm-up launches and one more of the same kernel."""
+    larger than L2), 2^19 x 4096 fused, 2^16 x 1024 BBS written (256 MiB), or
+    one batched launch of 300 uneven requests; two warm-up launches and one
+    more of the same kernel inside the NVTX range "profile"."""
     import torch
 
     from paper_1112_5239_gb300 import build as libbuild
@@ -70,21 +72,33 @@ def run_profile_case(kind: str) -> None:
     import paper_1112_5239_gb300 as ci
 
     torch.cuda.set_device(0)
+    ci.autotune()  # the launch shapes the benchmark uses
     if kind == "written":
         st = ci.States(1 << 19, seed=SEED_MAIN)
         out = torch.empty((1 << 19, CHUNK), dtype=torch.int32, device="cuda")
-        for _ in range(3):
-            st.generate(CHUNK, out=out)
+        run = lambda: st.generate(CHUNK, out=out)  # noqa: E731
     elif kind == "fused":
         st = ci.States(1 << 19, seed=SEED_MAIN)
         counts = torch.zeros(1 << 19, dtype=torch.int64, device="cuda")
-        for _ in range(3):
-            st.generate_fused_qc(L_MAIN, counts=counts)
-    else:
+        run = lambda: st.generate_fused_qc(L_MAIN, counts=counts)  # noqa: E731
+    elif kind == "bbs":
         st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
-        for _ in range(3):
-            st.generate(1024, out=out)
+        run = lambda: st.generate(1024, out=out)  # noqa: E731
+    else:  # batched: 300 uneven requests (lengths up to 2^12), digest sink, one launch
+        from paper_1112_5239_gb300.workloads import batched_requests
+
+        reqs = batched_requests(seed=4, count=300, max_len_log2=12)
+        sts = ci.States.many([dict(n_streams=r.n_streams, variant=r.variant, seed=r.seed) for r in reqs])
+        dg = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+        b = ci.Batch(len(reqs))
+        run = lambda: b.run([(x, r.n_per_stream, "digest", d) for x, r, d in zip(sts, reqs, dg)])  # noqa: E731
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profile")
+    run()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     print("profile case %s done" % kind)
 
@@ -329,10 +343,12 @@ def main():
     launch_evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(nchunks)] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     t0.record(stream)
     for k in range(args.steps):
         step(launch_evs[k])
     t1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier_sync()
     clk = clocks.stop()
     ms = max_over_ranks(t0.elapsed_time(t1))
@@ -390,6 +406,7 @@ def bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
         st.generate_fused_qc(L_MAIN, counts=counts)
     barrier_sync()
     evs = []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.fill_(1)  # evict the 24 MB state from L2 between steps
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -397,6 +414,7 @@ def bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
         st.generate_fused_qc(L_MAIN, counts=counts)
         b.record(stream)
         evs.append((a, b))
+    torch.cuda.nvtx.range_pop()
     barrier_sync()
     kms = [a.elapsed_time(b) for a, b in evs]
     ms = max_over_ranks(statistics.mean(kms))
@@ -422,12 +440,14 @@ def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world,
         st.generate(L_BBS, out=out)
     barrier_sync()
     evs = []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         st.generate(L_BBS, out=out)
         b.record(stream)
         evs.append((a, b))
+    torch.cuda.nvtx.range_pop()
     barrier_sync()
     ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
     value = world * S_BBS * L_BBS / (ms / 1e3)
@@ -479,9 +499,33 @@ def bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks,
     barrier_sync()
     sec = max_over_ranks(time.perf_counter() - t0)
     value = world * S_MAIN * L_MAIN * steps / sec
+    # the same end to end with the fused consumer: only the per-stream counts
+    # come back to the host
+    counts_h = torch.empty(S_MAIN, dtype=torch.int64, pin_memory=True)
+
+    def one_fused():
+        st = ci.States(S_MAIN, variant="xor", xl="xor128", comb_size=32, seed=SEED_MAIN, first_stream=first)
+        counts = torch.zeros(S_MAIN, dtype=torch.int64, device=dev)
+        st.generate_fused_qc(L_MAIN, counts=counts)
+        counts_h.copy_(counts, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        st.free()
+
+    one_fused()
+    barrier_sync()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_fused()
+    barrier_sync()
+    sec_f = max_over_ranks(time.perf_counter() - t0)
     return {"value": value, "unit": "uint32/s", "ms_per_step": 1e3 * sec / steps, "steps": steps,
             "h2d_bytes_per_step": 512 + 64, "d2h_bytes_per_step": S_MAIN * L_MAIN * 4,
-            "path": "ci_init_states (host params -> device) + 16 x ci_generate + D2H to pinned host"}
+            "path": "ci_init_states (host params -> device) + 16 x ci_generate + D2H to pinned host",
+            "bound": "device-to-host copy: 16 GiB per step at about 192 GB/s on this box",
+            "fused": {"value": world * S_MAIN * L_MAIN * steps / sec_f, "unit": "uint32/s",
+                      "ms_per_step": 1e3 * sec_f / steps, "h2d_bytes_per_step": 512 + 64,
+                      "d2h_bytes_per_step": S_MAIN * 8,
+                      "path": "ci_init_states + ci_generate_fused_qc + D2H of the per-stream counts"}}
 
 
 def bench_batched(args):
