@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ci_oracle.c")
 _LIB = os.path.join(_HERE, "libci_oracle.so")
 
-VAR_XOR, VAR_BBS = 0, 1
+VAR_XOR, VAR_BBS, VAR_BBS16 = 0, 1, 2
 XL_XOR128, XL_XORSHIFT32 = 0, 1
 
 # Layout of the C struct orc_lane (natural alignment).
@@ -44,6 +44,8 @@ LANE_DTYPE = np.dtype(
         ("y", "<u8"),
         ("sel1", "<u4"),
         ("sel2", "<u4"),
+        ("y16", "<u4", (8,)),
+        ("m16", "<u4", (8,)),
     ],
     align=True,
 )
@@ -84,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "orc_bbs_strategy_fed": (u32, [u32, vp, vp]),
             "orc_mix_ci_fed": (None, [u64, u64, vp, vp, vp, vp, vp, vp]),
             "orc_run": (i32, [i32, i32, u32, vp, vp, u64, u64, vp, vp]),
+            "orc_bbs16_strategy": (u32, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -136,11 +139,17 @@ def is_prime(n: int) -> bool:
 
 
 def comb_arrays(variant: int, C: int, comb_seed: int) -> np.ndarray:
-    n = 16 * C if variant == VAR_BBS else 2 * C
+    n = 16 * C if variant in (VAR_BBS, VAR_BBS16) else 2 * C
     out = np.zeros(n, dtype=np.uint8)
     if lib().orc_comb_arrays(variant, C, comb_seed, _ptr(out)) != 0:
         raise ValueError("bad combination size %r" % C)
     return out
+
+
+def bbs16_strategy(lane: np.ndarray) -> int:
+    """One Algorithm 5 strategy word from a variant-2 lane (advanced in place)."""
+    assert lane.dtype == LANE_DTYPE and lane.shape == (1,)
+    return int(lib().orc_bbs16_strategy(_ptr(lane)))
 
 
 def bbs_strategy_fed(w: int, feed) -> tuple[int, int]:

@@ -26,6 +26,9 @@
  *   Algorithm 5 (16 combination arrays, selection
  *     from the BBS state's low bits) ............... orc_run (BBS variant)
  *   Quarter-circle consumer of output pairs ......... orc_run (counts)
+ *   Algorithm 5 as printed (8 BBS generators per
+ *     thread, 16-bit moduli, 4 bits per squaring,
+ *     arrays chosen per call, rotation on store) ... orc_run (variant 2)
  *
  * Readings where the paper is silent or garbled (the same readings the CUDA
  * path takes; listed with reasons in the design notes):
@@ -39,6 +42,12 @@
  *   - BBS: one generator per lane, w = floor(log2(floor(log2 M))) bits per
  *     squaring, ceil(32 / w) chunks, then Algorithm 5's two shift steps;
  *     combination arrays chosen once from the seed's low bits.
+ *   - Algorithm 5 as printed (variant 2): eight generators per lane, each with
+ *     its own M = p q of Blum primes from [128, 256) (so x^2 < 2^32); 4 bits per
+ *     squaring as printed; per output BBS1..BBS8, then BBS3/BBS1 and BBS7/BBS2
+ *     for the two shift steps; the two arrays chosen when a call starts from
+ *     generators 1 and 2 (state & 7); at the end of a call generator k moves
+ *     to place k + 1 (state and modulus together).
  *
  * Parity pins (the tests that tie this file to the paper and to mathematics):
  *   Table 1 worked example; brute force of the single-cell and subset CI
@@ -177,7 +186,7 @@ static uint64_t orc_gcd(uint64_t a, uint64_t b)
 /* Per-lane state.                                                            */
 /* ------------------------------------------------------------------------- */
 
-enum { ORC_VAR_XOR = 0, ORC_VAR_BBS = 1 };
+enum { ORC_VAR_XOR = 0, ORC_VAR_BBS = 1, ORC_VAR_BBS16 = 2 };
 enum { ORC_XL_XOR128 = 0, ORC_XL_XORSHIFT32 = 1 };
 
 typedef struct {
@@ -189,6 +198,8 @@ typedef struct {
     uint64_t y;      /* BBS state, canonical residue in [0, M)               */
     uint32_t sel1;   /* BBS: first combination array index, in [0, 8)      */
     uint32_t sel2;   /* BBS: second combination array index is 8 + sel2    */
+    uint32_t y16[8]; /* variant 2: states of BBS1..BBS8                    */
+    uint32_t m16[8]; /* variant 2: their moduli                            */
 } orc_lane;
 
 uint32_t orc_lane_size(void) { return (uint32_t)sizeof(orc_lane); }
@@ -250,6 +261,36 @@ static void orc_init_bbs_lane(uint64_t seed, uint64_t lane, orc_lane *L)
     L->sel2 = (uint32_t)((v >> 3) & 7);
 }
 
+/* Variant 2 seeding: for each of the eight generators, in order, Blum primes
+ * p != q from candidates (128 + draw mod 128) | 3, kept if prime; a seed
+ * v = 2 + draw mod (M - 2) coprime to M; then one draw for x and the slot. */
+static void orc_init_bbs16_lane(uint64_t seed, uint64_t lane, orc_lane *L)
+{
+    memset(L, 0, sizeof *L);
+    uint64_t k = 0, d, v;
+    for (int g = 0; g < 8; ++g) {
+        uint32_t p, q;
+        do {
+            d = orc_lane_draw(seed, lane, k++);
+            p = (uint32_t)(128 + d % 128) | 3u;
+        } while (!orc_is_prime(p));
+        do {
+            d = orc_lane_draw(seed, lane, k++);
+            q = (uint32_t)(128 + d % 128) | 3u;
+        } while (!orc_is_prime(q) || q == p);
+        uint64_t M = (uint64_t)p * q;
+        do {
+            d = orc_lane_draw(seed, lane, k++);
+            v = 2 + d % (M - 2);
+        } while (orc_gcd(v, M) != 1);
+        L->y16[g] = (uint32_t)v;
+        L->m16[g] = (uint32_t)M;
+    }
+    d = orc_lane_draw(seed, lane, k++);
+    L->x = (uint32_t)d;
+    L->tprev = (uint32_t)(d >> 32);
+}
+
 /* Seed lanes [lane0, lane0 + nl) by their global index. */
 void orc_init_lanes(int variant, int xl, uint64_t seed, uint64_t lane0, uint64_t nl,
                     orc_lane *lanes)
@@ -257,6 +298,8 @@ void orc_init_lanes(int variant, int xl, uint64_t seed, uint64_t lane0, uint64_t
     for (uint64_t i = 0; i < nl; ++i) {
         if (variant == ORC_VAR_BBS)
             orc_init_bbs_lane(seed, lane0 + i, &lanes[i]);
+        else if (variant == ORC_VAR_BBS16)
+            orc_init_bbs16_lane(seed, lane0 + i, &lanes[i]);
         else
             orc_init_xor_lane(xl, seed, lane0 + i, &lanes[i]);
     }
@@ -288,7 +331,7 @@ int orc_comb_arrays(int variant, uint32_t C, uint64_t comb_seed, uint8_t *out)
     if (C < 1 || C > 32 || (C & (C - 1)))
         return -1;
     uint64_t ctr = 0;
-    if (variant == ORC_VAR_BBS) {
+    if (variant == ORC_VAR_BBS || variant == ORC_VAR_BBS16) {
         for (int a = 0; a < 16; ++a)
             orc_permutation(C, comb_seed, &ctr, out + (size_t)a * C);
         return 0;
@@ -347,6 +390,46 @@ static uint32_t orc_bbs_strategy_src(orc_bbs_src *s, uint32_t w)
         t |= (uint32_t)(orc_bbs_next(s) & array_shift[shift]);
     }
     return t;
+}
+
+/* Algorithm 5 as printed: BBSk advances generator k (x <- x^2 mod M_k) and
+ * returns it.  Eight 4-bit chunks from BBS1..BBS8, then
+ * shift = BBS3 & 3; t <<= shift; t |= BBS1 & array_shift[shift];
+ * shift = BBS7 & 3; t <<= shift; t |= BBS2 & array_shift[shift]. */
+static uint32_t orc_bbs16_next(orc_lane *L, int k)
+{
+    L->y16[k] = (uint32_t)(((uint64_t)L->y16[k] * L->y16[k]) % L->m16[k]);
+    return L->y16[k];
+}
+
+uint32_t orc_bbs16_strategy(orc_lane *L)
+{
+    static const uint32_t array_shift[4] = {0u, 1u, 3u, 7u};
+    uint32_t t = 0, shift;
+    for (int k = 0; k < 8; ++k) {
+        t <<= 4;
+        t |= orc_bbs16_next(L, k) & 15u;
+    }
+    shift = orc_bbs16_next(L, 2) & 3u;
+    t <<= shift;
+    t |= orc_bbs16_next(L, 0) & array_shift[shift];
+    shift = orc_bbs16_next(L, 6) & 3u;
+    t <<= shift;
+    t |= orc_bbs16_next(L, 1) & array_shift[shift];
+    return t;
+}
+
+/* End of a variant-2 call: generator k's state and modulus move to place
+ * k + 1, generator 8's to place 1. */
+static void orc_bbs16_rotate(orc_lane *L)
+{
+    uint32_t y = L->y16[7], m = L->m16[7];
+    for (int k = 7; k > 0; --k) {
+        L->y16[k] = L->y16[k - 1];
+        L->m16[k] = L->m16[k - 1];
+    }
+    L->y16[0] = y;
+    L->m16[0] = m;
 }
 
 /* Hand-fed form: assembles one strategy word from `feed` (needs
@@ -423,6 +506,10 @@ int orc_run(int variant, int xl, uint32_t C, const uint8_t *comb, orc_lane *lane
         if (variant == ORC_VAR_BBS) {
             c1 = comb + (size_t)lanes[l].sel1 * C;
             c2 = comb + (size_t)(8 + lanes[l].sel2) * C;
+        } else if (variant == ORC_VAR_BBS16) {
+            /* chosen when the call starts, from BBS1's and BBS2's states */
+            c1 = comb + (size_t)(lanes[l].y16[0] & 7u) * C;
+            c2 = comb + (size_t)(8 + (lanes[l].y16[1] & 7u)) * C;
         } else {
             c1 = comb;
             c2 = comb + C;
@@ -438,6 +525,8 @@ int orc_run(int variant, int xl, uint32_t C, const uint8_t *comb, orc_lane *lane
             if (variant == ORC_VAR_BBS) {
                 orc_bbs_src s = {&lanes[l], NULL, 0};
                 sw[l] = orc_bbs_strategy_src(&s, orc_bbs_w(lanes[l].M));
+            } else if (variant == ORC_VAR_BBS16) {
+                sw[l] = orc_bbs16_strategy(&lanes[l]);
             } else if (xl == ORC_XL_XOR128) {
                 sw[l] = orc_xor128_step(lanes[l].w);
             } else {
@@ -464,6 +553,8 @@ int orc_run(int variant, int xl, uint32_t C, const uint8_t *comb, orc_lane *lane
     for (uint64_t l = 0; l < nl; ++l) {
         lanes[l].x = xs[l];
         lanes[l].tprev = tp[l];
+        if (variant == ORC_VAR_BBS16 && L > 0)
+            orc_bbs16_rotate(&lanes[l]);
     }
     free(p1);
     free(p2);
