@@ -377,7 +377,7 @@ def main():
                    "streams_per_gpu": S_MAIN, "n_per_stream": L_MAIN, "chunk": CHUNK,
                    "l2": "each launch writes 1 GiB (> 129 MB L2): no flush between steps",
                    "parallelism": "dp%d (disjoint stream slices, no exchange)" % world,
-                   "autotuned": {k: tuned[k] for k in ("xor128/written", "xor128/qc", "bbs/written", "batch")}},
+                   "autotuned": {k: tuned[k] for k in ("xor128/written", "xor128/qc", "bbs/written", "bbs16/written", "batch")}},
         "roofline": roofline, "gpu_launches": args.steps * nchunks, "clocks": clk,
     }
     del out
@@ -386,6 +386,7 @@ def main():
     if not args.no_extras:
         result["fused"] = bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
         result["bbs"] = bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
+        result["bbs16"] = bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["e2e"] = bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
         if rank == 0 and world == 1:
             r, n, dt = oracle_sample(args.cpu_sample_streams)
@@ -457,6 +458,35 @@ def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world,
             "workload": "BBS-driven CI PRNG (Alg. 5, 62-bit Blum moduli, 11 Montgomery squarings per output,"
                         " C=32, seed 3): 2^16 streams x 16384, written (4 GiB per launch)",
             "modsq_per_s": 11 * value}
+
+
+def bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):
+    """Algorithm 5 as printed (eight 16-bit-modulus BBS per stream), 2^16
+    streams x 16384 outputs per call, written."""
+    st = ci.States(S_BBS, variant="bbs16", comb_size=32, seed=SEED_BBS, first_stream=rank * S_BBS)
+    out = torch.empty((S_BBS, L_BBS), dtype=torch.int32, device=dev)
+    steps = max(1, min(args.steps, 5))
+    for _ in range(min(args.warmup, 2)):
+        st.generate(L_BBS, out=out)
+    barrier_sync()
+    evs = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.generate(L_BBS, out=out)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.nvtx.range_pop()
+    barrier_sync()
+    ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
+    value = world * S_BBS * L_BBS / (ms / 1e3)
+    del out
+    st.free()
+    return {"value": value, "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
+            "workload": "Algorithm 5 as printed (8 BBS per stream, Blum primes in [128, 256), 4 bits per squaring, "
+                        "12 squarings per output, C=32, seed 3): 2^16 streams x 16384, written",
+            "modsq_per_s": 12 * value}
 
 
 def bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world):

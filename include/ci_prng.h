@@ -51,11 +51,17 @@ enum {
 };
 
 /* --------------------------------------------------------------- params */
-enum { CI_VAR_XOR = 0, CI_VAR_BBS = 1 };           /* Alg. 4 / Alg. 5       */
+enum { CI_VAR_XOR = 0, CI_VAR_BBS = 1, CI_VAR_BBS16 = 2 };  /* Alg. 4 / Alg. 5 / Alg. 5 as printed */
 enum { CI_XL_XOR128 = 0, CI_XL_XORSHIFT32 = 1 };   /* xor-like of Alg. 4    */
 
 typedef struct {
-    int32_t variant;      /* CI_VAR_XOR or CI_VAR_BBS                           */
+    int32_t variant;      /* CI_VAR_XOR, CI_VAR_BBS (one 62-bit-modulus BBS per
+                             stream, w = 5) or CI_VAR_BBS16 (Algorithm 5 as
+                             printed: eight BBS per stream with 16-bit moduli,
+                             4 bits per squaring, combination arrays chosen per
+                             call, generators rotated at the end of a call --
+                             so its outputs depend on how a stream's length is
+                             split into calls)                                */
     int32_t xl;           /* xor variant: CI_XL_XOR128 (the 32-bit xor128 the
                              paper uses for Alg. 4, Sec. 6.2) or
                              CI_XL_XORSHIFT32 (Alg. 2); ignored for BBS       */
@@ -147,7 +153,14 @@ ci_status ci_states_query(ci_states states, ci_states_desc *out);
 ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev,
                       uint64_t out_capacity_u32, void *cuda_stream);
 
-/* Algorithm 5 (Sec. 9.1): the same for a CI_VAR_BBS state.  Each strategy
+/* Algorithm 5 (Sec. 9.1): the same for a CI_VAR_BBS or CI_VAR_BBS16 state.
+ * CI_VAR_BBS16 follows the printed listing: BBS1..BBS8 give one 4-bit chunk
+ * each (x <- x^2 mod M_k, M_k = p q of Blum primes in [128, 256)), then
+ * shift = BBS3 & 3, t <<= shift, t |= BBS1 & {0,1,3,7}[shift] and the same
+ * with BBS7 and BBS2 (12 squarings per output); the arrays are comb[BBS1 & 7]
+ * and comb[8 + (BBS2 & 7)] taken when the call starts, and at its end
+ * generator k (state and modulus) moves to place k + 1.
+ * For CI_VAR_BBS:  Each strategy
  * word takes ceil(32/w) BBS outputs' low w bits (w = floor(log2 log2 M) = 5
  * for these 62-bit moduli), then twice: shift = BBS & 3; t <<= shift;
  * t |= BBS & {0,1,3,7}[shift] -- 11 modular squarings per output, done with
@@ -262,7 +275,9 @@ ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, voi
  *  - keeps up to two waves in flight, so requests that arrive while others
  *    are on the GPU join the next wave.
  * Slicing a stream over waves is exact: each result equals the one-call
- * result whether the request runs alone or in any mix.  Stream state stays
+ * result whether the request runs alone or in any mix.  (CI_VAR_BBS16, whose
+ * outputs depend on call boundaries, runs each request as one slice: one
+ * call.)  Stream state stays
  * resident in the arena between requests; a request may continue the streams
  * of an earlier request. */
 typedef struct ci_server_s *ci_server;
@@ -361,8 +376,10 @@ ci_status ci_server_destroy(ci_server server);
  *   then 9 uint32 fields of P lanes each (field f at 512 + 4*f*P):
  *     0..3 xor-like words (xor128 a, b, c, d; XORshift z in field 0),
  *     4 x, 5 slot (last strategy), 6 sel1 | sel2 << 8, 7 p, 8 q
- *   then (BBS only) 4 uint64 fields of P lanes: 0 y (canonical residue, BBS
- *     state), 1 M, 2 -M^-1 mod 2^64, 3 2^128 mod M.
+ *   then (CI_VAR_BBS16 only) 16 more uint32 fields: 9..16 the states of
+ *     BBS1..BBS8 (each < its modulus), 17..24 their moduli (>= 2, < 2^16);
+ *   then (CI_VAR_BBS only) 4 uint64 fields of P lanes: 0 y (canonical
+ *     residue, BBS state), 1 M, 2 -M^-1 mod 2^64, 3 2^128 mod M.
  * Importing replaces the state of a handle with the same parameters and
  * n_streams; an imported BBS state must hold y < 2^64 and the constants of M.
  * Errors: CI_E_INVAL (size mismatch), CI_E_CUDA. */
@@ -385,10 +402,10 @@ typedef struct {
                                   not measured)                                    */
 } ci_tune_choice;
 
-/* choice[source][sink]: source 0 xor128, 1 XORshift32, 2 BBS; sink 0 written
+/* choice[source][sink]: source 0 xor128, 1 XORshift32, 2 BBS, 3 BBS16; sink 0 written
  * 16-byte-aligned, 1 written unaligned, 2 quarter-circle, 3 digest. */
 typedef struct {
-    ci_tune_choice choice[3][4];
+    ci_tune_choice choice[4][4];
     uint32_t batch_warps_per_block;  /* batched persistent kernel (read when a
                                         ci_batch or ci_server is created)        */
     float batch_ms;

@@ -16,7 +16,7 @@ import torch
 from . import _lib
 from ._lib import CIError, ci_params, ci_states_desc
 
-VARIANTS = {"xor": _lib.CI_VAR_XOR, "bbs": _lib.CI_VAR_BBS}
+VARIANTS = {"xor": _lib.CI_VAR_XOR, "bbs": _lib.CI_VAR_BBS, "bbs16": _lib.CI_VAR_BBS16}
 XORLIKES = {"xor128": _lib.CI_XL_XOR128, "xorshift32": _lib.CI_XL_XORSHIFT32}
 
 SINKS = {"written": _lib.CI_SINK_WRITTEN, "qc": _lib.CI_SINK_QC, "digest": _lib.CI_SINK_DIGEST}
@@ -121,7 +121,7 @@ class States:
         n = int(n_per_stream)
         if out is None:
             out = torch.empty((self.n_streams, n), dtype=torch.int32, device="cuda")
-        name = "ci_generate_bbs" if self.variant == _lib.CI_VAR_BBS else "ci_generate"
+        name = "ci_generate" if self.variant == _lib.CI_VAR_XOR else "ci_generate_bbs"
         _lib.call(name, self.handle, n, out.data_ptr(), out.numel(), stream_ptr(stream))
         return out
 
@@ -304,7 +304,7 @@ class Server:
             pass
 
 
-SOURCES = ("xor128", "xorshift32", "bbs")
+SOURCES = ("xor128", "xorshift32", "bbs", "bbs16")
 SINK_CLASSES = ("written", "written_unaligned", "qc", "digest")
 
 
@@ -368,9 +368,12 @@ def batch_run_noalloc(items, stream=None) -> None:
 def unpack_state(buf: np.ndarray, n_lanes: int, variant: int) -> dict:
     """Splits an exported state into its documented fields."""
     P = int(n_lanes)
-    u32 = buf[512:512 + 36 * P].view(np.uint32).reshape(9, P)
+    nf = 25 if variant == _lib.CI_VAR_BBS16 else 9
+    u32 = buf[512:512 + 4 * nf * P].view(np.uint32).reshape(nf, P)
     out = {"table": buf[:512].reshape(16, 32), "a": u32[0], "b": u32[1], "c": u32[2], "d": u32[3],
            "x": u32[4], "slot": u32[5], "sel": u32[6], "p": u32[7], "q": u32[8]}
+    if variant == _lib.CI_VAR_BBS16:
+        out.update({"y16": u32[9:17].T, "m16": u32[17:25].T})
     if variant == _lib.CI_VAR_BBS:
         u64 = buf[512 + 36 * P:512 + 36 * P + 32 * P].view(np.uint64).reshape(4, P)
         out.update({"y": u64[0], "M": u64[1], "Mp": u64[2], "r2": u64[3]})

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "libci_prng.so")
 
 CI_OK, CI_PENDING = 0, 1
 CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE = -1, -2, -3, -4, -5, -6
-CI_VAR_XOR, CI_VAR_BBS = 0, 1
+CI_VAR_XOR, CI_VAR_BBS, CI_VAR_BBS16 = 0, 1, 2
 CI_SINK_WRITTEN, CI_SINK_QC, CI_SINK_DIGEST = 0, 1, 2
 CI_NOALLOC_MAX_ITEMS = 1024
 CI_XL_XOR128, CI_XL_XORSHIFT32 = 0, 1
@@ -110,7 +110,7 @@ class ci_tune_choice(ctypes.Structure):
 
 class ci_tune_table(ctypes.Structure):
     _fields_ = [
-        ("choice", (ci_tune_choice * 4) * 3),
+        ("choice", (ci_tune_choice * 4) * 4),
         ("batch_warps_per_block", ctypes.c_uint32),
         ("batch_ms", ctypes.c_float),
     ]

@@ -27,7 +27,7 @@ ci_status cuda_fail(cudaError_t e, const char *what) {
 bool valid_handle(const ci_states s) { return s != nullptr && s->magic == kMagic; }
 
 uint64_t state_bytes_for(int variant, uint64_t P) {
-    return (uint64_t)kTableBytes + 4ull * kU32Fields * P +
+    return (uint64_t)kTableBytes + 4ull * (variant == CI_VAR_BBS16 ? kU32FieldsBbs16 : kU32Fields) * P +
            (variant == CI_VAR_BBS ? 8ull * kU64Fields * P : 0ull);
 }
 
@@ -56,7 +56,7 @@ static void shuffle(uint32_t C, uint64_t seed, uint64_t &ctr, uint8_t *a) {
 // first at every position (an equal pair of partners cancels in the XOR).
 static void derive_comb(int variant, uint32_t C, uint64_t seed, uint8_t *comb) {
     uint64_t ctr = 0;
-    if (variant == CI_VAR_BBS) {
+    if (variant != CI_VAR_XOR) {
         for (int a = 0; a < 16; ++a) shuffle(C, seed, ctr, comb + a * C);
         return;
     }
@@ -73,14 +73,15 @@ static void derive_comb(int variant, uint32_t C, uint64_t seed, uint8_t *comb) {
 // Partner table: lane j of a warp, array a -> lane (j - j % C) + comb[a][j % C].
 static void build_table(int variant, uint32_t C, const uint8_t *comb, uint8_t *table) {
     std::memset(table, 0, kTableBytes);
-    const int arrays = variant == CI_VAR_BBS ? 16 : 2;
+    const int arrays = variant == CI_VAR_XOR ? 2 : 16;
     for (int a = 0; a < arrays; ++a)
         for (uint32_t j = 0; j < 32; ++j) table[a * 32 + j] = (uint8_t)((j & ~(C - 1)) + comb[a * C + (j & (C - 1))]);
 }
 
 static ci_status check_params(const ci_params *p, uint64_t S) {
     if (!p) return fail(CI_E_INVAL, "params is NULL");
-    if (p->variant != CI_VAR_XOR && p->variant != CI_VAR_BBS) return fail(CI_E_INVAL, "unknown variant");
+    if (p->variant != CI_VAR_XOR && p->variant != CI_VAR_BBS && p->variant != CI_VAR_BBS16)
+        return fail(CI_E_INVAL, "unknown variant");
     if (p->variant == CI_VAR_XOR && p->xl != CI_XL_XOR128 && p->xl != CI_XL_XORSHIFT32)
         return fail(CI_E_INVAL, "unknown xor-like generator");
     const uint32_t C = p->comb_size;
@@ -90,7 +91,7 @@ static ci_status check_params(const ci_params *p, uint64_t S) {
     if ((p->first_stream & 31ull) != 0 || p->first_stream > (1ull << 32) - S)
         return fail(CI_E_INVAL, "first_stream must be a multiple of 32 with first_stream + n_streams <= 2^32");
     if (p->comb) {
-        const uint32_t n = (p->variant == CI_VAR_BBS ? 16u : 2u) * C;
+        const uint32_t n = (p->variant == CI_VAR_XOR ? 2u : 16u) * C;
         for (uint32_t i = 0; i < n; ++i)
             if (p->comb[i] >= C) return fail(CI_E_INVAL, "combination array entry >= comb_size");
     }
@@ -112,7 +113,7 @@ ci_status prepare_handle(const ci_params *p, uint64_t S, void *dev, uint64_t byt
     h->dev = dev;
     h->owns = owns;
     std::memset(h->comb, 0, sizeof h->comb);
-    const uint32_t ncomb = (p->variant == CI_VAR_BBS ? 16u : 2u) * h->C;
+    const uint32_t ncomb = (p->variant == CI_VAR_XOR ? 2u : 16u) * h->C;
     if (p->comb)
         std::memcpy(h->comb, p->comb, ncomb);
     else
@@ -296,7 +297,7 @@ ci_status ci_generate(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void
 
 ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void *stream) {
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
-    if (s->variant != CI_VAR_BBS) return fail(CI_E_STATE, "ci_generate_bbs needs a BBS-variant state (use ci_generate)");
+    if (s->variant == CI_VAR_XOR) return fail(CI_E_STATE, "ci_generate_bbs needs a BBS-variant state (use ci_generate)");
     if (n == 0) return CI_OK;
     ci_status st = check_out(s, n, out, cap);
     if (st != CI_OK) return st;

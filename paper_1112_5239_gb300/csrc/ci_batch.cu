@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_batched(BatchHeader *hdr, const 
         const uint64_t g = T.g0 + (u - T.prefix);
         if (T.kind == K_BBS)
             run_sink<SrcBbs>(T, g, tile);
+        else if (T.kind == K_BBS16)
+            run_sink<SrcBbs16>(T, g, tile);
         else if (T.kind == K_XS32)
             run_sink<SrcXorshift32>(T, g, tile);
         else
@@ -96,8 +98,9 @@ BatchGeometry batch_geometry(int warps_per_block) {
 }
 
 double kind_cost(uint32_t kind) {
-    // measured ratio of per-output cost (BBS: 11 modular squarings per output)
-    return kind == K_BBS ? 40.0 : 1.0;
+    // measured ratios of per-output cost (BBS: 11 Montgomery squarings per
+    // output; BBS16: 12 32-bit Barrett squarings)
+    return kind == K_BBS ? 40.0 : kind == K_BBS16 ? 8.0 : 1.0;
 }
 
 BatchTask make_task(const ci_states_s &h, uint64_t n, int sink_abi, uint32_t *out, uint64_t *aux, uint64_t ld,
@@ -112,7 +115,9 @@ BatchTask make_task(const ci_states_s &h, uint64_t n, int sink_abi, uint32_t *ou
     t.n = n;
     t.g0 = 0;
     t.ngroups = h.P / 32;
-    t.kind = h.variant == CI_VAR_BBS ? K_BBS : (h.xl == CI_XL_XORSHIFT32 ? K_XS32 : K_XOR128);
+    t.kind = h.variant == CI_VAR_BBS     ? K_BBS
+             : h.variant == CI_VAR_BBS16 ? K_BBS16
+             : (h.xl == CI_XL_XORSHIFT32 ? K_XS32 : K_XOR128);
     if (sink_abi == CI_SINK_QC)
         t.sink = SINK_QC;
     else if (sink_abi == CI_SINK_DIGEST)

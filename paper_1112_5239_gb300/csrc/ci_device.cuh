@@ -177,6 +177,64 @@ struct SrcBbs {
     }
 };
 
+// Algorithm 5 as printed: eight BBS generators per lane with moduli below
+// 2^16, so x^2 fits 32 bits.  x^2 mod M by Barrett reduction with
+// mu = floor(2^32 / M): q = mulhi(x^2, mu) is floor(x^2 / M) or one less, so a
+// single conditional subtraction gives the canonical residue.  The arrays are
+// read from BBS1 and BBS2 when the call starts; at the end of the call
+// generator k (state and modulus) is stored in place k + 1.
+struct SrcBbs16 {
+    static constexpr bool kHeavy = true;
+    uint32_t y[8], M[8], mu[8];
+    uint32_t sel1, sel2;
+    __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            y[k] = s.u32[(F_Y16 + k) * s.P + l];
+            M[k] = s.u32[(F_M16 + k) * s.P + l];
+            mu[k] = (uint32_t)((1ull << 32) / M[k]);
+        }
+        sel1 = y[0] & 7u;
+        sel2 = y[1] & 7u;
+    }
+    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            s.u32[(F_Y16 + (k + 1) % 8) * s.P + l] = y[k];
+            s.u32[(F_M16 + (k + 1) % 8) * s.P + l] = M[k];
+        }
+    }
+    __device__ __forceinline__ void arrays(const DevState &, uint64_t, int &a1, int &a2) const {
+        a1 = (int)sel1;
+        a2 = 8 + (int)sel2;
+    }
+    template <int K>
+    __device__ __forceinline__ uint32_t bbs() {  // BBS(K+1)
+        const uint32_t a = y[K] * y[K];
+        uint32_t r = a - __umulhi(a, mu[K]) * M[K];
+        if (r >= M[K]) r -= M[K];
+        y[K] = r;
+        return r;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        uint32_t t = (bbs<0>() & 15u) << 28;
+        t |= (bbs<1>() & 15u) << 24;
+        t |= (bbs<2>() & 15u) << 20;
+        t |= (bbs<3>() & 15u) << 16;
+        t |= (bbs<4>() & 15u) << 12;
+        t |= (bbs<5>() & 15u) << 8;
+        t |= (bbs<6>() & 15u) << 4;
+        t |= bbs<7>() & 15u;
+        uint32_t shift = bbs<2>() & 3u;
+        t <<= shift;
+        t |= bbs<0>() & ((1u << shift) - 1u);  // array_shift = {0, 1, 3, 7}
+        shift = bbs<6>() & 3u;
+        t <<= shift;
+        t |= bbs<1>() & ((1u << shift) - 1u);
+        return t;
+    }
+};
+
 // ----------------------------------------------------- generation loop
 enum Sink { SINK_V4 = 0, SINK_SCALAR = 1, SINK_QC = 2, SINK_DIGEST = 3 };
 

@@ -148,6 +148,50 @@ __global__ void __launch_bounds__(256) k_init_bbs(DevState st, TableParam tp, ui
         init_bbs_lane(st, seed, first, l);
 }
 
+// Algorithm 5 as printed: eight generators per lane, Blum primes p != q from
+// candidates (128 + draw mod 128) | 3 (odd, < 256: prime iff no divisor in
+// 3..13), a seed coprime to M, then x and the slot.
+__device__ __forceinline__ bool is_prime_below_256(uint32_t c) {  // c odd, >= 131
+    return c % 3u && c % 5u && c % 7u && c % 11u && c % 13u;
+}
+
+__device__ void init_bbs16_lane(const DevState &st, uint64_t seed, uint64_t first, uint64_t l) {
+    uint64_t k = 0, d;
+    for (int g = 0; g < 8; ++g) {
+        uint32_t p, q;
+        do {
+            d = lane_draw(seed, first + l, k++);
+            p = (uint32_t)(128u + d % 128u) | 3u;
+        } while (!is_prime_below_256(p));
+        do {
+            d = lane_draw(seed, first + l, k++);
+            q = (uint32_t)(128u + d % 128u) | 3u;
+        } while (q == p || !is_prime_below_256(q));
+        const uint32_t M = p * q;
+        uint32_t v;
+        do {
+            d = lane_draw(seed, first + l, k++);
+            v = 2u + (uint32_t)(d % (uint64_t)(M - 2u));
+        } while (v % p == 0u || v % q == 0u);
+        st.u32[(F_Y16 + g) * st.P + l] = v;
+        st.u32[(F_M16 + g) * st.P + l] = M;
+    }
+    d = lane_draw(seed, first + l, k++);
+    for (int f = F_A; f <= F_D; ++f) st.u32[f * st.P + l] = 0u;
+    st.u32[F_X * st.P + l] = (uint32_t)d;
+    st.u32[F_SLOT * st.P + l] = (uint32_t)(d >> 32);
+    st.u32[F_SEL * st.P + l] = 0u;
+    st.u32[F_P * st.P + l] = 0u;
+    st.u32[F_Q * st.P + l] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_init_bbs16(DevState st, TableParam tp, uint64_t seed, uint64_t first) {
+    write_table(st, tp);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < st.P; l += stride)
+        init_bbs16_lane(st, seed, first, l);
+}
+
 // Seeding of many states in one launch: thread g takes global lane g, finds
 // its task (largest lane prefix <= g) and seeds that lane; the first lanes of
 // each task also write its partner table.
@@ -168,6 +212,8 @@ __global__ void __launch_bounds__(256) k_init_batched(const InitTask *tasks, uin
             reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(T.st.table))[w] = T.table[w];
         if (T.variant == CI_VAR_BBS)
             init_bbs_lane(T.st, T.seed, T.first, l);
+        else if (T.variant == CI_VAR_BBS16)
+            init_bbs16_lane(T.st, T.seed, T.first, l);
         else
             init_xor_lane(T.st, T.seed, T.first, T.xl, l);
     }
@@ -203,6 +249,8 @@ cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first, cud
     std::memcpy(tp.w, h.table, kTableBytes);
     if (h.variant == CI_VAR_BBS)
         k_init_bbs<<<grid, kBlockThreads, 0, stream>>>(st, tp, seed, first);
+    else if (h.variant == CI_VAR_BBS16)
+        k_init_bbs16<<<grid, kBlockThreads, 0, stream>>>(st, tp, seed, first);
     else
         k_init_xor<<<grid, kBlockThreads, 0, stream>>>(st, tp, seed, first, h.xl);
     return cudaGetLastError();
@@ -212,11 +260,13 @@ cudaError_t launch_with(const ci_states_s &h, int sink, const TuneChoice &c, uin
                         uint64_t *counts, cudaStream_t stream) {
     const DevState st = h.view();
     if (h.variant == CI_VAR_BBS) return gen_bbs(sink, c, st, n, out, counts, stream);
+    if (h.variant == CI_VAR_BBS16) return gen_bbs16(sink, c, st, n, out, counts, stream);
     if (h.xl == CI_XL_XORSHIFT32) return gen_xs32(sink, c, st, n, out, counts, stream);
     return gen_xor128(sink, c, st, n, out, counts, stream);
 }
 
 static int src_kind(const ci_states_s &h) {
+    if (h.variant == CI_VAR_BBS16) return SK_BBS16;
     return h.variant == CI_VAR_BBS ? SK_BBS : (h.xl == CI_XL_XORSHIFT32 ? SK_XS32 : SK_XOR128);
 }
 

@@ -341,7 +341,11 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w) {  // un
     for (Req *qp : s->active) {
         Req &q = *qp;
         if (q.enq >= q.L) continue;
-        const uint64_t slice = q.variant == CI_VAR_BBS ? s->cfg.slice_bbs : s->cfg.slice_xor;
+        // CI_VAR_BBS16 outputs depend on call boundaries (per-call arrays and
+        // rotation): such a request runs as a single slice, i.e. one call
+        const uint64_t slice = q.variant == CI_VAR_BBS16 ? q.L
+                               : q.variant == CI_VAR_BBS ? s->cfg.slice_bbs
+                                                         : s->cfg.slice_xor;
         const uint64_t n = std::min(slice, q.L - q.enq);
         tasks.push_back(q.tmpl);
         BatchTask &tk = tasks.back();
@@ -481,7 +485,7 @@ ci_status submit_locked(ci_server_s *s, const ci_request *req, uint64_t *ticket)
         q.S = req->n_streams;
         q.variant = req->params.variant;
         if (req->params.comb) {
-            const uint32_t n = (req->params.variant == CI_VAR_BBS ? 16u : 2u) * req->params.comb_size;
+            const uint32_t n = (req->params.variant == CI_VAR_XOR ? 2u : 16u) * req->params.comb_size;
             std::memcpy(q.comb, req->params.comb, n);
             q.has_comb = true;
         }

@@ -21,7 +21,7 @@ static std::mutex g_tune_mu;
 static ci_tune_table g_table = [] {
     ci_tune_table t;
     std::memset(&t, 0, sizeof t);
-    for (int s = 0; s < 3; ++s)
+    for (int s = 0; s < kSrcKinds; ++s)
         for (int k = 0; k < 4; ++k) {
             t.choice[s][k].warps_per_block = 8;
             t.choice[s][k].tile_depth = 32;
@@ -46,7 +46,7 @@ static bool valid_choice(int src, int sink, const ci_tune_choice &c) {
     if (c.warps_per_block != 4 && c.warps_per_block != 8 && c.warps_per_block != 16) return false;
     if (c.cache_policy > 1) return false;
     if (c.tile_depth != 32 && c.tile_depth != 64) return false;
-    if (c.tile_depth == 64 && !(sink == dev::SINK_V4 && src != SK_BBS)) return false;
+    if (c.tile_depth == 64 && !(sink == dev::SINK_V4 && (src == SK_XOR128 || src == SK_XS32))) return false;
     if (c.cache_policy == 1 && sink != dev::SINK_V4) return false;
     return true;
 }
@@ -101,7 +101,7 @@ ci_status ci_tune_get(ci_tune_table *out) {
 
 ci_status ci_tune_set(const ci_tune_table *in) {
     if (!in) return fail(CI_E_INVAL, "in is NULL");
-    for (int s = 0; s < 3; ++s)
+    for (int s = 0; s < kSrcKinds; ++s)
         for (int k = 0; k < 4; ++k)
             if (!valid_choice(s, k, in->choice[s][k])) return fail(CI_E_INVAL, "launch shape not allowed for its class");
     if (in->batch_warps_per_block != 4 && in->batch_warps_per_block != 8 && in->batch_warps_per_block != 16)
@@ -120,18 +120,18 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out) {
         table = g_table;
     }
     // Representative problems: xor sources 2^19 streams (written: 256 outputs
-    // per stream, 512 MiB; consumers: 1024), BBS 2^16 streams x 128.
+    // per stream, 512 MiB; consumers: 1024), BBS sources 2^16 streams x 128.
     const uint64_t S_xor = 1ull << 19, S_bbs = 1ull << 16;
     const uint64_t L_written = 256, L_fused = 1024, L_bbs = 128;
     ci_params p;
     std::memset(&p, 0, sizeof p);
     p.comb_size = 32;
     p.seed = 12345;
-    ci_states hs[3] = {nullptr, nullptr, nullptr};
-    const uint64_t S_of[3] = {S_xor, S_xor, S_bbs};
+    ci_states hs[kSrcKinds] = {nullptr, nullptr, nullptr, nullptr};
+    const uint64_t S_of[kSrcKinds] = {S_xor, S_xor, S_bbs, S_bbs};
     ci_status rc = CI_OK;
-    for (int s = 0; s < 3 && rc == CI_OK; ++s) {
-        p.variant = s == SK_BBS ? CI_VAR_BBS : CI_VAR_XOR;
+    for (int s = 0; s < kSrcKinds && rc == CI_OK; ++s) {
+        p.variant = s == SK_BBS ? CI_VAR_BBS : (s == SK_BBS16 ? CI_VAR_BBS16 : CI_VAR_XOR);
         p.xl = s == SK_XS32 ? CI_XL_XORSHIFT32 : CI_XL_XOR128;
         rc = ci_init_states(&p, S_of[s], cuda_stream, &hs[s]);
     }
@@ -141,9 +141,9 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out) {
     if (rc == CI_OK) e = cudaMalloc(&out_dev, S_xor * L_written * 4 + 64);
     if (rc == CI_OK && e == cudaSuccess) e = cudaMalloc(&aux_dev, S_xor * 8);
     if (rc == CI_OK && e != cudaSuccess) rc = cuda_fail(e, "autotuner buffers");
-    for (int s = 0; s < 3 && rc == CI_OK; ++s) {
+    for (int s = 0; s < kSrcKinds && rc == CI_OK; ++s) {
         for (int k = 0; k < 4 && rc == CI_OK; ++k) {
-            const uint64_t L = s == SK_BBS ? L_bbs : (k <= dev::SINK_SCALAR ? L_written : L_fused);
+            const uint64_t L = s >= SK_BBS ? L_bbs : (k <= dev::SINK_SCALAR ? L_written : L_fused);
             // the unaligned written sink runs on an output offset by one word
             uint32_t *o = k == dev::SINK_SCALAR ? out_dev + 1 : out_dev;
             float best = 1e30f;

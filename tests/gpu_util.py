@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 
-VAR = {"xor": 0, "bbs": 1}
+VAR = {"xor": 0, "bbs": 1, "bbs16": 2}
 XL = {"xor128": 0, "xorshift32": 1}
 
 

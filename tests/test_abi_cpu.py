@@ -55,6 +55,9 @@ def test_version_and_errors_without_gpu(L):
     p.variant = 1
     assert lib.ci_state_bytes(ctypes.byref(p), 33, ctypes.byref(nbytes)) == 0
     assert nbytes.value == 512 + 9 * 4 * 64 + 4 * 8 * 64
+    p.variant = 2
+    assert lib.ci_state_bytes(ctypes.byref(p), 40, ctypes.byref(nbytes)) == 0
+    assert nbytes.value == 512 + 25 * 4 * 64
     bad = []
     for field, value in [("comb_size", 3), ("comb_size", 64), ("variant", 7), ("flags", 1),
                          ("first_stream", 5)]:

@@ -20,7 +20,7 @@ def _shapes(src, sink):
     for w in (4, 8, 16):
         for kt in (32, 64):
             for cp in (0, 1):
-                if kt == 64 and not (sink == "written" and src != "bbs"):
+                if kt == 64 and not (sink == "written" and src in ("xor128", "xorshift32")):
                     continue
                 if cp == 1 and sink != "written":
                     continue
@@ -28,11 +28,11 @@ def _shapes(src, sink):
     return out
 
 
-@pytest.mark.parametrize("src", ["xor128", "xorshift32", "bbs"])
+@pytest.mark.parametrize("src", ["xor128", "xorshift32", "bbs", "bbs16"])
 def test_every_launch_shape_matches_oracle(env, src):
     torch, ci = env
     base = ci.tune_table()
-    variant = "bbs" if src == "bbs" else "xor"
+    variant = src if src in ("bbs", "bbs16") else "xor"
     xl = "xorshift32" if src == "xorshift32" else "xor128"
     S, L = 1000, 200  # 32 warp groups (several blocks) and a ragged tail of the 64-deep tile
     ref_orc = oracle_gen(variant, xl, 32, 31, 0, S)
