@@ -221,6 +221,14 @@ def ncu_traffic(kernel_key: str):
     return None
 
 
+def written_kernel_name(choice: dict) -> str:
+    """Name of the written xor128 kernel the tuned launch shape selects."""
+    w = choice["warps_per_block"]
+    if choice["cache_policy"] == 2:
+        return "k_generate_tma<SrcXor128,%d>" % w
+    return "k_generate<SrcXor128,SINK_V4,%d,TileCfg<%d,%d>>" % (w, choice["tile_depth"], choice["cache_policy"])
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -360,11 +368,13 @@ def main():
     peak, peak_kind, peaks = measured_peaks()
     alg_bytes = S_MAIN * CHUNK * 4 + S_MAIN * 2 * STATE_BYTES_PER_LANE_XOR128
     achieved = alg_bytes / avg_launch_s / 1e9
+    kname = written_kernel_name(tuned["xor128/written"])
+    traffic = ncu_traffic(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy read+write)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "traffic": ncu_traffic("k_generate<SrcXor128,SINK_V4>"),
-                "kernel": "k_generate<SrcXor128,SINK_V4>", "alg_bytes_per_launch": alg_bytes,
+                "traffic": traffic, "traffic_over_alg_bytes": (traffic / alg_bytes) if traffic else None,
+                "kernel": kname, "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": avg_launch_s * 1e3}
 
     result = {

@@ -397,7 +397,10 @@ typedef struct {
                                   shared memory per flush, 32 or 64 (64 only for
                                   16-byte-aligned xor-variant outputs)             */
     uint32_t cache_policy;     /* 16-byte-aligned written outputs: 0 streaming
-                                  (evict-first) stores, 1 write-back stores        */
+                                  (evict-first) 16-byte stores, 1 write-back
+                                  16-byte stores, 2 TMA bulk tensor stores of the
+                                  staging tile (xor sources, tile depth 32; falls
+                                  back to 0 where TMA's alignment rules fail)     */
     float ms;                  /* time of the tuning problem with this shape (0:
                                   not measured)                                    */
 } ci_tune_choice;
@@ -412,10 +415,11 @@ typedef struct {
 } ci_tune_table;
 
 /* Times every allowed shape of every class on representative problems (xor:
- * 2^19 streams x 256 written / x 1024 consumed; BBS: 2^16 streams x 128; a
- * 64-request mixed batch) on cuda_stream, installs the fastest for this
- * process and returns the table.  Allocates and frees its own test states and
- * buffers; takes well under a second.  flags must be 0.  Errors: CI_E_INVAL,
+ * 2^20 streams x 256 written / x 1024 consumed; BBS: 2^16 streams x 128; a
+ * 64-request mixed batch; median of 5 launches each) on cuda_stream, installs
+ * the fastest for this process and returns the table.  Allocates and frees its
+ * own test states and buffers (about 1.2 GB); takes about a second.  flags
+ * must be 0.  Errors: CI_E_INVAL,
  * CI_E_NOMEM, CI_E_CUDA. */
 ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out);
 

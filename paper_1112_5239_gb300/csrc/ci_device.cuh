@@ -13,6 +13,8 @@
 // the partners' strategies of iteration i - 1.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (TMA descriptor type only)
+
 #include <cstdint>
 
 #include "ci_internal.h"
@@ -400,6 +402,98 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
     st.u32[F_SLOT * st.P + l] = slot;
     if (SINK == SINK_QC && l < st.S) counts[l] += hits;
     if (SINK == SINK_DIGEST && l < st.S) counts[l] = hits;
+}
+
+// ------------------------------------------------ TMA bulk tensor stores
+// A warp's 32 x 32 staging tile leaves as ONE cp.async.bulk.tensor store: the
+// tile's layout (16-byte chunk c of row r at chunk position c ^ (r % 8), tile
+// base 1024-byte aligned) is the TMA 128-byte swizzle, so the tensor map uses
+// CU_TENSOR_MAP_SWIZZLE_128B over the output [rows][cols] with a 32 x 32 box.
+// The store carries an L2 evict-first policy (outputs are streamed out, as the
+// 16-byte path's st.global.cs does).
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void tma_store_tile(const CUtensorMap *map, const void *smem, int x, int y,
+                                               uint64_t policy) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;"
+                 :
+                 : "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(s), "l"(policy)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until at most one committed store still reads its shared-memory source.
+__device__ __forceinline__ void tma_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until every committed store has completed.
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Make this thread's ordinary shared-memory writes visible to the TMA unit.
+__device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Written sink through TMA: per 32-iteration tile, the lanes fill one of two
+// 4 KB tiles (double buffering: a tile is refilled only after the store issued
+// from it two tiles earlier has read it), then lane 0 issues the tile's bulk
+// tensor store at (column col0 + i0, row 32 g); rows past the tensor's row
+// count (streams >= S) are clipped by the TMA unit.  A ragged tail of fewer
+// than 32 iterations leaves through ordinary stores.  `tiles` is 2 x 4 KB,
+// 1024-byte aligned.  Requires out 16-byte aligned, ld % 4 == 0, col0 % 4 == 0
+// (checked by the host when it builds the tensor map).
+template <class Src>
+__device__ __forceinline__ void warp_task_tma(const DevState &st, uint64_t g, uint64_t n, const CUtensorMap *map,
+                                              uint32_t *out, uint64_t ld, uint64_t col0, uint4 *tiles) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t l = g * 32 + lane;
+    Src src;
+    src.load(st, l);
+    uint32_t x = st.u32[F_X * st.P + l];
+    uint32_t slot = st.u32[F_SLOT * st.P + l];
+    int a1, a2;
+    src.arrays(st, l, a1, a2);
+    const int p1 = st.table[a1 * 32 + lane];
+    const int p2 = st.table[a2 * 32 + lane];
+    const uint64_t row0 = g * 32;
+    const uint64_t nfull = n & ~31ull;
+    if (lane == 0) tma_wait_read_0();  // tiles free (stores of the previous task have read them)
+    __syncwarp();
+    const uint64_t policy = l2_evict_first_policy();
+    int k = 0;
+    for (uint64_t i0 = 0; i0 < nfull; i0 += 32, ++k) {
+        uint4 *tile = tiles + (k & 1) * 256;
+        if (k >= 2) {
+            if (lane == 0) tma_wait_read_1();
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint4 v;
+            v.x = ci_step(src, x, slot, p1, p2);
+            v.y = ci_step(src, x, slot, p1, p2);
+            v.z = ci_step(src, x, slot, p1, p2);
+            v.w = ci_step(src, x, slot, p1, p2);
+            tile[lane * 8 + (q ^ (lane & 7))] = v;
+        }
+        fence_smem_to_async();
+        __syncwarp();
+        if (lane == 0) tma_store_tile(map, tile, (int)(col0 + i0), (int)row0, policy);
+    }
+    const int rem = (int)(n - nfull);
+    if (rem) {
+        if (lane == 0) tma_wait_read_0();
+        __syncwarp();
+        uint32_t *tw = reinterpret_cast<uint32_t *>(tiles);
+        for (int kk = 0; kk < rem; ++kk) tw[tile_word<32>(lane, kk)] = ci_step(src, x, slot, p1, p2);
+        __syncwarp();
+        for (int r = 0; r < 32; ++r)
+            if (lane < rem && row0 + r < st.S) out[(row0 + r) * ld + col0 + nfull + lane] = tw[tile_word<32>(r, lane)];
+        __syncwarp();
+    }
+    src.store(st, l);
+    st.u32[F_X * st.P + l] = x;
+    st.u32[F_SLOT * st.P + l] = slot;
 }
 
 }  // namespace dev

@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "ci_device.cuh"
+#include "ci_gen.cuh"
 #include "ci_tune.h"
 
 namespace ci {
@@ -254,6 +255,43 @@ cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first, cud
     else
         k_init_xor<<<grid, kBlockThreads, 0, stream>>>(st, tp, seed, first, h.xl);
     return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+bool make_out_tensor_map(CUtensorMap *map, uint32_t *out, uint64_t rows, uint64_t cols) {
+    // TMA: base 16-byte aligned, row stride a multiple of 16 bytes (cols % 4),
+    // int32 coordinates; box 32 x 32 words, 128-byte swizzle
+    if ((reinterpret_cast<uintptr_t>(out) & 15u) || cols % 4 || cols < 32 || rows == 0 || cols >= (1ull << 31) ||
+        rows >= (1ull << 31))
+        return false;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 4ull};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t elem[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, out, dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
 }
 
 cudaError_t launch_with(const ci_states_s &h, int sink, const TuneChoice &c, uint64_t n, uint32_t *out,

@@ -44,10 +44,12 @@ int tuned_batch_warps() {
 
 static bool valid_choice(int src, int sink, const ci_tune_choice &c) {
     if (c.warps_per_block != 4 && c.warps_per_block != 8 && c.warps_per_block != 16) return false;
-    if (c.cache_policy > 1) return false;
+    if (c.cache_policy > 2) return false;
     if (c.tile_depth != 32 && c.tile_depth != 64) return false;
-    if (c.tile_depth == 64 && !(sink == dev::SINK_V4 && (src == SK_XOR128 || src == SK_XS32))) return false;
+    const bool xor_src = src == SK_XOR128 || src == SK_XS32;
+    if (c.tile_depth == 64 && !(sink == dev::SINK_V4 && xor_src)) return false;
     if (c.cache_policy == 1 && sink != dev::SINK_V4) return false;
+    if (c.cache_policy == 2 && !(sink == dev::SINK_V4 && xor_src && c.tile_depth == 32)) return false;
     return true;
 }
 
@@ -56,7 +58,7 @@ static std::vector<ci_tune_choice> candidates(int src, int sink) {
     std::vector<ci_tune_choice> v;
     for (uint32_t w : {4u, 8u, 16u})
         for (uint32_t kt : {32u, 64u})
-            for (uint32_t cp : {0u, 1u}) {
+            for (uint32_t cp : {0u, 1u, 2u}) {
                 ci_tune_choice c;
                 std::memset(&c, 0, sizeof c);
                 c.warps_per_block = w;
@@ -67,11 +69,12 @@ static std::vector<ci_tune_choice> candidates(int src, int sink) {
     return v;
 }
 
+// Median of reps - 1 timed launches (the first launch is the warm-up).
 static float time_launches(cudaStream_t s, int reps, const std::function<cudaError_t()> &fn, cudaError_t *err) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    float best = 1e30f;
+    std::vector<float> t;
     for (int r = 0; r < reps && *err == cudaSuccess; ++r) {
         cudaEventRecord(a, s);
         *err = fn();
@@ -79,11 +82,13 @@ static float time_launches(cudaStream_t s, int reps, const std::function<cudaErr
         cudaEventSynchronize(b);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a, b);
-        if (r > 0) best = std::min(best, ms);  // first launch is the warm-up
+        if (r > 0) t.push_back(ms);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    return best;
+    if (t.empty()) return 1e30f;
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
 }
 
 }  // namespace ci
@@ -119,9 +124,9 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         table = g_table;
     }
-    // Representative problems: xor sources 2^19 streams (written: 256 outputs
-    // per stream, 512 MiB; consumers: 1024), BBS sources 2^16 streams x 128.
-    const uint64_t S_xor = 1ull << 19, S_bbs = 1ull << 16;
+    // Representative problems: xor sources 2^20 streams (written: 256 outputs
+    // per stream, a 1 GiB launch; consumers: 1024), BBS sources 2^16 x 128.
+    const uint64_t S_xor = 1ull << 20, S_bbs = 1ull << 16;
     const uint64_t L_written = 256, L_fused = 1024, L_bbs = 128;
     ci_params p;
     std::memset(&p, 0, sizeof p);
@@ -150,7 +155,7 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out) {
             ci_tune_choice pick = table.choice[s][k];
             for (const ci_tune_choice &c : candidates(s, k)) {
                 const TuneChoice tc{c.warps_per_block, c.tile_depth, c.cache_policy};
-                const float ms = time_launches(cs, 4, [&] { return launch_with(*hs[s], k, tc, L, o, aux_dev, cs); }, &e);
+                const float ms = time_launches(cs, 6, [&] { return launch_with(*hs[s], k, tc, L, o, aux_dev, cs); }, &e);
                 if (e != cudaSuccess) break;
                 if (ms < best) {
                     best = ms;

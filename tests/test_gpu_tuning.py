@@ -19,10 +19,12 @@ def _shapes(src, sink):
     out = []
     for w in (4, 8, 16):
         for kt in (32, 64):
-            for cp in (0, 1):
+            for cp in (0, 1, 2):
                 if kt == 64 and not (sink == "written" and src in ("xor128", "xorshift32")):
                     continue
                 if cp == 1 and sink != "written":
+                    continue
+                if cp == 2 and not (sink == "written" and src in ("xor128", "xorshift32") and kt == 32):
                     continue
                 out.append({"warps_per_block": w, "tile_depth": kt, "cache_policy": cp})
     return out
@@ -88,3 +90,26 @@ def test_tune_set_rejects_disallowed_shapes(env):
     with pytest.raises(ci.CIError):
         ci.set_tune_table(bad)
     assert ci.tune_table() == t
+
+
+@pytest.mark.parametrize("S,L", [(45, 96), (1000, 200), (32, 32), (70, 36)])
+def test_tma_store_path_clips_rows_and_matches_oracle(env, S, L):
+    """Store policy 2 (TMA bulk tensor stores): rows past the last stream are
+    clipped by the tensor bounds (guard words after the output untouched), a
+    ragged tail leaves through ordinary stores, outputs equal the oracle."""
+    torch, ci = env
+    base = ci.tune_table()
+    try:
+        for w in (4, 8, 16):
+            t = copy.deepcopy(base)
+            t["xor128/written"].update({"warps_per_block": w, "tile_depth": 32, "cache_policy": 2})
+            ci.set_tune_table(t)
+            st = ci.States(S, seed=S + L)
+            buf = torch.full((S * L + 1024,), 777, dtype=torch.int32, device="cuda")
+            st.generate(L, out=buf[:S * L].view(S, L))
+            got = u32(buf)
+            assert np.array_equal(got[:S * L].reshape(S, L), oracle_gen("xor", "xor128", 32, S + L, 0, S).streams(L))
+            assert np.all(got[S * L:] == 777)
+            assert np.array_equal(u32(st.generate(L)), oracle_gen("xor", "xor128", 32, S + L, 0, S).streams(2 * L)[:, L:])
+    finally:
+        ci.set_tune_table(base)
