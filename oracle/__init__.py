@@ -30,7 +30,7 @@ _SRC = os.path.join(_HERE, "ci_oracle.c")
 _LIB = os.path.join(_HERE, "libci_oracle.so")
 
 VAR_XOR, VAR_BBS, VAR_BBS16 = 0, 1, 2
-XL_XOR128, XL_XORSHIFT32 = 0, 1
+XL_XOR128, XL_XORSHIFT32, XL_XOR64 = 0, 1, 2
 
 # Layout of the C struct orc_lane (natural alignment).
 LANE_DTYPE = np.dtype(
@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
             "orc_xorshift32_step": (u32, [u32]),
             "orc_xorshift32_period": (u64, [u32, u64]),
             "orc_xor128_step": (u32, [vp]),
+            "orc_xor64_step": (u64, [u64]),
             "orc_bbs_step": (u64, [u64, u64]),
             "orc_bbs_w": (u32, [u64]),
             "orc_is_prime": (i32, [u64]),
@@ -124,6 +125,10 @@ def xor128_step(state) -> tuple[np.ndarray, int]:
     s = np.array(state, dtype=np.uint32).copy()
     out = int(lib().orc_xor128_step(_ptr(s)))
     return s, out
+
+
+def xor64_step(x: int) -> int:
+    return int(lib().orc_xor64_step(x))
 
 
 def bbs_step(y: int, M: int) -> int:

@@ -16,6 +16,7 @@
  * What it computes (paper construct -> function):
  *   Eq. (Oplus), x^n = x^{n-1} XOR S^n ............ orc_ci_step
  *   Algorithm 2 (XORshift round) ................... orc_xorshift32_step
+ *   xor64, the xor-like of the Sec. 7 experiments ... orc_xor64_step
  *   xor128 with 32-bit words (Sec. 6.2 text) ........ orc_xor128_step
  *   Algorithm 4 (one xor-like per thread, two
  *     combination arrays, mixing with the partners'
@@ -39,6 +40,8 @@
  *     iteration i - 1 (what warp lockstep gives Algorithm 4's unsynchronised
  *     shared-memory read/write); partner = group * C + comb[offset].
  *   - stream-major output out[s * L + i] = x after the (i + 1)-th update.
+ *   - xor64 feeds Algorithm 4 with the low 32 bits of each step (the way
+ *     Listing 1 takes "(unsigned int)t" from its 64-bit generators).
  *   - BBS: one generator per lane, w = floor(log2(floor(log2 M))) bits per
  *     squaring, ceil(32 / w) chunks, then Algorithm 5's two shift steps;
  *     combination arrays chosen once from the seed's low bits.
@@ -138,6 +141,17 @@ uint32_t orc_xor128_step(uint32_t *s)
     return s[3];
 }
 
+/* xor64 (Marsaglia's 64-bit xorshift, the generator of the Sec. 7
+ * measurements): x ^= x << 13; x ^= x >> 7; x ^= x << 17.  Returns the new
+ * state; the strategy word is its low 32 bits. */
+uint64_t orc_xor64_step(uint64_t x)
+{
+    x = x ^ (x << 13);
+    x = x ^ (x >> 7);
+    x = x ^ (x << 17);
+    return x;
+}
+
 /* BBS (Sec. 9.1): x_{n+1} = x_n^2 mod M, by the definition. */
 uint64_t orc_bbs_step(uint64_t y, uint64_t M)
 {
@@ -187,10 +201,11 @@ static uint64_t orc_gcd(uint64_t a, uint64_t b)
 /* ------------------------------------------------------------------------- */
 
 enum { ORC_VAR_XOR = 0, ORC_VAR_BBS = 1, ORC_VAR_BBS16 = 2 };
-enum { ORC_XL_XOR128 = 0, ORC_XL_XORSHIFT32 = 1 };
+enum { ORC_XL_XOR128 = 0, ORC_XL_XORSHIFT32 = 1, ORC_XL_XOR64 = 2 };
 
 typedef struct {
-    uint32_t w[4];   /* xor-like words: xor128 {a,b,c,d}; xorshift32 uses w[0] */
+    uint32_t w[4];   /* xor-like words: xor128 {a,b,c,d}; xorshift32 uses w[0];
+                        xor64 keeps its state as w[0] (low) and w[1] (high) */
     uint32_t x;      /* CI state x */
     uint32_t tprev;  /* the lane's last strategy (its shared-memory slot)     */
     uint32_t p, q;   /* BBS Blum primes                                      */
@@ -218,6 +233,11 @@ static void orc_init_xor_lane(int xl, uint64_t seed, uint64_t lane, orc_lane *L)
         L->w[2] = (uint32_t)d1;
         L->w[3] = (uint32_t)(d1 >> 32);
         if ((L->w[0] | L->w[1] | L->w[2] | L->w[3]) == 0)
+            L->w[0] = 1;
+    } else if (xl == ORC_XL_XOR64) {
+        L->w[0] = (uint32_t)d0;
+        L->w[1] = (uint32_t)(d0 >> 32);
+        if ((L->w[0] | L->w[1]) == 0)
             L->w[0] = 1;
     } else {
         L->w[0] = (uint32_t)d0;
@@ -529,6 +549,12 @@ int orc_run(int variant, int xl, uint32_t C, const uint8_t *comb, orc_lane *lane
                 sw[l] = orc_bbs16_strategy(&lanes[l]);
             } else if (xl == ORC_XL_XOR128) {
                 sw[l] = orc_xor128_step(lanes[l].w);
+            } else if (xl == ORC_XL_XOR64) {
+                uint64_t z = ((uint64_t)lanes[l].w[1] << 32) | lanes[l].w[0];
+                z = orc_xor64_step(z);
+                lanes[l].w[0] = (uint32_t)z;
+                lanes[l].w[1] = (uint32_t)(z >> 32);
+                sw[l] = (uint32_t)z;
             } else {
                 lanes[l].w[0] = orc_xorshift32_step(lanes[l].w[0]);
                 sw[l] = lanes[l].w[0];

@@ -7,6 +7,7 @@ import pytest
 # Prime factors of 2^32 - 1 and of 2^128 - 1 = F0 F1 F2 F3 F4 F5 F6 (Fermat numbers).
 PRIMES_2_32_M1 = [3, 5, 17, 257, 65537]
 PRIMES_2_128_M1 = [3, 5, 17, 257, 641, 65537, 274177, 6700417, 67280421310721]
+PRIMES_2_64_M1 = [3, 5, 17, 257, 641, 65537, 6700417]
 
 
 def _check_factorisations():
@@ -18,6 +19,10 @@ def _check_factorisations():
     for q in PRIMES_2_128_M1:
         p *= q
     assert p == 2**128 - 1
+    p = 1
+    for q in PRIMES_2_64_M1:
+        p *= q
+    assert p == 2**64 - 1
 
 
 def _gf2_matrix(step, nbits, nwords):
@@ -106,3 +111,35 @@ def test_xor128_linear(orc):
         sab, oab = orc.xor128_step(a ^ b)
         assert oab == oa ^ ob
         assert np.array_equal(sab, sa ^ sb)
+
+
+def test_xor64_full_period_gf2(orc):
+    """xor64 (the generator of the paper's Sec. 7 measurements) is GF(2)-linear
+    on 64 bits; full period 2^64 - 1 is the defining property of its shift
+    triple."""
+
+    def step(v):
+        z = orc.xor64_step(v[0] | (v[1] << 32))
+        return [z & 0xFFFFFFFF, z >> 32]
+
+    m = _gf2_matrix(step, 64, 2)
+    assert _has_full_period(m, 64, PRIMES_2_64_M1)
+    assert orc.xor64_step(0) == 0
+
+
+def test_xor64_strategy_is_low_word(orc):
+    """In Algorithm 4 the xor64 lane's own strategy is the low 32 bits of each
+    step: with the mixing cancelled (comb1 == comb2) a stream is the prefix XOR
+    of those words."""
+    C = 4
+    comb = np.array([1, 3, 0, 2, 1, 3, 0, 2], dtype=np.uint8)
+    lanes = orc.init_lanes(0, 2, 21, 0, C)
+    x0 = lanes["x"].copy()
+    z = [int(w[0]) | (int(w[1]) << 32) for w in lanes["w"]]
+    out, _ = orc.run(0, 2, C, comb, lanes, 30)
+    for l in range(C):
+        words = []
+        for _ in range(30):
+            z[l] = orc.xor64_step(z[l])
+            words.append(z[l] & 0xFFFFFFFF)
+        assert np.array_equal(out[l], np.bitwise_xor.accumulate(np.array(words, dtype=np.uint32)) ^ x0[l])
