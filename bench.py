@@ -17,7 +17,6 @@ from __future__ import annotations
 
 import argparse
 import ctypes
-import glob
 import hashlib
 import json
 import os
@@ -198,11 +197,15 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback", {}
 
 
+# Sources that define the written xor128 kernel (its device code and launch).
+KERNEL_SOURCES = ("ci_device.cuh", "ci_gen.cuh", "ci_gen_xor128.cu", "ci_internal.h", "ci_tune.h")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1112_5239_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode() + f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1112_5239_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -395,6 +398,8 @@ def main():
 
     if not args.no_extras:
         result["fused"] = bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
+        result["fused_xor64"] = bench_fused_xor64(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks,
+                                                  world)
         result["bbs"] = bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["bbs16"] = bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["e2e"] = bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
@@ -468,6 +473,30 @@ def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world,
             "workload": "BBS-driven CI PRNG (Alg. 5, 62-bit Blum moduli, 11 Montgomery squarings per output,"
                         " C=32, seed 3): 2^16 streams x 16384, written (4 GiB per launch)",
             "modsq_per_s": 11 * value}
+
+
+def bench_fused_xor64(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world):
+    """The same 2^20 x 4096 fused workload driven by xor64, the generator of the
+    paper's Sec. 7 measurement (storage removed, about 20 GS/s on GT200)."""
+    st = ci.States(S_MAIN, variant="xor", xl="xor64", comb_size=32, seed=SEED_MAIN, first_stream=first)
+    counts = torch.zeros(S_MAIN, dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        st.generate_fused_qc(L_MAIN, counts=counts)
+    barrier_sync()
+    evs = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.generate_fused_qc(L_MAIN, counts=counts)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.nvtx.range_pop()
+    barrier_sync()
+    ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
+    st.free()
+    return {"value": world * S_MAIN * L_MAIN / (ms / 1e3), "unit": "uint32/s", "ms_per_step": ms,
+            "workload": "2^20 x 4096, xor64 as the Algorithm 4 xor-like, outputs consumed by the quarter-circle counter"}
 
 
 def bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):

@@ -52,7 +52,7 @@ enum {
 
 /* --------------------------------------------------------------- params */
 enum { CI_VAR_XOR = 0, CI_VAR_BBS = 1, CI_VAR_BBS16 = 2 };  /* Alg. 4 / Alg. 5 / Alg. 5 as printed */
-enum { CI_XL_XOR128 = 0, CI_XL_XORSHIFT32 = 1 };   /* xor-like of Alg. 4    */
+enum { CI_XL_XOR128 = 0, CI_XL_XORSHIFT32 = 1, CI_XL_XOR64 = 2 };   /* xor-like of Alg. 4 */
 
 typedef struct {
     int32_t variant;      /* CI_VAR_XOR, CI_VAR_BBS (one 62-bit-modulus BBS per
@@ -63,8 +63,10 @@ typedef struct {
                              so its outputs depend on how a stream's length is
                              split into calls)                                */
     int32_t xl;           /* xor variant: CI_XL_XOR128 (the 32-bit xor128 the
-                             paper uses for Alg. 4, Sec. 6.2) or
-                             CI_XL_XORSHIFT32 (Alg. 2); ignored for BBS       */
+                             paper uses for Alg. 4, Sec. 6.2), CI_XL_XORSHIFT32
+                             (Alg. 2) or CI_XL_XOR64 (the 64-bit xorshift of the
+                             Sec. 7 measurements; strategy = low 32 bits of each
+                             step); ignored for BBS                           */
     uint32_t comb_size;   /* combination_size C of Alg. 4/5: 1, 2, 4, 8, 16 or
                              32; a group of C streams mixes within itself     */
     uint32_t flags;       /* reserved, must be 0                               */
@@ -374,7 +376,8 @@ ci_status ci_server_destroy(ci_server server);
  *   [0, 512)            partner table u8[16][32]: lane j of a warp mixes with
  *                       lanes table[a][j] (xor: a = 0, 1; BBS: a = sel1, 8+sel2)
  *   then 9 uint32 fields of P lanes each (field f at 512 + 4*f*P):
- *     0..3 xor-like words (xor128 a, b, c, d; XORshift z in field 0),
+ *     0..3 xor-like words (xor128 a, b, c, d; XORshift z in field 0; xor64
+ *       low word in field 0, high word in field 1),
  *     4 x, 5 slot (last strategy), 6 sel1 | sel2 << 8, 7 p, 8 q
  *   then (CI_VAR_BBS16 only) 16 more uint32 fields: 9..16 the states of
  *     BBS1..BBS8 (each < its modulus), 17..24 their moduli (>= 2, < 2^16);
@@ -405,10 +408,10 @@ typedef struct {
                                   not measured)                                    */
 } ci_tune_choice;
 
-/* choice[source][sink]: source 0 xor128, 1 XORshift32, 2 BBS, 3 BBS16; sink 0 written
+/* choice[source][sink]: source 0 xor128, 1 XORshift32, 2 BBS, 3 BBS16, 4 xor64; sink 0 written
  * 16-byte-aligned, 1 written unaligned, 2 quarter-circle, 3 digest. */
 typedef struct {
-    ci_tune_choice choice[4][4];
+    ci_tune_choice choice[5][4];
     uint32_t batch_warps_per_block;  /* batched persistent kernel (read when a
                                         ci_batch or ci_server is created)        */
     float batch_ms;

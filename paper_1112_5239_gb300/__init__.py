@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import CIError, ci_params, ci_states_desc
 
 VARIANTS = {"xor": _lib.CI_VAR_XOR, "bbs": _lib.CI_VAR_BBS, "bbs16": _lib.CI_VAR_BBS16}
-XORLIKES = {"xor128": _lib.CI_XL_XOR128, "xorshift32": _lib.CI_XL_XORSHIFT32}
+XORLIKES = {"xor128": _lib.CI_XL_XOR128, "xorshift32": _lib.CI_XL_XORSHIFT32, "xor64": _lib.CI_XL_XOR64}
 
 SINKS = {"written": _lib.CI_SINK_WRITTEN, "qc": _lib.CI_SINK_QC, "digest": _lib.CI_SINK_DIGEST}
 DIGEST_MUL = 0xD1342543DE82EF95
@@ -304,7 +304,7 @@ class Server:
             pass
 
 
-SOURCES = ("xor128", "xorshift32", "bbs", "bbs16")
+SOURCES = ("xor128", "xorshift32", "bbs", "bbs16", "xor64")
 SINK_CLASSES = ("written", "written_unaligned", "qc", "digest")
 
 

@@ -16,7 +16,7 @@ CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE = -1, -2,
 CI_VAR_XOR, CI_VAR_BBS, CI_VAR_BBS16 = 0, 1, 2
 CI_SINK_WRITTEN, CI_SINK_QC, CI_SINK_DIGEST = 0, 1, 2
 CI_NOALLOC_MAX_ITEMS = 1024
-CI_XL_XOR128, CI_XL_XORSHIFT32 = 0, 1
+CI_XL_XOR128, CI_XL_XORSHIFT32, CI_XL_XOR64 = 0, 1, 2
 
 STATUS_NAMES = {0: "CI_OK", 1: "CI_PENDING", -1: "CI_E_INVAL", -2: "CI_E_NOMEM", -3: "CI_E_CUDA",
                 -4: "CI_E_BUSY", -5: "CI_E_TIMEOUT", -6: "CI_E_STATE"}
@@ -110,7 +110,7 @@ class ci_tune_choice(ctypes.Structure):
 
 class ci_tune_table(ctypes.Structure):
     _fields_ = [
-        ("choice", (ci_tune_choice * 4) * 4),
+        ("choice", (ci_tune_choice * 4) * 5),
         ("batch_warps_per_block", ctypes.c_uint32),
         ("batch_ms", ctypes.c_float),
     ]

@@ -82,7 +82,7 @@ static ci_status check_params(const ci_params *p, uint64_t S) {
     if (!p) return fail(CI_E_INVAL, "params is NULL");
     if (p->variant != CI_VAR_XOR && p->variant != CI_VAR_BBS && p->variant != CI_VAR_BBS16)
         return fail(CI_E_INVAL, "unknown variant");
-    if (p->variant == CI_VAR_XOR && p->xl != CI_XL_XOR128 && p->xl != CI_XL_XORSHIFT32)
+    if (p->variant == CI_VAR_XOR && p->xl != CI_XL_XOR128 && p->xl != CI_XL_XORSHIFT32 && p->xl != CI_XL_XOR64)
         return fail(CI_E_INVAL, "unknown xor-like generator");
     const uint32_t C = p->comb_size;
     if (C < 1 || C > 32 || (C & (C - 1)) != 0) return fail(CI_E_INVAL, "comb_size must be 1, 2, 4, 8, 16 or 32");

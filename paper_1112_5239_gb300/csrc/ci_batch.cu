@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_batched(BatchHeader *hdr, const 
             run_sink<SrcBbs16>(T, g, tile);
         else if (T.kind == K_XS32)
             run_sink<SrcXorshift32>(T, g, tile);
+        else if (T.kind == K_XOR64)
+            run_sink<SrcXor64>(T, g, tile);
         else
             run_sink<SrcXor128>(T, g, tile);
     }
@@ -117,7 +119,7 @@ BatchTask make_task(const ci_states_s &h, uint64_t n, int sink_abi, uint32_t *ou
     t.ngroups = h.P / 32;
     t.kind = h.variant == CI_VAR_BBS     ? K_BBS
              : h.variant == CI_VAR_BBS16 ? K_BBS16
-             : (h.xl == CI_XL_XORSHIFT32 ? K_XS32 : K_XOR128);
+             : (h.xl == CI_XL_XORSHIFT32 ? K_XS32 : h.xl == CI_XL_XOR64 ? K_XOR64 : K_XOR128);
     if (sink_abi == CI_SINK_QC)
         t.sink = SINK_QC;
     else if (sink_abi == CI_SINK_DIGEST)

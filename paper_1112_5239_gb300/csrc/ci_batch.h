@@ -11,7 +11,7 @@
 namespace ci {
 
 // Source kinds of a task.
-enum TaskKind : uint32_t { K_XOR128 = 0, K_XS32 = 1, K_BBS = 2, K_BBS16 = 3 };
+enum TaskKind : uint32_t { K_XOR128 = 0, K_XS32 = 1, K_BBS = 2, K_BBS16 = 3, K_XOR64 = 4 };
 
 // One queue entry: warp groups [g0, g0 + ngroups) of one state, each advanced
 // by n iterations; written outputs of row r go to out[r * ld + col0 + i].

@@ -88,6 +88,30 @@ struct SrcXorshift32 {
     }
 };
 
+// xor64, the 64-bit xorshift of the paper's Sec. 7 measurements; the lane's
+// strategy word is the low 32 bits of each step.
+struct SrcXor64 {
+    static constexpr bool kHeavy = false;
+    uint64_t z;
+    __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
+        z = (uint64_t)s.u32[F_A * s.P + l] | ((uint64_t)s.u32[F_B * s.P + l] << 32);
+    }
+    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const {
+        s.u32[F_A * s.P + l] = (uint32_t)z;
+        s.u32[F_B * s.P + l] = (uint32_t)(z >> 32);
+    }
+    __device__ __forceinline__ void arrays(const DevState &, uint64_t, int &a1, int &a2) const {
+        a1 = 0;
+        a2 = 1;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        z ^= z << 13;
+        z ^= z >> 7;
+        z ^= z << 17;
+        return (uint32_t)z;
+    }
+};
+
 // ------------------------------------------------ Montgomery arithmetic
 // R = 2^64, M odd with 2^32 <= M < 2^62, Mp = -M^-1 mod R.  Values are kept
 // "lazy" in [0, 2M): for a, b < 2M, a*b < 4M^2 < M R (as 4M < R), so

@@ -45,6 +45,10 @@ __device__ __forceinline__ void init_xor_lane(const DevState &st, uint64_t seed,
         c = (uint32_t)d1;
         d = (uint32_t)(d1 >> 32);
         if ((a | b | c | d) == 0u) a = 1u;
+    } else if (xl == CI_XL_XOR64) {
+        a = (uint32_t)d0;
+        b = (uint32_t)(d0 >> 32);
+        if ((a | b) == 0u) a = 1u;
     } else {
         a = (uint32_t)d0;
         if (a == 0u) a = 1u;
@@ -300,12 +304,14 @@ cudaError_t launch_with(const ci_states_s &h, int sink, const TuneChoice &c, uin
     if (h.variant == CI_VAR_BBS) return gen_bbs(sink, c, st, n, out, counts, stream);
     if (h.variant == CI_VAR_BBS16) return gen_bbs16(sink, c, st, n, out, counts, stream);
     if (h.xl == CI_XL_XORSHIFT32) return gen_xs32(sink, c, st, n, out, counts, stream);
+    if (h.xl == CI_XL_XOR64) return gen_xor64(sink, c, st, n, out, counts, stream);
     return gen_xor128(sink, c, st, n, out, counts, stream);
 }
 
 static int src_kind(const ci_states_s &h) {
     if (h.variant == CI_VAR_BBS16) return SK_BBS16;
-    return h.variant == CI_VAR_BBS ? SK_BBS : (h.xl == CI_XL_XORSHIFT32 ? SK_XS32 : SK_XOR128);
+    if (h.variant == CI_VAR_BBS) return SK_BBS;
+    return h.xl == CI_XL_XORSHIFT32 ? SK_XS32 : h.xl == CI_XL_XOR64 ? SK_XOR64 : SK_XOR128;
 }
 
 cudaError_t launch_generate(const ci_states_s &h, uint64_t n, uint32_t *out, cudaStream_t stream) {

@@ -46,7 +46,7 @@ static bool valid_choice(int src, int sink, const ci_tune_choice &c) {
     if (c.warps_per_block != 4 && c.warps_per_block != 8 && c.warps_per_block != 16) return false;
     if (c.cache_policy > 2) return false;
     if (c.tile_depth != 32 && c.tile_depth != 64) return false;
-    const bool xor_src = src == SK_XOR128 || src == SK_XS32;
+    const bool xor_src = src == SK_XOR128 || src == SK_XS32 || src == SK_XOR64;
     if (c.tile_depth == 64 && !(sink == dev::SINK_V4 && xor_src)) return false;
     if (c.cache_policy == 1 && sink != dev::SINK_V4) return false;
     if (c.cache_policy == 2 && !(sink == dev::SINK_V4 && xor_src && c.tile_depth == 32)) return false;
@@ -132,12 +132,12 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out) {
     std::memset(&p, 0, sizeof p);
     p.comb_size = 32;
     p.seed = 12345;
-    ci_states hs[kSrcKinds] = {nullptr, nullptr, nullptr, nullptr};
-    const uint64_t S_of[kSrcKinds] = {S_xor, S_xor, S_bbs, S_bbs};
+    ci_states hs[kSrcKinds] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    const uint64_t S_of[kSrcKinds] = {S_xor, S_xor, S_bbs, S_bbs, S_xor};
     ci_status rc = CI_OK;
     for (int s = 0; s < kSrcKinds && rc == CI_OK; ++s) {
         p.variant = s == SK_BBS ? CI_VAR_BBS : (s == SK_BBS16 ? CI_VAR_BBS16 : CI_VAR_XOR);
-        p.xl = s == SK_XS32 ? CI_XL_XORSHIFT32 : CI_XL_XOR128;
+        p.xl = s == SK_XS32 ? CI_XL_XORSHIFT32 : s == SK_XOR64 ? CI_XL_XOR64 : CI_XL_XOR128;
         rc = ci_init_states(&p, S_of[s], cuda_stream, &hs[s]);
     }
     uint32_t *out_dev = nullptr;
@@ -148,7 +148,8 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out) {
     if (rc == CI_OK && e != cudaSuccess) rc = cuda_fail(e, "autotuner buffers");
     for (int s = 0; s < kSrcKinds && rc == CI_OK; ++s) {
         for (int k = 0; k < 4 && rc == CI_OK; ++k) {
-            const uint64_t L = s >= SK_BBS ? L_bbs : (k <= dev::SINK_SCALAR ? L_written : L_fused);
+            const bool bbs_src = s == SK_BBS || s == SK_BBS16;
+            const uint64_t L = bbs_src ? L_bbs : (k <= dev::SINK_SCALAR ? L_written : L_fused);
             // the unaligned written sink runs on an output offset by one word
             uint32_t *o = k == dev::SINK_SCALAR ? out_dev + 1 : out_dev;
             float best = 1e30f;

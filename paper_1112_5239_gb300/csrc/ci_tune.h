@@ -16,8 +16,8 @@ struct TuneChoice {
     uint32_t cache_policy;     // written sinks: 0 streaming (evict-first) stores, 1 write-back
 };
 
-enum SrcKind { SK_XOR128 = 0, SK_XS32 = 1, SK_BBS = 2, SK_BBS16 = 3 };
-constexpr int kSrcKinds = 4;
+enum SrcKind { SK_XOR128 = 0, SK_XS32 = 1, SK_BBS = 2, SK_BBS16 = 3, SK_XOR64 = 4 };
+constexpr int kSrcKinds = 5;
 
 // Current choice for a (source kind, SINK_*) pair.
 TuneChoice tuned(int src, int sink);
@@ -30,6 +30,8 @@ cudaError_t gen_xs32(int sink, const TuneChoice &c, const DevState &st, uint64_t
                      uint64_t *counts, cudaStream_t stream);
 cudaError_t gen_bbs(int sink, const TuneChoice &c, const DevState &st, uint64_t n, uint32_t *out,
                     uint64_t *counts, cudaStream_t stream);
+cudaError_t gen_xor64(int sink, const TuneChoice &c, const DevState &st, uint64_t n, uint32_t *out,
+                      uint64_t *counts, cudaStream_t stream);
 cudaError_t gen_bbs16(int sink, const TuneChoice &c, const DevState &st, uint64_t n, uint32_t *out,
                       uint64_t *counts, cudaStream_t stream);
 

@@ -6,7 +6,7 @@ import pytest
 import oracle
 
 VAR = {"xor": 0, "bbs": 1, "bbs16": 2}
-XL = {"xor128": 0, "xorshift32": 1}
+XL = {"xor128": 0, "xorshift32": 1, "xor64": 2}
 
 
 def cuda_or_skip():

@@ -38,7 +38,7 @@ def test_plain_4096x1024_full(env):
 SHAPES = [(1, 1), (5, 3), (31, 32), (32, 33), (33, 64), (100, 31), (257, 129), (64, 100), (40, 4)]
 
 
-@pytest.mark.parametrize("xl", ["xor128", "xorshift32"])
+@pytest.mark.parametrize("xl", ["xor128", "xorshift32", "xor64"])
 @pytest.mark.parametrize("C", [1, 2, 4, 8, 16, 32])
 def test_small_shapes_xor(env, xl, C):
     torch, ci = env
@@ -72,7 +72,8 @@ def test_guard_words_untouched(env):
     assert np.all(u32(buf[S * L:]) == 12345)
 
 
-@pytest.mark.parametrize("variant,xl", [("xor", "xor128"), ("xor", "xorshift32"), ("bbs", "xor128")])
+@pytest.mark.parametrize("variant,xl", [("xor", "xor128"), ("xor", "xorshift32"), ("xor", "xor64"),
+                                        ("bbs", "xor128")])
 def test_continuation_any_split(env, variant, xl):
     torch, ci = env
     S = 96

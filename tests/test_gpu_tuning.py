@@ -20,22 +20,22 @@ def _shapes(src, sink):
     for w in (4, 8, 16):
         for kt in (32, 64):
             for cp in (0, 1, 2):
-                if kt == 64 and not (sink == "written" and src in ("xor128", "xorshift32")):
+                if kt == 64 and not (sink == "written" and src in ("xor128", "xorshift32", "xor64")):
                     continue
                 if cp == 1 and sink != "written":
                     continue
-                if cp == 2 and not (sink == "written" and src in ("xor128", "xorshift32") and kt == 32):
+                if cp == 2 and not (sink == "written" and src in ("xor128", "xorshift32", "xor64") and kt == 32):
                     continue
                 out.append({"warps_per_block": w, "tile_depth": kt, "cache_policy": cp})
     return out
 
 
-@pytest.mark.parametrize("src", ["xor128", "xorshift32", "bbs", "bbs16"])
+@pytest.mark.parametrize("src", ["xor128", "xorshift32", "bbs", "bbs16", "xor64"])
 def test_every_launch_shape_matches_oracle(env, src):
     torch, ci = env
     base = ci.tune_table()
     variant = src if src in ("bbs", "bbs16") else "xor"
-    xl = "xorshift32" if src == "xorshift32" else "xor128"
+    xl = src if src in ("xorshift32", "xor64") else "xor128"
     S, L = 1000, 200  # 32 warp groups (several blocks) and a ragged tail of the 64-deep tile
     ref_orc = oracle_gen(variant, xl, 32, 31, 0, S)
     ref = ref_orc.streams(L)
