@@ -88,6 +88,9 @@ def lib() -> ctypes.CDLL:
             "orc_mix_ci_fed": (None, [u64, u64, vp, vp, vp, vp, vp, vp]),
             "orc_run": (i32, [i32, i32, u32, vp, vp, u64, u64, vp, vp]),
             "orc_bbs16_strategy": (u32, [vp]),
+            "orc_bg_encrypt": (u32, [u64, u32, u64, u64, vp, vp, vp]),
+            "orc_bg_recover_x0": (u64, [u64, u64, u64, u64]),
+            "orc_bg_decrypt": (None, [u64, u64, u32, u64, u64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -176,6 +179,26 @@ def mix_ci_fed(xl: np.ndarray, part1, part2, x0, tprev0):
     out = np.zeros((nl, L), dtype=np.uint32)
     lib().orc_mix_ci_fed(nl, L, _ptr(xl), _ptr(p1), _ptr(p2), _ptr(x), _ptr(tp), _ptr(out))
     return out, x, tp
+
+
+def bg_encrypt(N: int, S0: int, r: int, m: np.ndarray):
+    """Chaotic Blum-Goldwasser encryption (Sec. 9.2): returns (c, y, w)."""
+    m = np.ascontiguousarray(m, dtype=np.uint8)
+    c = np.zeros_like(m)
+    y = np.zeros(1, dtype=np.uint64)
+    w = int(lib().orc_bg_encrypt(N, S0, r, m.size, _ptr(m), _ptr(c), _ptr(y)))
+    return c, int(y[0]), w
+
+
+def bg_recover_x0(p: int, q: int, y: int, L: int) -> int:
+    return int(lib().orc_bg_recover_x0(p, q, y, L))
+
+
+def bg_decrypt(p: int, q: int, S0: int, y: int, c: np.ndarray) -> np.ndarray:
+    c = np.ascontiguousarray(c, dtype=np.uint8)
+    m = np.zeros_like(c)
+    lib().orc_bg_decrypt(p, q, S0, y, c.size, _ptr(c), _ptr(m))
+    return m
 
 
 # ---------------------------------------------------------------- generator

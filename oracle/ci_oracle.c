@@ -27,6 +27,7 @@
  *   Algorithm 5 (16 combination arrays, selection
  *     from the BBS state's low bits) ............... orc_run (BBS variant)
  *   Quarter-circle consumer of output pairs ......... orc_run (counts)
+ *   Chaotic Blum-Goldwasser (Sec. 9.2) ............ orc_bg_encrypt, orc_bg_decrypt
  *   Algorithm 5 as printed (8 BBS generators per
  *     thread, 16-bit moduli, 4 bits per squaring,
  *     arrays chosen per call, rotation on store) ... orc_run (variant 2)
@@ -590,4 +591,90 @@ int orc_run(int variant, int xl, uint32_t C, const uint8_t *comb, orc_lane *lane
     free(sw);
     free(held);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Chaotic Blum-Goldwasser (Sec. 9.2): Blum-Goldwasser whose keystream is    */
+/* Eq. (Oplus) applied to the BBS bits, i.e. k_i = S0 ^ b_0 ^ ... ^ b_i.     */
+/* ------------------------------------------------------------------------- */
+
+static uint64_t orc_mulmod(uint64_t a, uint64_t b, uint64_t m)
+{
+    return (uint64_t)(((unsigned __int128)a * b) % m);
+}
+
+static uint64_t orc_powmod(uint64_t a, uint64_t e, uint64_t m)
+{
+    uint64_t r = 1 % m;
+    a %= m;
+    while (e) {
+        if (e & 1)
+            r = orc_mulmod(r, a, m);
+        a = orc_mulmod(a, a, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+/* Inverse of a modulo m (gcd(a, m) = 1) by the extended Euclidean algorithm. */
+static uint64_t orc_invmod(uint64_t a, uint64_t m)
+{
+    __int128 t = 0, nt = 1, r = (__int128)m, nr = (__int128)(a % m);
+    while (nr != 0) {
+        __int128 q = r / nr, tmp;
+        tmp = t - q * nt; t = nt; nt = tmp;
+        tmp = r - q * nr; r = nr; nr = tmp;
+    }
+    if (t < 0)
+        t += m;
+    return (uint64_t)t;
+}
+
+/* Encryption by Bob: x_0 = r^2 mod N; for i = 0 .. L-1: b_i = the w low bits
+ * of x_i (w = floor(log2(floor(log2 N)))), c_i = m_i ^ (S0 ^ b_0 ^ ... ^ b_i),
+ * x_{i+1} = x_i^2 mod N; the ciphertext is (c, y = x_L).  Returns w. */
+uint32_t orc_bg_encrypt(uint64_t N, uint32_t S0, uint64_t r, uint64_t L, const uint8_t *m, uint8_t *c,
+                        uint64_t *y)
+{
+    const uint32_t w = orc_bbs_w(N);
+    const uint64_t mask = (1ULL << w) - 1;
+    uint64_t x = orc_mulmod(r, r, N);
+    uint32_t k = S0;
+    for (uint64_t i = 0; i < L; ++i) {
+        k ^= (uint32_t)(x & mask);
+        c[i] = (uint8_t)(m[i] ^ k);
+        x = orc_bbs_step(x, N);
+    }
+    *y = x;
+    return w;
+}
+
+/* Alice's recovery of x_0 from y = x_0^(2^L) mod N with p = q = 3 mod 4:
+ * r_p = y^(((p+1)/4)^L) mod p, r_q likewise (exponents reduced mod p - 1,
+ * q - 1), x_0 = q (q^-1 mod p) r_p + p (p^-1 mod q) r_q mod N. */
+uint64_t orc_bg_recover_x0(uint64_t p, uint64_t q, uint64_t y, uint64_t L)
+{
+    const uint64_t N = p * q;
+    const uint64_t ep = orc_powmod((p + 1) / 4, L, p - 1);
+    const uint64_t eq = orc_powmod((q + 1) / 4, L, q - 1);
+    const uint64_t rp = orc_powmod(y % p, ep, p);
+    const uint64_t rq = orc_powmod(y % q, eq, q);
+    const uint64_t a = orc_mulmod(orc_mulmod(q, orc_invmod(q % p, p), N), rp, N);
+    const uint64_t b = orc_mulmod(orc_mulmod(p, orc_invmod(p % q, q), N), rq, N);
+    return (a + b) % N;
+}
+
+/* Decryption by Alice: recover x_0, regenerate b_i and the keystream
+ * k_i = S0 ^ b_0 ^ ... ^ b_i, m_i = c_i ^ k_i. */
+void orc_bg_decrypt(uint64_t p, uint64_t q, uint32_t S0, uint64_t y, uint64_t L, const uint8_t *c, uint8_t *m)
+{
+    const uint64_t N = p * q;
+    const uint64_t mask = (1ULL << orc_bbs_w(N)) - 1;
+    uint64_t x = orc_bg_recover_x0(p, q, y, L);
+    uint32_t k = S0;
+    for (uint64_t i = 0; i < L; ++i) {
+        k ^= (uint32_t)(x & mask);
+        m[i] = (uint8_t)(c[i] ^ k);
+        x = orc_bbs_step(x, N);
+    }
 }
