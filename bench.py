@@ -6,8 +6,9 @@ the xor128-driven generator with Algorithm 4 mixing (C = 32, seed 2), written
 to HBM as 16 time chunks of 256 outputs per stream (1 GiB per launch).
 Alongside: the same workload fused into the quarter-circle consumer (no
 stores), the BBS-driven secure variant on 2^16 streams x 16384, the
-end-to-end figure through the public API with host buffers, and the CPU
-oracle timed on the host cores.
+end-to-end figure through the public API with host buffers, the chaotic
+Blum-Goldwasser cryptosystem (Sec. 9.2) on 2^20 messages x 1024 chunks, and
+the CPU oracle timed on the host cores.
 
 Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): each rank generates its
 own slice of a global stream range (first_stream = rank * 2^20), no exchange;
@@ -34,6 +35,7 @@ METRIC = "uint32/s on 1 GB300 (written & fused) vs HBM roofline; batched vs per-
 S_MAIN, L_MAIN, CHUNK = 1 << 20, 1 << 12, 256
 SEED_MAIN = 2
 S_BBS, L_BBS, SEED_BBS = 1 << 16, 1 << 14, 3
+SEED_BG = 6
 STATE_BYTES_PER_LANE_XOR128 = 24      # a, b, c, d, x, slot: read once and written once per launch
 FALLBACK_HBM_GBS = 6800.0
 GPU_SM_COUNT_NOMINAL = 152
@@ -52,7 +54,7 @@ def parse_args():
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
-    ap.add_argument("--profile", choices=["written", "fused", "bbs", "batched"], default=None,
+    ap.add_argument("--profile", choices=["written", "fused", "bbs", "batched", "bg"], default=None,
                     help="small case for ncu: autotune, 2 warm-up launches, then 1 launch of one kernel inside "
                          "the NVTX range 'profile'; no timing")
     return ap.parse_args()
@@ -84,6 +86,15 @@ def run_profile_case(kind: str) -> None:
         st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
         run = lambda: st.generate(1024, out=out)  # noqa: E731
+    elif kind == "bg":  # chaotic Blum-Goldwasser encryption, 2^18 messages x 1024 chunks (256 MiB each way)
+        from paper_1112_5239_gb300 import workloads as W
+
+        b = W.bg_batch(SEED_BG, 1 << 18)
+        N, r = torch.from_numpy(b["N"]).cuda(), torch.from_numpy(b["r"]).cuda()
+        S0 = torch.from_numpy(b["S0"]).cuda()
+        msg = torch.randint(0, 32, (1 << 18, 1024), dtype=torch.uint8, device="cuda")
+        c, y = torch.empty_like(msg), torch.empty(1 << 18, dtype=torch.int64, device="cuda")
+        run = lambda: ci.bg_encrypt(N, S0, r, msg, out=c, y=y)  # noqa: E731
     else:  # batched: 300 uneven requests (lengths up to 2^12), digest sink, one launch
         from paper_1112_5239_gb300.workloads import batched_requests
 
@@ -403,6 +414,7 @@ def main():
         result["bbs"] = bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["bbs16"] = bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["e2e"] = bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
+        result["bg"] = bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         if rank == 0 and world == 1:
             r, n, dt = oracle_sample(args.cpu_sample_streams)
             result["cpu_baseline"] = {"value": r, "unit": "uint32/s", "cores": 1, "kind": "oracle",
@@ -470,7 +482,7 @@ def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world,
     del out
     st.free()
     return {"value": value, "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
-            "workload": "BBS-driven CI PRNG (Alg. 5, 62-bit Blum moduli, 11 Montgomery squarings per output,"
+            "workload": "BBS-driven CI PRNG (Alg. 5, 62-bit Blum moduli, 11 Barrett squarings per output,"
                         " C=32, seed 3): 2^16 streams x 16384, written (4 GiB per launch)",
             "modsq_per_s": 11 * value}
 
@@ -526,6 +538,59 @@ def bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, worl
             "workload": "Algorithm 5 as printed (8 BBS per stream, Blum primes in [128, 256), 4 bits per squaring, "
                         "12 squarings per output, C=32, seed 3): 2^16 streams x 16384, written",
             "modsq_per_s": 12 * value}
+
+
+def bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):
+    """Chaotic Blum-Goldwasser (Sec. 9.2): encryption and decryption of 2^20
+    messages x 1024 five-bit chunks (one per byte, 1 GiB each way), keys from a
+    pool of 4096 recipients with 62-bit moduli, inputs resident in HBM."""
+    from paper_1112_5239_gb300 import workloads as W
+
+    n, L = W.BG_2E20x1024
+    b = W.bg_batch(SEED_BG + 1000 * rank, n)
+    key = {k: torch.from_numpy(v).to(dev) for k, v in b.items()}
+    g = torch.Generator(device=dev)
+    g.manual_seed(SEED_BG + 1000 * rank)
+    msg = torch.randint(0, 32, (n, L), dtype=torch.uint8, device=dev, generator=g)
+    cipher, back = torch.empty_like(msg), torch.empty_like(msg)
+    y = torch.empty(n, dtype=torch.int64, device=dev)
+    steps = max(1, min(args.steps, 10))
+
+    def enc():
+        ci.bg_encrypt(key["N"], key["S0"], key["r"], msg, out=cipher, y=y)
+
+    def dec():
+        ci.bg_decrypt(key["p"], key["q"], key["S0"], y, cipher, out=back)
+
+    for _ in range(max(3, min(args.warmup, 5))):
+        enc()
+        dec()
+    barrier_sync()
+    ev_e, ev_d = [], []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        evs[0].record(stream)
+        enc()
+        evs[1].record(stream)
+        dec()
+        evs[2].record(stream)
+        ev_e.append((evs[0], evs[1]))
+        ev_d.append((evs[1], evs[2]))
+    torch.cuda.nvtx.range_pop()
+    barrier_sync()
+    ms_e = max_over_ranks(statistics.mean(a.elapsed_time(b_) for a, b_ in ev_e))
+    ms_d = max_over_ranks(statistics.mean(a.elapsed_time(b_) for a, b_ in ev_d))
+    ok = bool(torch.equal(back, msg))
+    del msg, cipher, back
+    chunks = world * n * L
+    return {"unit": "chunks/s", "bits_per_chunk": 5,
+            "encrypt": {"value": chunks / (ms_e / 1e3), "ms_per_step": ms_e},
+            "decrypt": {"value": chunks / (ms_d / 1e3), "ms_per_step": ms_d},
+            "steps": steps, "round_trip_ok": ok,
+            "workload": "2^20 messages x 1024 chunks (w = 5 bits each, one per byte), 62-bit Blum moduli from a "
+                        "pool of 4096 keys, seed %d; one Barrett squaring per chunk" % SEED_BG,
+            "modsq_per_s": {"encrypt": chunks / (ms_e / 1e3), "decrypt": chunks / (ms_d / 1e3)}}
 
 
 def bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world):

@@ -11,7 +11,9 @@
  *     size combination_size; the result is the strategy S^n;
  *   - Algorithm 5 (Sec. 9.1): the secure variant, whose own word is assembled
  *     from the low bits of a Blum Blum Shub generator x_{k+1} = x_k^2 mod M,
- *     with sixteen combination arrays of which each stream uses two.
+ *     with sixteen combination arrays of which each stream uses two;
+ *   - Sec. 9.2: the chaotic Blum-Goldwasser cryptosystem built on the same
+ *     BBS iteration and Eq. (Oplus) (ci_bg_encrypt / ci_bg_decrypt).
  *
  * Conventions shared by every call:
  *   - Every function returns a ci_status; nothing throws across the ABI.
@@ -166,7 +168,7 @@ ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev
  * word takes ceil(32/w) BBS outputs' low w bits (w = floor(log2 log2 M) = 5
  * for these 62-bit moduli), then twice: shift = BBS & 3; t <<= shift;
  * t |= BBS & {0,1,3,7}[shift] -- 11 modular squarings per output, done with
- * 64x64->128-bit multiplies and Montgomery reduction.  The stream's two
+ * 64x64->128-bit multiplies and Barrett reduction.  The stream's two
  * combination arrays are comb[sel1] and comb[8 + sel2] with sel1 = v & 7,
  * sel2 = (v >> 3) & 7 of its BBS seed v.  Errors as ci_generate
  * (CI_E_STATE for an xor handle). */
@@ -381,10 +383,11 @@ ci_status ci_server_destroy(ci_server server);
  *     4 x, 5 slot (last strategy), 6 sel1 | sel2 << 8, 7 p, 8 q
  *   then (CI_VAR_BBS16 only) 16 more uint32 fields: 9..16 the states of
  *     BBS1..BBS8 (each < its modulus), 17..24 their moduli (>= 2, < 2^16);
- *   then (CI_VAR_BBS only) 4 uint64 fields of P lanes: 0 y (canonical
- *     residue, BBS state), 1 M, 2 -M^-1 mod 2^64, 3 2^128 mod M.
+ *   then (CI_VAR_BBS only) 3 uint64 fields of P lanes: 0 y (canonical
+ *     residue, BBS state), 1 M (odd, bit length n <= 62), 2 the Barrett
+ *     reciprocal floor(2^(2n) / M) << (63 - n).
  * Importing replaces the state of a handle with the same parameters and
- * n_streams; an imported BBS state must hold y < 2^64 and the constants of M.
+ * n_streams; an imported BBS state must hold y < M and the reciprocal of M.
  * Errors: CI_E_INVAL (size mismatch), CI_E_CUDA. */
 ci_status ci_export_state(ci_states states, void *host_buf, uint64_t bytes, void *cuda_stream);
 ci_status ci_import_state(ci_states states, const void *host_buf, uint64_t bytes,
@@ -430,6 +433,46 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out);
  * ci_tune_set rejects shapes not allowed for their class (CI_E_INVAL). */
 ci_status ci_tune_get(ci_tune_table *out);
 ci_status ci_tune_set(const ci_tune_table *in);
+
+/* ------------------------------------------- chaotic Blum-Goldwasser */
+
+/* The chaotic Blum-Goldwasser cryptosystem of Sec. 9.2: Blum-Goldwasser
+ * whose keystream is Eq. (Oplus) iterated on the BBS bits.  n_msgs messages of
+ * n_chunks chunks each, every message under its own key; per message i:
+ *   x_0 = r^2 mod N;  for k = 0 .. n_chunks-1:
+ *     b_k = x_k & (2^w - 1), w = floor(log2 floor(log2 N)) (w = 5 for
+ *     2^32 <= N < 2^62),
+ *     key_k = S0 ^ b_0 ^ ... ^ b_k,  c_k = m_k ^ key_k,  x_{k+1} = x_k^2 mod N;
+ *   y = x_{n_chunks}.
+ * Layout (device memory, caller-owned): msg_dev / cipher_dev are uint8,
+ * message-major: chunk k of message i at [i * n_chunks + k]; one chunk per
+ * byte, its low w bits carrying the message (higher bits pass through the XOR
+ * unchanged, as do S0's).  N_dev, r_dev, y_dev: uint64[n_msgs]; S0_dev:
+ * uint8[n_msgs] (the paper's S^0, normally < 2^w).  cipher_dev may equal
+ * msg_dev (in place).  Requirements: N odd with 3 <= N < 2^62 (else the
+ * message is REJECTED: its ciphertext row and y are written as zeros), N the
+ * product of two primes = 3 mod 4 and gcd(r, N) = 1 for the ciphertext to be
+ * decryptable (not checkable without the factors).  n_rejected_dev (uint32,
+ * may be NULL) is INCREMENTED by the number of rejected messages.
+ * Asynchronous on cuda_stream.  n_msgs == 0 is a no-op; n_chunks == 0 still
+ * writes y = r^2 mod N.
+ * Errors: CI_E_INVAL (a null array, n_msgs * n_chunks overflowing), CI_E_CUDA. */
+ci_status ci_bg_encrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *N_dev, const uint8_t *S0_dev,
+                        const uint64_t *r_dev, const uint8_t *msg_dev, uint8_t *cipher_dev, uint64_t *y_dev,
+                        uint32_t *n_rejected_dev, void *cuda_stream);
+
+/* Decryption (Sec. 9.2) with the private key (p, q), N = p q: x_0 is the
+ * square root of y taken n_chunks times, by y^(((p+1)/4)^n_chunks) mod p and
+ * likewise mod q, joined by the Chinese remainder theorem; then the keystream
+ * of ci_bg_encrypt is regenerated and m_k = c_k ^ key_k.  p_dev, q_dev, y_dev:
+ * uint64[n_msgs]; S0_dev, cipher_dev, msg_dev as for encryption (msg_dev may
+ * equal cipher_dev).  A key is REJECTED (message row written as zeros,
+ * n_rejected_dev incremented) unless p != q are primes = 3 mod 4 below 2^32
+ * with p q < 2^62 (primality by Miller-Rabin with bases 2, 7, 61, exact there).
+ * n_msgs == 0 or n_chunks == 0 is a no-op.  Errors as ci_bg_encrypt. */
+ci_status ci_bg_decrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *p_dev, const uint64_t *q_dev,
+                        const uint8_t *S0_dev, const uint64_t *y_dev, const uint8_t *cipher_dev, uint8_t *msg_dev,
+                        uint32_t *n_rejected_dev, void *cuda_stream);
 
 /* --------------------------------------------------------------- misc */
 

@@ -365,6 +365,51 @@ def batch_run_noalloc(items, stream=None) -> None:
     _lib.call("ci_batch_run_noalloc", ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
 
 
+def _bg_check(name, t, dtype, numel):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA tensor" % name)
+    if t.dtype != dtype or t.numel() != numel:
+        raise ValueError("%s must be %s with %d elements" % (name, dtype, numel))
+    return t.data_ptr()
+
+
+def bg_encrypt(N, S0, r, msg, out=None, y=None, rejected=None, stream=None):
+    """Chaotic Blum-Goldwasser encryption (Sec. 9.2) of a batch of messages.
+
+    ``msg`` is uint8 (n_msgs, n_chunks), one w-bit chunk per byte; ``N`` and
+    ``r`` int64 (n_msgs,) (bit patterns of the uint64 keys and seeds), ``S0``
+    uint8 (n_msgs,).  Returns (cipher uint8 like msg, y int64 (n_msgs,)).
+    ``rejected`` (int32 (1,), optional) is incremented by the number of
+    rejected keys."""
+    n_msgs, n_chunks = msg.shape
+    if out is None:
+        out = torch.empty_like(msg)
+    if y is None:
+        y = torch.empty(n_msgs, dtype=torch.int64, device=msg.device)
+    _lib.call("ci_bg_encrypt", n_msgs, n_chunks, _bg_check("N", N, torch.int64, n_msgs),
+              _bg_check("S0", S0, torch.uint8, n_msgs), _bg_check("r", r, torch.int64, n_msgs),
+              _bg_check("msg", msg, torch.uint8, n_msgs * n_chunks),
+              _bg_check("out", out, torch.uint8, n_msgs * n_chunks), _bg_check("y", y, torch.int64, n_msgs),
+              _bg_check("rejected", rejected, torch.int32, 1) if rejected is not None else None,
+              stream_ptr(stream))
+    return out, y
+
+
+def bg_decrypt(p, q, S0, y, cipher, out=None, rejected=None, stream=None):
+    """Chaotic Blum-Goldwasser decryption (Sec. 9.2) with the factors p, q
+    (int64 (n_msgs,)) of each message's N; returns the uint8 messages."""
+    n_msgs, n_chunks = cipher.shape
+    if out is None:
+        out = torch.empty_like(cipher)
+    _lib.call("ci_bg_decrypt", n_msgs, n_chunks, _bg_check("p", p, torch.int64, n_msgs),
+              _bg_check("q", q, torch.int64, n_msgs), _bg_check("S0", S0, torch.uint8, n_msgs),
+              _bg_check("y", y, torch.int64, n_msgs), _bg_check("cipher", cipher, torch.uint8, n_msgs * n_chunks),
+              _bg_check("out", out, torch.uint8, n_msgs * n_chunks),
+              _bg_check("rejected", rejected, torch.int32, 1) if rejected is not None else None,
+              stream_ptr(stream))
+    return out
+
+
 def unpack_state(buf: np.ndarray, n_lanes: int, variant: int) -> dict:
     """Splits an exported state into its documented fields."""
     P = int(n_lanes)
@@ -375,6 +420,6 @@ def unpack_state(buf: np.ndarray, n_lanes: int, variant: int) -> dict:
     if variant == _lib.CI_VAR_BBS16:
         out.update({"y16": u32[9:17].T, "m16": u32[17:25].T})
     if variant == _lib.CI_VAR_BBS:
-        u64 = buf[512 + 36 * P:512 + 36 * P + 32 * P].view(np.uint64).reshape(4, P)
-        out.update({"y": u64[0], "M": u64[1], "Mp": u64[2], "r2": u64[3]})
+        u64 = buf[512 + 36 * P:512 + 36 * P + 24 * P].view(np.uint64).reshape(3, P)
+        out.update({"y": u64[0], "M": u64[1], "mu": u64[2]})
     return out

@@ -100,7 +100,7 @@ BatchGeometry batch_geometry(int warps_per_block) {
 }
 
 double kind_cost(uint32_t kind) {
-    // measured ratios of per-output cost (BBS: 11 Montgomery squarings per
+    // measured ratios of per-output cost (BBS: 11 Barrett squarings per
     // output; BBS16: 12 32-bit Barrett squarings)
     return kind == K_BBS ? 40.0 : kind == K_BBS16 ? 8.0 : 1.0;
 }

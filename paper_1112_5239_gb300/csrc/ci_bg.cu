@@ -1,0 +1,199 @@
+// ci_bg.cu -- the chaotic Blum-Goldwasser cryptosystem of Sec. 9.2 on the
+// device (include/ci_prng.h: ci_bg_encrypt, ci_bg_decrypt).
+//
+// Per message: x_0 = r^2 mod N, b_i = the w low bits of x_i
+// (w = floor(log2 floor(log2 N))), x_{i+1} = x_i^2 mod N.  The keystream is
+// Eq. (Oplus) run on the b_i from S^0: k_i = S^0 ^ b_0 ^ ... ^ b_i, and
+// chunk i of the ciphertext is c_i = m_i ^ k_i; the ciphertext carries
+// y = x_L.  Decryption recovers x_0 from y with the factors p, q = 3 mod 4
+// (square roots by the exponent ((p + 1) / 4)^L, joined by Garner's CRT) and
+// regenerates the same keystream.
+//
+// One lane owns one message; a warp owns 32 consecutive messages and moves
+// their chunks (one byte each, message-major) through a warp-private 32 x 32
+// byte tile in shared memory, so global loads and stores are 32-byte rows
+// while each lane walks its own row.  The squarings use the Barrett
+// reduction of the BBS strategy source (modulus odd, below 2^62), which keeps
+// x_i canonical so its low bits are read directly.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "ci_device.cuh"
+#include "ci_internal.h"
+#include "ci_modarith.cuh"
+
+namespace ci {
+namespace {
+
+using namespace dev;
+
+#ifndef CI_BG_MIN_BLOCKS
+#define CI_BG_MIN_BLOCKS 6  // resident blocks per SM asked of the register allocator: 40 registers,
+                            // no spills (measured: 6 and 8 equal, 4 slower for decryption)
+#endif
+
+constexpr int kBgWarps = 8;    // warps per block
+constexpr int kBgTile = 32;    // chunks per staged row
+constexpr int kBgRowPad = 36;  // bytes per staged row: 9 words, so the 32 lanes'
+                               // word reads of their own rows hit 32 banks
+
+__device__ __forceinline__ uint32_t bg_w(uint64_t N) {
+    const uint32_t lg = 63u - (uint32_t)__clzll((long long)N);  // floor(log2 N), N >= 2
+    return lg ? 31u - (uint32_t)__clz((int)lg) : 0u;             // floor(log2 lg)
+}
+
+// One chunk: b = x_i & mask (x_i canonical), key ^= b, x_{i+1} = x_i^2.
+struct BgLane {
+    Barrett62 B;
+    uint64_t x;
+    uint32_t mask, key;
+    __device__ __forceinline__ uint32_t chunk(uint32_t v) {
+        key ^= (uint32_t)x & mask;
+        x = B.sqr(x);
+        return (v ^ key) & 0xFFu;
+    }
+    __device__ __forceinline__ uint32_t word(uint32_t w) {
+        uint32_t o = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) o |= chunk((w >> (8 * b)) & 0xFFu) << (8 * b);
+        return o;
+    }
+};
+
+// Encryption key check: N odd, 3 <= N < 2^62 (the range of Barrett62).
+__device__ __forceinline__ bool bg_setup_encrypt(uint64_t N, uint64_t r, BgLane &s) {
+    const bool ok = (N & 1ull) && N >= 3 && N < (1ull << 62);
+    if (!ok) N = 3;
+    s.B.set(N, barrett_mu(N));
+    s.x = s.B.sqr(r % N);  // x_0 = r^2 mod N
+    return ok;
+}
+
+// Decryption key check: p != q, both prime, = 3 mod 4, below 2^32, p q < 2^62.
+// x_0 = the square root of y taken L times mod p and mod q, joined by
+// Garner's formula x_0 = r_p + p ((r_q - r_p) p^-1 mod q).
+__device__ __forceinline__ bool bg_setup_decrypt(uint64_t p, uint64_t q, uint64_t y, uint64_t L, BgLane &s) {
+    const bool ok = p < (1ull << 32) && q < (1ull << 32) && (p & 3ull) == 3 && (q & 3ull) == 3 && p != q &&
+                    p * q < (1ull << 62) && is_prime_u32(p) && is_prime_u32(q);
+    uint64_t x0 = 0, N = 3;
+    if (ok) {
+        const Barrett32 Bp(p), Bq(q), Bp1(p - 1), Bq1(q - 1);
+        const uint64_t ep = Bp1.pow((p + 1) / 4, L);  // ((p+1)/4)^L mod (p-1)
+        const uint64_t eq = Bq1.pow((q + 1) / 4, L);
+        const uint64_t rp = Bp.pow(Bp.reduce(y), ep);
+        const uint64_t rq = Bq.pow(Bq.reduce(y), eq);
+        const uint64_t pinv = Bq.pow(p, q - 2);      // Fermat: p^(q-2) = p^-1 mod q
+        const uint64_t t = Bq.mul(Bq.reduce(rq + q - Bq.reduce(rp)), pinv);
+        x0 = rp + p * t;                             // < p + p (q - 1) = N
+        N = p * q;
+    }
+    s.B.set(N, barrett_mu(N));
+    s.x = x0;
+    return ok;
+}
+
+template <bool kDecrypt>
+__global__ void __launch_bounds__(kBgWarps * 32, CI_BG_MIN_BLOCKS)
+    k_bg(uint64_t n_msgs, uint64_t L, const uint64_t *__restrict__ key_a, const uint64_t *__restrict__ key_b,
+         const uint8_t *__restrict__ S0, const uint64_t *__restrict__ y_in, const uint8_t *in, uint8_t *out,
+         uint64_t *__restrict__ y_out, uint32_t *__restrict__ n_rejected) {
+    __shared__ __align__(16) uint8_t stage[kBgWarps][32 * kBgRowPad];
+    const uint32_t lane = threadIdx.x & 31u;
+    uint8_t *tile = stage[threadIdx.x >> 5];
+    uint8_t *row = tile + lane * kBgRowPad;
+    const uint64_t n_groups = (n_msgs + 31) / 32;
+    const uint64_t stride = (uint64_t)gridDim.x * kBgWarps;
+    for (uint64_t g = (uint64_t)blockIdx.x * kBgWarps + (threadIdx.x >> 5); g < n_groups; g += stride) {
+        const uint64_t m0 = g * 32;
+        const uint64_t msg = m0 + lane;
+        const bool live = msg < n_msgs;
+        const uint32_t rows = n_msgs - m0 < 32 ? (uint32_t)(n_msgs - m0) : 32u;
+        BgLane s;
+        bool ok = false;
+        if (live) {
+            ok = kDecrypt ? bg_setup_decrypt(key_a[msg], key_b[msg], y_in[msg], L, s)
+                          : bg_setup_encrypt(key_a[msg], key_b[msg], s);
+            s.mask = ok ? (1u << bg_w(s.B.M)) - 1u : 0u;
+            s.key = S0[msg];
+            if (!ok && n_rejected) atomicAdd(n_rejected, 1u);
+        }
+        const uint32_t keep = ok ? 0xFFFFFFFFu : 0u;  // a rejected key's row is written as zeros
+        for (uint64_t k0 = 0; k0 < L; k0 += kBgTile) {
+            const uint32_t width = L - k0 < (uint64_t)kBgTile ? (uint32_t)(L - k0) : (uint32_t)kBgTile;
+            __syncwarp();
+#pragma unroll 8
+            for (uint32_t r = 0; r < rows; ++r)
+                if (lane < width) tile[r * kBgRowPad + lane] = in[(m0 + r) * L + k0 + lane];
+            __syncwarp();
+            if (live) {
+                uint32_t *w = reinterpret_cast<uint32_t *>(row);
+                if (width == kBgTile) {
+#pragma unroll
+                    for (int j = 0; j < kBgTile / 4; ++j) w[j] = s.word(w[j]) & keep;
+                } else {
+                    for (uint32_t j = 0; j < width; ++j) row[j] = (uint8_t)(s.chunk(row[j]) & keep);
+                }
+            }
+            __syncwarp();
+#pragma unroll 8
+            for (uint32_t r = 0; r < rows; ++r)
+                if (lane < width) out[(m0 + r) * L + k0 + lane] = tile[r * kBgRowPad + lane];
+        }
+        if (!kDecrypt && live) y_out[msg] = ok ? s.x : 0ull;
+    }
+}
+
+template <bool kDecrypt>
+int bg_grid(uint64_t n_msgs) {
+    static int per_sm = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bg<kDecrypt>, kBgWarps * 32, 0);
+        if (per_sm <= 0) per_sm = 1;
+    });
+    const uint64_t blocks = (n_msgs + 32 * kBgWarps - 1) / (32 * kBgWarps);
+    return (int)std::min<uint64_t>(blocks, (uint64_t)sm_count() * per_sm);
+}
+
+ci_status bg_check(uint64_t n_msgs, uint64_t n_chunks, const void *a, const void *b, const void *S0,
+                   const void *y, const void *in, const void *out) {
+    if (!a || !b || !S0 || !y) return fail(CI_E_INVAL, "bg: key, S0 and y arrays must be non-null");
+    if (n_chunks && (!in || !out)) return fail(CI_E_INVAL, "bg: message and ciphertext must be non-null");
+    if (n_chunks > ~0ull / n_msgs) return fail(CI_E_INVAL, "bg: n_msgs * n_chunks overflows");
+    return CI_OK;
+}
+
+}  // namespace
+}  // namespace ci
+
+extern "C" {
+
+ci_status ci_bg_encrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *N_dev, const uint8_t *S0_dev,
+                        const uint64_t *r_dev, const uint8_t *msg_dev, uint8_t *cipher_dev, uint64_t *y_dev,
+                        uint32_t *n_rejected_dev, void *cuda_stream) {
+    using namespace ci;
+    if (n_msgs == 0) return CI_OK;
+    const ci_status st = bg_check(n_msgs, n_chunks, N_dev, r_dev, S0_dev, y_dev, msg_dev, cipher_dev);
+    if (st != CI_OK) return st;
+    k_bg<false><<<bg_grid<false>(n_msgs), kBgWarps * 32, 0, (cudaStream_t)cuda_stream>>>(
+        n_msgs, n_chunks, N_dev, r_dev, S0_dev, nullptr, msg_dev, cipher_dev, y_dev, n_rejected_dev);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "ci_bg_encrypt launch");
+}
+
+ci_status ci_bg_decrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *p_dev, const uint64_t *q_dev,
+                        const uint8_t *S0_dev, const uint64_t *y_dev, const uint8_t *cipher_dev, uint8_t *msg_dev,
+                        uint32_t *n_rejected_dev, void *cuda_stream) {
+    using namespace ci;
+    if (n_msgs == 0 || n_chunks == 0) return CI_OK;
+    const ci_status st = bg_check(n_msgs, n_chunks, p_dev, q_dev, S0_dev, y_dev, cipher_dev, msg_dev);
+    if (st != CI_OK) return st;
+    k_bg<true><<<bg_grid<true>(n_msgs), kBgWarps * 32, 0, (cudaStream_t)cuda_stream>>>(
+        n_msgs, n_chunks, p_dev, q_dev, S0_dev, y_dev, cipher_dev, msg_dev, nullptr, n_rejected_dev);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "ci_bg_decrypt launch");
+}
+
+}  // extern "C"

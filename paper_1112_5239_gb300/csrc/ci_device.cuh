@@ -1,6 +1,6 @@
 // ci_device.cuh -- device building blocks of the chaotic-iterations PRNG for
 // sm_103a: seeding, strategy sources (Algorithm 2 XORshift, 32-bit xor128,
-// BBS with Montgomery reduction), and the per-warp generation loop that runs
+// BBS with Barrett reduction), and the per-warp generation loop that runs
 // Algorithm 4/5's mixing and the Eq. (Oplus) update with the lanes' state in
 // registers.
 //
@@ -112,12 +112,17 @@ struct SrcXor64 {
     }
 };
 
-// ------------------------------------------------ Montgomery arithmetic
-// R = 2^64, M odd with 2^32 <= M < 2^62, Mp = -M^-1 mod R.  Values are kept
-// "lazy" in [0, 2M): for a, b < 2M, a*b < 4M^2 < M R (as 4M < R), so
-// (a*b + m M) / R < 2M with m = (a*b mod R) Mp mod R -- no final subtraction.
-// (A 32-bit-limb square exploiting a0*a1 = a1*a0 measured 16 % slower on
-// sm_103a than the 64-bit multiply-high form below.)
+// ------------------------------------------------ Barrett arithmetic
+// x^2 mod M for odd M of bit length n, 2 <= n <= 62, and canonical x < M, by
+// Barrett reduction (Barrett 1986; base-2 form of Menezes et al., Handbook of
+// Applied Cryptography, Alg. 14.42): q1 = floor(x^2 / 2^(n-1)),
+// q3 = floor(q1 mu / 2^(n+1)) with mu = floor(2^(2n) / M), and
+// r = x^2 - q3 M lies in [0, 3M), so at most two subtractions give the
+// canonical residue.  As mu < 2^(n+1), q3 = mulhi(q1, mu << (63 - n)) exactly;
+// that shifted reciprocal is what the state stores.  The result is canonical
+// at every step, so the BBS low bits need no conversion (a Montgomery square
+// plus the reduction to canonical form measured 22 % slower at full
+// occupancy on sm_103a).
 __host__ __device__ __forceinline__ uint64_t mul_hi64(uint64_t a, uint64_t b) {
 #ifdef __CUDA_ARCH__
     return __umul64hi(a, b);
@@ -126,68 +131,70 @@ __host__ __device__ __forceinline__ uint64_t mul_hi64(uint64_t a, uint64_t b) {
 #endif
 }
 
-__host__ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t M, uint64_t Mp) {
-    const uint64_t tlo = a * b;
-    const uint64_t thi = mul_hi64(a, b);
-    const uint64_t m = tlo * Mp;
-    // tlo + lo(m M) = 0 mod R: it wraps (carry 1) exactly when tlo != 0
-    return thi + mul_hi64(m, M) + (tlo != 0 ? 1ull : 0ull);
+__host__ __device__ __forceinline__ uint32_t bit_length64(uint64_t M) {
+#ifdef __CUDA_ARCH__
+    return 64u - (uint32_t)__clzll((long long)M);
+#else
+    return 64u - (uint32_t)__builtin_clzll(M);
+#endif
 }
 
-// Canonical residue of a lazy value a < 2M: (a + m M) / R with m = a Mp.
-// The quotient is < M + 2M/R, i.e. <= M, and equals M only if a = 0 mod M,
-// which for a in [0, 2M) with a != M means a = 0 (giving 0): the result is
-// already in [0, M).  (a = M cannot arise: 0 stays 0 under squaring.)
-__host__ __device__ __forceinline__ uint64_t mont_out(uint64_t a, uint64_t M, uint64_t Mp) {
-    const uint64_t m = a * Mp;
-    return mul_hi64(m, M) + (a != 0 ? 1ull : 0ull);
-}
-
-// -M^-1 mod 2^64 by Newton's iteration (each step doubles the correct bits;
-// M * M = 1 mod 8 gives 3 bits to start).
-__device__ __forceinline__ uint64_t neg_inv64(uint64_t M) {
-    uint64_t inv = M;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) inv *= 2ull - M * inv;
-    return 0ull - inv;
-}
-
-// 2^128 mod M: 2^64 mod M, then 64 modular doublings (values < 2^62).
-__device__ __forceinline__ uint64_t r2_mod(uint64_t M) {
-    uint64_t r = (0ull - M) % M;
-    for (int i = 0; i < 64; ++i) {
+// floor(2^(2n) / M) << (63 - n) by restoring long division of 2^(2n)
+// (remainders stay below M < 2^62).
+__host__ __device__ __forceinline__ uint64_t barrett_mu(uint64_t M) {
+    const uint32_t n = bit_length64(M);
+    uint64_t r = 1, q = 0;
+    for (uint32_t i = 0; i < 2 * n; ++i) {
         r <<= 1;
-        if (r >= M) r -= M;
+        q <<= 1;
+        if (r >= M) {
+            r -= M;
+            q |= 1;
+        }
     }
-    return r;
+    return q << (63 - n);
 }
+
+struct Barrett62 {
+    uint64_t M, mu;  // mu: barrett_mu(M)
+    uint32_t s1, s2;  // n - 1, 65 - n
+    __host__ __device__ __forceinline__ void set(uint64_t mod, uint64_t mu_shifted) {
+        M = mod;
+        mu = mu_shifted;
+        const uint32_t n = bit_length64(mod);
+        s1 = n - 1;
+        s2 = 65 - n;
+    }
+    __host__ __device__ __forceinline__ uint64_t sqr(uint64_t x) const {
+        const uint64_t lo = x * x, hi = mul_hi64(x, x);
+        const uint64_t q3 = mul_hi64((hi << s2) | (lo >> s1), mu);
+        uint64_t r = lo - q3 * M;
+        r = r >= M ? r - M : r;
+        return r >= M ? r - M : r;
+    }
+};
 
 // Blum Blum Shub strategy source (Algorithm 5 generalised to w = 5 bits per
 // squaring for 62-bit moduli): 7 chunks of 5 bits, then two shift steps.
 struct SrcBbs {
     static constexpr bool kHeavy = true;
-    uint64_t Y, M, Mp;  // Y: Montgomery form of the BBS state, lazy in [0, 2M)
+    Barrett62 B;
+    uint64_t y;  // BBS state, canonical in [0, M)
     uint32_t sel;
     __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
-        const uint64_t y = s.u64[G_Y * s.P + l];
-        M = s.u64[G_M * s.P + l];
-        Mp = s.u64[G_MP * s.P + l];
-        const uint64_t r2 = s.u64[G_R2 * s.P + l];
-        Y = mont_mul(y, r2, M, Mp);  // y R mod M (y < 2^64, r2 < M: product < M R)
+        y = s.u64[G_Y * s.P + l];
+        B.set(s.u64[G_M * s.P + l], s.u64[G_MU * s.P + l]);
         sel = s.u32[F_SEL * s.P + l];
     }
-    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const {
-        s.u64[G_Y * s.P + l] = mont_out(Y, M, Mp);
-    }
+    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const { s.u64[G_Y * s.P + l] = y; }
     __device__ __forceinline__ void arrays(const DevState &, uint64_t, int &a1, int &a2) const {
         a1 = (int)(sel & 7u);
         a2 = 8 + (int)((sel >> 8) & 7u);
     }
-    // One BBS output: x <- x^2 mod M, returned canonical (its low bits are the
-    // secure ones).
+    // One BBS output: x <- x^2 mod M (its low bits are the secure ones).
     __device__ __forceinline__ uint32_t bbs() {
-        Y = mont_mul(Y, Y, M, Mp);
-        return (uint32_t)mont_out(Y, M, Mp);
+        y = B.sqr(y);
+        return (uint32_t)y;
     }
     __device__ __forceinline__ uint32_t next() {
         uint32_t t = 0;

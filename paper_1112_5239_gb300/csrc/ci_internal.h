@@ -16,9 +16,9 @@ namespace ci {
 constexpr int kTableBytes = 512;     // partner table u8[16][32]
 constexpr int kU32Fields = 9;        // a b c d x slot sel p q
 constexpr int kU32FieldsBbs16 = 25;  // ... then y16[8], m16[8] (CI_VAR_BBS16)
-constexpr int kU64Fields = 4;        // y M Mp r2 (BBS only)
+constexpr int kU64Fields = 3;        // y M mu (BBS only)
 enum U32Field { F_A = 0, F_B = 1, F_C = 2, F_D = 3, F_X = 4, F_SLOT = 5, F_SEL = 6, F_P = 7, F_Q = 8, F_Y16 = 9, F_M16 = 17 };
-enum U64Field { G_Y = 0, G_M = 1, G_MP = 2, G_R2 = 3 };
+enum U64Field { G_Y = 0, G_M = 1, G_MU = 2 };
 
 // Device view of one handle's state, passed to kernels by value.
 struct DevState {

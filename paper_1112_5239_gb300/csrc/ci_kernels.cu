@@ -12,6 +12,7 @@
 
 #include "ci_device.cuh"
 #include "ci_gen.cuh"
+#include "ci_modarith.cuh"
 #include "ci_tune.h"
 
 namespace ci {
@@ -71,46 +72,6 @@ __global__ void __launch_bounds__(256) k_init_xor(DevState st, TableParam tp, ui
         init_xor_lane(st, seed, first, xl, l);
 }
 
-__device__ __forceinline__ uint32_t mulmod32(uint32_t a, uint32_t b, uint32_t n) {
-    return (uint32_t)(((uint64_t)a * b) % n);
-}
-
-__device__ uint32_t powmod32(uint32_t a, uint32_t e, uint32_t n) {
-    uint32_t r = 1u;
-    while (e) {
-        if (e & 1u) r = mulmod32(r, a, n);
-        a = mulmod32(a, a, n);
-        e >>= 1;
-    }
-    return r;
-}
-
-// Miller-Rabin with bases 2, 7, 61: exact for odd n < 4,759,123,141
-// (Jaeschke 1993); here n is an odd number in [2^30, 2^31).
-__device__ bool is_prime_mr(uint32_t n) {
-    uint32_t d = n - 1u;
-    int s = 0;
-    while ((d & 1u) == 0u) {
-        d >>= 1;
-        ++s;
-    }
-    const uint32_t bases[3] = {2u, 7u, 61u};
-    for (int i = 0; i < 3; ++i) {
-        uint32_t x = powmod32(bases[i], d, n);
-        if (x == 1u || x == n - 1u) continue;
-        bool composite = true;
-        for (int r = 1; r < s; ++r) {
-            x = mulmod32(x, x, n);
-            if (x == n - 1u) {
-                composite = false;
-                break;
-            }
-        }
-        if (composite) return false;
-    }
-    return true;
-}
-
 // Blum prime candidate from a draw: 2^30 + (d >> 34), forced to 3 mod 4.
 __device__ __forceinline__ uint32_t blum_candidate(uint64_t d) {
     return (uint32_t)((1ull << 30) + (d >> 34)) | 3u;
@@ -122,11 +83,11 @@ __device__ void init_bbs_lane(const DevState &st, uint64_t seed, uint64_t first,
     do {
         d = lane_draw(seed, first + l, k++);
         p = blum_candidate(d);
-    } while (!is_prime_mr(p));
+    } while (!is_prime_u32(p));
     do {
         d = lane_draw(seed, first + l, k++);
         q = blum_candidate(d);
-    } while (q == p || !is_prime_mr(q));
+    } while (q == p || !is_prime_u32(q));
     const uint64_t M = (uint64_t)p * q;
     uint64_t v;
     do {
@@ -142,8 +103,7 @@ __device__ void init_bbs_lane(const DevState &st, uint64_t seed, uint64_t first,
     st.u32[F_Q * st.P + l] = q;
     st.u64[G_Y * st.P + l] = v;
     st.u64[G_M * st.P + l] = M;
-    st.u64[G_MP * st.P + l] = neg_inv64(M);
-    st.u64[G_R2 * st.P + l] = r2_mod(M);
+    st.u64[G_MU * st.P + l] = barrett_mu(M);
 }
 
 __global__ void __launch_bounds__(256) k_init_bbs(DevState st, TableParam tp, uint64_t seed, uint64_t first) {

@@ -92,3 +92,82 @@ def serving_requests(seed: int = 5, count: int = 2000, rate: float = 1000.0, con
             S = 1 << min(max(int(math.floor(math.log2(max(n, 1)))) - 10, 0), 16)
             reqs.append(Request(variant, S, max(1, -(-n // S)), sd, 0, -1, t))
     return reqs
+
+
+# ------------------------------------------------ chaotic Blum-Goldwasser
+# Batches of messages for the Sec. 9.2 cryptosystem: keys are products of two
+# distinct Blum primes (= 3 mod 4) in [2^30, 2^31), so 2^60 <= N < 2^62 and
+# w = 5 bits per chunk; messages share a pool of recipients' keys (many
+# messages to few recipients), each with its own r and S^0 < 2^5.
+BG_2E20x1024 = (1 << 20, 1 << 10)   # n_msgs, n_chunks of the throughput workload (1 GiB of chunks)
+BG_KEY_POOL = 4096
+
+
+def _is_probable_prime(n: int) -> bool:
+    """Deterministic Miller-Rabin for odd n < 4,759,123,141 (bases 2, 7, 61)."""
+    if n < 3 or n % 2 == 0:
+        return n == 2
+    d, s = n - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        s += 1
+    for a in (2, 7, 61):
+        if a % n == 0:
+            continue
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(s - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def blum_primes(rng: np.random.Generator, count: int, lo: int = 1 << 30, hi: int = 1 << 31) -> list[int]:
+    out: list[int] = []
+    while len(out) < count:
+        c = int(rng.integers(lo, hi)) | 3
+        if c < hi and _is_probable_prime(c):
+            out.append(c)
+    return out
+
+
+def bg_keys(seed: int, n_keys: int, lo: int = 1 << 30, hi: int = 1 << 31) -> tuple[np.ndarray, np.ndarray]:
+    """n_keys private keys (p, q), p != q Blum primes in [lo, hi), as int64."""
+    rng = np.random.default_rng(seed)
+    ps, qs = [], []
+    while len(ps) < n_keys:
+        p, q = blum_primes(rng, 2, lo, hi)
+        if p != q:
+            ps.append(p)
+            qs.append(q)
+    return np.array(ps, dtype=np.int64), np.array(qs, dtype=np.int64)
+
+
+def bg_batch(seed: int, n_msgs: int, n_keys: int = BG_KEY_POOL, lo: int = 1 << 30, hi: int = 1 << 31):
+    """Per-message keys and randomness: dict of int64 arrays p, q, N, r and a
+    uint8 array S0, each of n_msgs entries.  A recipient's public key is
+    (S^0, N) with S^0 < 2^w (Sec. 9.2), so S0 is drawn per key of the pool;
+    r is per message, drawn in [2, N) and redrawn until gcd(r, N) = 1."""
+    kp, kq = bg_keys(seed, n_keys, lo, hi)
+    rng = np.random.default_rng(seed + 1)
+    kN = kp * kq
+    kw = np.floor(np.log2(np.floor(np.log2(kN.astype(np.float64))))).astype(np.int64)
+    kS0 = (rng.integers(0, 1 << 8, size=n_keys) & ((1 << kw) - 1)).astype(np.uint8)
+    pick = rng.integers(0, n_keys, size=n_msgs)
+    p, q, N, S0 = kp[pick], kq[pick], kN[pick], kS0[pick]
+    r = (rng.random(n_msgs) * (N - 2).astype(np.float64)).astype(np.int64) % (N - 2) + 2
+    bad = np.gcd(r, N) != 1
+    while bad.any():
+        r[bad] = (rng.random(int(bad.sum())) * (N[bad] - 2).astype(np.float64)).astype(np.int64) % (N[bad] - 2) + 2
+        bad = np.gcd(r, N) != 1
+    return {"p": p, "q": q, "N": N, "r": r, "S0": S0}
+
+
+def bg_messages(seed: int, n_msgs: int, n_chunks: int, bits: int = 5) -> np.ndarray:
+    """Uniform w-bit chunks, one per byte, message-major (n_msgs, n_chunks)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 1 << bits, size=(n_msgs, n_chunks), dtype=np.uint8)

@@ -7,7 +7,10 @@ import os
 import re
 import shutil
 
+import numpy as np
 import pytest
+
+import oracle
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -54,7 +57,7 @@ def test_version_and_errors_without_gpu(L):
     assert nbytes.value == 512 + 9 * 4 * 4096
     p.variant = 1
     assert lib.ci_state_bytes(ctypes.byref(p), 33, ctypes.byref(nbytes)) == 0
-    assert nbytes.value == 512 + 9 * 4 * 64 + 4 * 8 * 64
+    assert nbytes.value == 512 + 9 * 4 * 64 + 3 * 8 * 64
     p.variant = 2
     assert lib.ci_state_bytes(ctypes.byref(p), 40, ctypes.byref(nbytes)) == 0
     assert nbytes.value == 512 + 25 * 4 * 64
@@ -78,6 +81,18 @@ def test_version_and_errors_without_gpu(L):
     assert lib.ci_free_states(None) == 0
 
 
+def test_bg_argument_checks_without_gpu(L):
+    lib = L.lib()
+    one = ctypes.c_void_p(16)  # never dereferenced: every call below fails its host checks or is a no-op
+    assert lib.ci_bg_encrypt(0, 5, None, None, None, None, None, None, None, None) == 0
+    assert lib.ci_bg_decrypt(3, 0, one, one, one, one, None, None, None, None) == 0
+    assert lib.ci_bg_encrypt(3, 5, None, one, one, one, one, one, None, None) == -1
+    assert lib.ci_bg_encrypt(3, 5, one, one, one, None, one, one, None, None) == -1
+    assert lib.ci_bg_decrypt(3, 5, one, one, one, one, None, one, None, None) == -1
+    assert lib.ci_bg_encrypt(2**33, 2**33, one, one, one, one, one, one, None, None) == -1
+    assert b"overflows" in lib.ci_last_error()
+
+
 def test_workload_generators_are_deterministic():
     from paper_1112_5239_gb300 import workloads as W
 
@@ -87,6 +102,11 @@ def test_workload_generators_are_deterministic():
     assert all(1 <= r.n_streams <= 2**16 and 2**6 <= r.n_per_stream <= 2**20 for r in a)
     frac_xor = sum(r.variant == "xor" for r in a) / len(a)
     assert 0.7 < frac_xor < 0.9
+    b = W.bg_batch(9, 500, n_keys=16)
+    assert all(np.array_equal(b[k], W.bg_batch(9, 500, n_keys=16)[k]) for k in b)
+    assert (b["N"] == b["p"] * b["q"]).all() and (b["N"] >= 2**60).all() and (b["N"] < 2**62).all()
+    assert ((b["p"] & 3) == 3).all() and (b["p"] != b["q"]).all() and (np.gcd(b["r"], b["N"]) == 1).all()
+    assert all(oracle.is_prime(int(v)) for v in np.concatenate([b["p"][:40], b["q"][:40]]))
     s = W.serving_requests(count=300)
     assert s == W.serving_requests(count=300)
     assert all(s[i].arrival <= s[i + 1].arrival for i in range(len(s) - 1))

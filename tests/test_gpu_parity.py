@@ -150,13 +150,17 @@ def test_bbs_small(env, C):
         assert np.array_equal(s["sel"][:P] >> 8, orc.lanes["sel2"])
 
 
-def test_bbs_montgomery_constants(env):
+def test_bbs_barrett_reciprocals(env):
+    """The stored reciprocal of each modulus is floor(2^(2n) / M) << (63 - n),
+    n = bit length of M, and the state stays canonical (y < M)."""
     torch, ci = env
     st = _states(ci, "bbs", "xor128", 32, 3, 0, 256)
+    st.generate(40)
     s = ci.unpack_state(st.export_state(), 256, 1)
-    for M, Mp, r2 in zip(s["M"].tolist(), s["Mp"].tolist(), s["r2"].tolist()):
-        assert (M * Mp) % 2**64 == 2**64 - 1
-        assert r2 == pow(2, 128, M)
+    for M, mu, y in zip(s["M"].tolist(), s["mu"].tolist(), s["y"].tolist()):
+        n = M.bit_length()
+        assert mu == (2 ** (2 * n) // M) << (63 - n)
+        assert y < M
 
 
 def test_error_statuses(env):
