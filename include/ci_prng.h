@@ -434,6 +434,33 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out);
 ci_status ci_tune_get(ci_tune_table *out);
 ci_status ci_tune_set(const ci_tune_table *in);
 
+/* ---------------------------------------------- time-parallel generation */
+
+/* Not a construct of the paper: one call of n_per_stream iterations cut into
+ * n_segments time segments that run concurrently, with outputs, sink results
+ * and the final state IDENTICAL to the sequential call (ci_generate /
+ * ci_generate_bbs for CI_SINK_WRITTEN, ci_generate_fused_qc for CI_SINK_QC,
+ * ci_generate_digest for CI_SINK_DIGEST).  For states with few streams and
+ * long lengths, whose sequential chains leave most of the GPU idle.
+ * Method: each segment's own generator is jumped ahead (xor-likes: GF(2)
+ * matrix powers of their step; BBS: x <- x^(2^(11 k len) mod lcm(p-1, q-1))
+ * mod M), the segments run from a zero mixing state, a per-warp scan restores
+ * their true starts from the linearity of Algorithm 4/5's mixing and Eq.
+ * (Oplus) over the lanes, and the segments run again from those starts into
+ * the sink.  Cost: about twice the generator work, spread over up to
+ * n_segments times more warps.
+ * out_dev: uint32 outputs (CI_SINK_WRITTEN, out_capacity elements, layout as
+ * ci_generate) or uint64[n_streams] (counts INCREMENTED for CI_SINK_QC,
+ * digests SET for CI_SINK_DIGEST; out_capacity ignored).  n_segments == 0
+ * picks the count from the GPU size; the count is capped at 8192 and
+ * segments hold a multiple of 32 iterations, so small calls run unsplit.
+ * Allocates a stream-ordered workspace of about n_segments state copies.
+ * Errors: CI_E_STATE (invalid handle, or CI_VAR_BBS16, whose outputs depend
+ * on call boundaries), CI_E_INVAL (unknown sink, NULL output, capacity, odd
+ * length for CI_SINK_QC), CI_E_NOMEM, CI_E_CUDA. */
+ci_status ci_generate_split(ci_states states, uint64_t n_per_stream, int32_t sink, void *out_dev,
+                           uint64_t out_capacity, uint32_t n_segments, void *cuda_stream);
+
 /* ------------------------------------------- chaotic Blum-Goldwasser */
 
 /* The chaotic Blum-Goldwasser cryptosystem of Sec. 9.2: Blum-Goldwasser

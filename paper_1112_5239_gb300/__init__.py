@@ -142,6 +142,22 @@ class States:
         _lib.call("ci_generate_digest", self.handle, int(n_per_stream), digest.data_ptr(), stream_ptr(stream))
         return digest
 
+    def generate_split(self, n_per_stream, sink="written", out=None, segments=0, stream=None) -> torch.Tensor:
+        """The same results as ``generate`` / ``generate_fused_qc`` /
+        ``generate_digest`` (sink "written" / "qc" / "digest"), computed as
+        up to ``segments`` concurrent time segments (0: chosen from the GPU
+        size) by jump-ahead: for few streams with long lengths."""
+        n = int(n_per_stream)
+        code = SINKS[sink] if isinstance(sink, str) else int(sink)
+        if out is None:
+            if code == _lib.CI_SINK_WRITTEN:
+                out = torch.empty((self.n_streams, n), dtype=torch.int32, device="cuda")
+            else:
+                out = torch.zeros(self.n_streams, dtype=torch.int64, device="cuda")
+        _lib.call("ci_generate_split", self.handle, n, code, out.data_ptr(), out.numel(), int(segments),
+                  stream_ptr(stream))
+        return out
+
     # ------------------------------------------------- checkpoint/resume
     def export_state(self, stream=None) -> np.ndarray:
         buf = np.zeros(self.state_bytes, dtype=np.uint8)

@@ -172,6 +172,14 @@ struct Barrett62 {
         r = r >= M ? r - M : r;
         return r >= M ? r - M : r;
     }
+    // a b mod M for a, b < M (the same reduction; any M of bit length 2..62).
+    __host__ __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) const {
+        const uint64_t lo = a * b, hi = mul_hi64(a, b);
+        const uint64_t q3 = mul_hi64((hi << s2) | (lo >> s1), mu);
+        uint64_t r = lo - q3 * M;
+        r = r >= M ? r - M : r;
+        return r >= M ? r - M : r;
+    }
 };
 
 // Blum Blum Shub strategy source (Algorithm 5 generalised to w = 5 bits per

@@ -1,0 +1,480 @@
+// ci_split.cu -- time-parallel generation of long streams by jump-ahead
+// (include/ci_prng.h: ci_generate_split).  Not a construct of the paper: it
+// cuts one call of n iterations into K segments of `len` iterations that run
+// at the same time, with results identical to the sequential call.
+//
+// Why it is exact.  Per warp, the own words o(i) of the strategy sources do
+// not depend on the mixing state, and the mixing is GF(2)-linear on the
+// lanes: with s the vector of the 32 lanes' slots and P the 32 x 32 matrix
+// whose row l has ones at the partners o1(l), o2(l) (Algorithm 4/5),
+//   s(i) = o(i) ^ P s(i-1),   x(i) = x(i-1) ^ s(i)   (Eq. Oplus),
+// so a segment started from (s, x) = (0, 0) gives a particular solution, and
+// the true one adds P^j s_a to s and x_a ^ (P + ... + P^j) s_a to x.
+//
+// Steps of one call (all on the caller's stream):
+//   1. k_split_setup: segment states k = 0 .. K-1 are copies of the state
+//      with the own generator jumped ahead by k len iterations (GF(2) matrix
+//      powers for the xor-likes, x <- x^(2^(11 k len) mod lambda(M)) for BBS)
+//      and (s, x) = (0, 0) for k >= 1;
+//   2. one batched launch runs segments 0 .. K-2 for len iterations into a
+//      digest sink (only their end states are needed);
+//   3. k_split_carry: one warp per warp group scans the segments in order:
+//      the true start of segment k is its predecessor's particular end plus
+//      (Q s_a, x_a ^ S s_a) with Q = P^len, S = P + ... + P^len; the own words
+//      of segment k take the end of segment k-1;
+//   4. one batched launch runs every segment from its true start into the
+//      caller's sink (segment 0 is the caller's state itself);
+//   5. the last segment's end state becomes the caller's state, and the
+//      per-segment quarter-circle counts or digests are combined.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ci_batch.h"
+#include "ci_device.cuh"
+
+namespace ci {
+namespace {
+
+using namespace dev;
+
+// ------------------------------------------------ xor-like jump tables
+// Column form of the GF(2)-linear step A of a xor-like with W 32-bit words:
+// T[i][j] = A^(2^i) e_j, so v <- A^(2^i) v is the XOR of the columns j at the
+// set bits of v.  Built on the device from the sources' own next().
+constexpr int kJumpLevels = 64;
+__device__ uint32_t g_jump_xor128[kJumpLevels][128][4];
+__device__ uint32_t g_jump_xor64[kJumpLevels][64][2];
+__device__ uint32_t g_jump_xs32[kJumpLevels][32][1];
+
+template <int W>
+__device__ __forceinline__ void step_words(uint32_t (&v)[W]) {
+    if (W == 4) {
+        SrcXor128 s;
+        s.a = v[0];
+        s.b = v[1 % W];
+        s.c = v[2 % W];
+        s.d = v[3 % W];
+        s.next();
+        v[0] = s.a;
+        v[1 % W] = s.b;
+        v[2 % W] = s.c;
+        v[3 % W] = s.d;
+    } else if (W == 2) {
+        SrcXor64 s;
+        s.z = (uint64_t)v[0] | ((uint64_t)v[1 % W] << 32);
+        s.next();
+        v[0] = (uint32_t)s.z;
+        v[1 % W] = (uint32_t)(s.z >> 32);
+    } else {
+        SrcXorshift32 s;
+        s.z = v[0];
+        s.next();
+        v[0] = s.z;
+    }
+}
+
+// One block of 32 W threads; thread j owns column j at every level.
+template <int W>
+__global__ void k_build_jump(uint32_t (*T)[32 * W][W]) {
+    const int j = threadIdx.x;
+    uint32_t v[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = (w == j / 32) ? (1u << (j % 32)) : 0u;
+    step_words<W>(v);
+#pragma unroll
+    for (int w = 0; w < W; ++w) T[0][j][w] = v[w];
+    for (int i = 1; i < kJumpLevels; ++i) {
+        __syncthreads();
+        uint32_t r[W] = {};
+        for (int b = 0; b < 32 * W; ++b)
+            if ((T[i - 1][j][b / 32] >> (b % 32)) & 1u)
+#pragma unroll
+                for (int w = 0; w < W; ++w) r[w] ^= T[i - 1][b][w];
+#pragma unroll
+        for (int w = 0; w < W; ++w) T[i][j][w] = r[w];
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void jump_words(uint32_t (&v)[W], uint64_t dist, const uint32_t (*T)[32 * W][W]) {
+    for (int i = 0; dist; ++i, dist >>= 1) {
+        if (!(dist & 1ull)) continue;
+        uint32_t r[W] = {};
+        for (int b = 0; b < 32 * W; ++b)
+            if ((v[b / 32] >> (b % 32)) & 1u)
+#pragma unroll
+                for (int w = 0; w < W; ++w) r[w] ^= T[i][b][w];
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = r[w];
+    }
+}
+
+std::mutex g_tables_mu;
+std::vector<int> g_tables_ready;  // per device ordinal
+
+cudaError_t ensure_jump_tables(cudaStream_t stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    if ((int)g_tables_ready.size() <= dev) g_tables_ready.resize(dev + 1, 0);
+    if (g_tables_ready[dev]) return cudaSuccess;
+    void *p128 = nullptr, *p64 = nullptr, *p32 = nullptr;
+    if ((e = cudaGetSymbolAddress(&p128, g_jump_xor128)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress(&p64, g_jump_xor64)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress(&p32, g_jump_xs32)) != cudaSuccess) return e;
+    k_build_jump<4><<<1, 128, 0, stream>>>(static_cast<uint32_t(*)[128][4]>(p128));
+    k_build_jump<2><<<1, 64, 0, stream>>>(static_cast<uint32_t(*)[64][2]>(p64));
+    k_build_jump<1><<<1, 32, 0, stream>>>(static_cast<uint32_t(*)[32][1]>(p32));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Wait once, so that calls on any stream of this device find finished tables.
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return e;
+    g_tables_ready[dev] = 1;
+    return cudaSuccess;
+}
+
+// ------------------------------------------------ BBS jump
+// x <- x^(2^E) mod M with E = 11 * dist squarings, through the exponent
+// 2^E mod lambda(M), lambda = lcm(p - 1, q - 1) (x is a unit mod M).
+__device__ __forceinline__ uint64_t gcd64(uint64_t a, uint64_t b) {
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+__device__ __forceinline__ uint64_t pow_mod(const Barrett62 &B, uint64_t a, uint64_t e) {
+    uint64_t r = 1 % B.M;
+    while (e) {
+        if (e & 1ull) r = B.mul(r, a);
+        a = B.mul(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint64_t bbs_jump(uint64_t y, uint64_t M, uint64_t mu, uint64_t p, uint64_t q,
+                                             uint64_t squarings) {
+    const uint64_t lam = (p - 1) / gcd64(p - 1, q - 1) * (q - 1);
+    Barrett62 L;
+    L.set(lam, barrett_mu(lam));
+    // 2^squarings mod lam by square-and-multiply on the exponent's bits
+    const uint64_t e = pow_mod(L, 2 % lam, squarings);
+    Barrett62 B;
+    B.set(M, mu);
+    return pow_mod(B, y, e);
+}
+
+// ------------------------------------------------ segment states
+struct SegSpace {
+    DevState v0;        // view of segment 0 (pointers into the workspace)
+    uint64_t stride;    // bytes between segment states
+    __device__ __forceinline__ DevState at(uint64_t k) const {
+        DevState s = v0;
+        const uint64_t off = k * stride;
+        s.table = v0.table + off;
+        s.u32 = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(v0.u32) + off);
+        if (v0.u64) s.u64 = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(v0.u64) + off);
+        return s;
+    }
+};
+
+constexpr int kOwnWords = 4;  // F_A .. F_D
+
+// Thread (k, l): segment k's lane l.  Copies the caller's lane (and the
+// partner table), jumps the own generator by k * len iterations and, for
+// k >= 1, clears slot and x.
+__global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg, uint32_t K, uint64_t len,
+                                                     int variant, int xl) {
+    const uint64_t total = (uint64_t)K * src.P;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint64_t k = t / src.P, l = t % src.P;
+        const DevState d = seg.at(k);
+        for (uint64_t w = l; w < kTableBytes / 4; w += src.P)
+            reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(d.table))[w] =
+                reinterpret_cast<const uint32_t *>(src.table)[w];
+        for (int f = 0; f < kU32Fields; ++f) d.u32[f * src.P + l] = src.u32[f * src.P + l];
+        if (variant == CI_VAR_BBS)
+            for (int f = 0; f < kU64Fields; ++f) d.u64[f * src.P + l] = src.u64[f * src.P + l];
+        if (k == 0) continue;
+        d.u32[F_X * src.P + l] = 0;
+        d.u32[F_SLOT * src.P + l] = 0;
+        const uint64_t dist = k * len;
+        if (variant == CI_VAR_BBS) {
+            d.u64[G_Y * src.P + l] = bbs_jump(src.u64[G_Y * src.P + l], src.u64[G_M * src.P + l],
+                                              src.u64[G_MU * src.P + l], src.u32[F_P * src.P + l],
+                                              src.u32[F_Q * src.P + l], 11ull * dist);
+        } else if (xl == CI_XL_XOR128) {
+            uint32_t v[4];
+            for (int w = 0; w < 4; ++w) v[w] = src.u32[(F_A + w) * src.P + l];
+            jump_words<4>(v, dist, g_jump_xor128);
+            for (int w = 0; w < 4; ++w) d.u32[(F_A + w) * src.P + l] = v[w];
+        } else if (xl == CI_XL_XOR64) {
+            uint32_t v[2] = {src.u32[F_A * src.P + l], src.u32[F_B * src.P + l]};
+            jump_words<2>(v, dist, g_jump_xor64);
+            d.u32[F_A * src.P + l] = v[0];
+            d.u32[F_B * src.P + l] = v[1];
+        } else {
+            uint32_t v[1] = {src.u32[F_A * src.P + l]};
+            jump_words<1>(v, dist, g_jump_xs32);
+            d.u32[F_A * src.P + l] = v[0];
+        }
+    }
+}
+
+// 32 x 32 GF(2) matrices over a warp's lanes, lane l holding row l (bit m of
+// row l = entry (l, m)).  C = A B: row_l(C) = XOR of row_m(B) over the set
+// bits m of row_l(A).  M v for a vector of words v (one per lane): lane l
+// takes the XOR of v_m over the set bits m of row_l(M).
+__device__ __forceinline__ uint32_t mat_mul(uint32_t a_row, uint32_t b_row) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const uint32_t b = __shfl_sync(kFull, b_row, m);
+        c ^= ((a_row >> m) & 1u) ? b : 0u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t mat_vec(uint32_t m_row, uint32_t v) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const uint32_t b = __shfl_sync(kFull, v, m);
+        r ^= ((m_row >> m) & 1u) ? b : 0u;
+    }
+    return r;
+}
+
+// One warp per warp group g of the caller's state.
+template <class Src>
+__global__ void __launch_bounds__(128) k_split_carry(SegSpace seg, uint32_t K, uint64_t len, uint64_t groups) {
+    const uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (g >= groups) return;  // whole warps leave together (blockDim is a multiple of 32)
+    const int lane = threadIdx.x & 31;
+    const DevState s0 = seg.at(0);
+    const uint64_t P = s0.P, l = g * 32 + lane;
+    Src src;
+    src.load(s0, l);
+    int a1, a2;
+    src.arrays(s0, l, a1, a2);
+    const uint32_t prow = (1u << s0.table[a1 * 32 + lane]) ^ (1u << s0.table[a2 * 32 + lane]);
+    // Q = P^len, S = P + ... + P^len, by the bits of len from the top:
+    // (Q, S) for k -> 2k: S <- S ^ Q S, Q <- Q Q; k -> k + 1: Q <- Q P, S <- S ^ Q.
+    uint32_t Q = 1u << lane, S = 0;
+    for (int b = 63; b >= 0; --b) {
+        S ^= mat_mul(Q, S);
+        Q = mat_mul(Q, Q);
+        if ((len >> b) & 1ull) {
+            Q = mat_mul(Q, prow);
+            S ^= Q;
+        }
+    }
+    const bool bbs = s0.u64 != nullptr;
+    uint32_t cs = 0, cx = 0;  // true (slot, x) at the start of the current segment
+    uint32_t pe_s = s0.u32[F_SLOT * P + l], pe_x = s0.u32[F_X * P + l];
+    uint32_t own[kOwnWords];
+    for (int w = 0; w < kOwnWords; ++w) own[w] = s0.u32[(F_A + w) * P + l];
+    uint64_t own_y = bbs ? s0.u64[G_Y * P + l] : 0;
+    for (uint32_t k = 1; k < K; ++k) {
+        const DevState d = seg.at(k);
+        const uint32_t ns = pe_s ^ mat_vec(Q, cs);
+        const uint32_t nx = pe_x ^ cx ^ mat_vec(S, cs);
+        cs = ns;
+        cx = nx;
+        pe_s = d.u32[F_SLOT * P + l];
+        pe_x = d.u32[F_X * P + l];
+        d.u32[F_SLOT * P + l] = cs;
+        d.u32[F_X * P + l] = cx;
+        for (int w = 0; w < kOwnWords; ++w) {
+            const uint32_t t = d.u32[(F_A + w) * P + l];
+            d.u32[(F_A + w) * P + l] = own[w];
+            own[w] = t;
+        }
+        if (bbs) {
+            const uint64_t t = d.u64[G_Y * P + l];
+            d.u64[G_Y * P + l] = own_y;
+            own_y = t;
+        }
+    }
+}
+
+// The last segment's state becomes the caller's state.
+__global__ void __launch_bounds__(256) k_split_copy_back(DevState dst, DevState last) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < dst.P; l += stride) {
+        for (int f = 0; f < kU32Fields; ++f) dst.u32[f * dst.P + l] = last.u32[f * dst.P + l];
+        if (dst.u64)
+            for (int f = 0; f < kU64Fields; ++f) dst.u64[f * dst.P + l] = last.u64[f * dst.P + l];
+    }
+}
+
+// Combines per-segment consumer results r[k * P + l] for stream l < S:
+// quarter-circle counts are added to out[l]; digests are joined by Horner,
+// D = sum_k D_k K^(n - end of segment k), the last segment ending at n.
+__global__ void __launch_bounds__(256) k_split_combine(const uint64_t *r, uint64_t *out, uint64_t P, uint64_t S,
+                                                       uint32_t K, uint64_t len, uint64_t len_last, int digest) {
+    const uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= S) return;
+    if (!digest) {
+        uint64_t c = 0;
+        for (uint32_t k = 0; k < K; ++k) c += r[(uint64_t)k * P + l];
+        out[l] += c;
+        return;
+    }
+    auto kpow = [](uint64_t e) {
+        uint64_t b = kDigestMul, p = 1;
+        while (e) {
+            if (e & 1ull) p *= b;
+            b *= b;
+            e >>= 1;
+        }
+        return p;
+    };
+    const uint64_t step = kpow(len);
+    uint64_t d = 0, mult = 1;
+    for (uint32_t k = K; k-- > 0;) {
+        d += r[(uint64_t)k * P + l] * mult;
+        mult *= (k == K - 1) ? kpow(len_last) : step;
+    }
+    out[l] = d;
+}
+
+// ------------------------------------------------ host side
+constexpr uint32_t kMaxSegments = 8192;
+constexpr uint64_t kMinSegment = 256;  // iterations per segment (auto choice)
+
+std::mutex g_split_mu;  // the shared batch below
+ci_batch g_split_batch[64] = {};
+
+ci_batch split_batch(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_split_batch[dev]) {
+        ci_batch b = nullptr;
+        if (ci_batch_create(kMaxSegments, &b) != CI_OK) return nullptr;
+        g_split_batch[dev] = b;
+    }
+    return g_split_batch[dev];
+}
+
+int split_block_count(uint64_t items) {
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, (uint64_t)sm_count() * 8));
+}
+
+}  // namespace
+}  // namespace ci
+
+extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, void *out_dev,
+                                       uint64_t out_capacity, uint32_t n_segments, void *cuda_stream) {
+    using namespace ci;
+    if (!valid_handle(h)) return fail(CI_E_STATE, "invalid states handle");
+    if (h->variant == CI_VAR_BBS16)
+        return fail(CI_E_STATE, "CI_VAR_BBS16 outputs depend on call boundaries; it cannot be split");
+    if (sink != CI_SINK_WRITTEN && sink != CI_SINK_QC && sink != CI_SINK_DIGEST)
+        return fail(CI_E_INVAL, "unknown sink");
+    if (n == 0) return CI_OK;
+    if (!out_dev) return fail(CI_E_INVAL, "output is NULL");
+    if (sink == CI_SINK_WRITTEN && (n > ~0ull / h->S || out_capacity < h->S * n))
+        return fail(CI_E_INVAL, "out_capacity is smaller than n_streams * n");
+    if (sink == CI_SINK_QC && (n & 1ull)) return fail(CI_E_INVAL, "quarter-circle sink needs an even length");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const uint64_t groups = h->P / 32;
+
+    uint64_t K = n_segments;
+    if (K == 0) {  // fill about four waves of resident warps
+        const uint64_t target = (uint64_t)sm_count() * 64;
+        K = std::max<uint64_t>(1, target / groups);
+        K = std::min<uint64_t>(K, std::max<uint64_t>(1, n / kMinSegment));
+    }
+    K = std::min<uint64_t>(K, kMaxSegments);
+    uint64_t len = (n + K - 1) / K;
+    len = (len + 31) / 32 * 32;  // whole staging tiles and 16-byte column offsets
+    K = (n + len - 1) / len;
+    if (K <= 1) {
+        if (sink == CI_SINK_QC) return ci_generate_fused_qc(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
+        if (sink == CI_SINK_DIGEST) return ci_generate_digest(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
+        return h->variant == CI_VAR_BBS
+                   ? ci_generate_bbs(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream)
+                   : ci_generate(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream);
+    }
+    const uint64_t len_last = n - (K - 1) * len;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_split_mu);
+    ci_batch batch = split_batch(dev);
+    if (!batch) return fail(CI_E_NOMEM, "could not create the split batch");
+    if ((e = ensure_jump_tables(stream)) != cudaSuccess) return cuda_fail(e, "jump tables");
+
+    const uint64_t stride = (h->bytes + 255) / 256 * 256;
+    const uint64_t res_bytes = 8ull * K * h->P;  // per-segment consumer results
+    uint8_t *ws = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&ws), stride * K + 2 * res_bytes, stream)) != cudaSuccess)
+        return cuda_fail(e, "workspace");
+    uint64_t *res1 = reinterpret_cast<uint64_t *>(ws + stride * K);
+    uint64_t *res3 = res1 + K * h->P;
+
+    // Handles over the segment states (host copies of the caller's, moved).
+    std::vector<ci_states_s> segs(K, *h);
+    for (uint64_t k = 0; k < K; ++k) {
+        segs[k].dev = ws + k * stride;
+        segs[k].owns = false;
+    }
+    SegSpace sp;
+    sp.v0 = segs[0].view();
+    sp.stride = stride;
+    const DevState src = h->view();
+
+    ci_status st = CI_OK;
+    k_split_setup<<<split_block_count(K * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl);
+    if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split setup");
+
+    std::vector<BatchTask> tasks;
+    if (st == CI_OK) {  // pass 1: particular solutions of segments 0 .. K-2
+        tasks.reserve(K);
+        for (uint64_t k = 0; k + 1 < K; ++k)
+            tasks.push_back(make_task(segs[k], len, CI_SINK_DIGEST, nullptr, res1 + k * h->P, len, 0));
+        st = batch_launch_tasks(batch, tasks.data(), (uint32_t)tasks.size(), stream, false);
+    }
+    if (st == CI_OK) {
+        const unsigned blocks = (unsigned)((groups * 32 + 127) / 128);
+        if (h->variant == CI_VAR_BBS)
+            k_split_carry<SrcBbs><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups);
+        else
+            k_split_carry<SrcXor128><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups);
+        if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split carry");
+    }
+    if (st == CI_OK && sink == CI_SINK_QC && (e = cudaMemsetAsync(res3, 0, res_bytes, stream)) != cudaSuccess)
+        st = cuda_fail(e, "clearing counts");
+    if (st == CI_OK) {  // pass 2: every segment from its true start
+        tasks.clear();
+        for (uint64_t k = 0; k < K; ++k) {
+            const ci_states_s &sh = k == 0 ? *h : segs[k];
+            const uint64_t nk = k + 1 == K ? len_last : len;
+            if (sink == CI_SINK_WRITTEN)
+                tasks.push_back(make_task(sh, nk, sink, static_cast<uint32_t *>(out_dev), nullptr, n, k * len));
+            else
+                tasks.push_back(make_task(sh, nk, sink, nullptr, res3 + k * h->P, nk, 0));
+        }
+        st = batch_launch_tasks(batch, tasks.data(), (uint32_t)tasks.size(), stream, false);
+    }
+    if (st == CI_OK) {
+        k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view());
+        if (sink != CI_SINK_WRITTEN)
+            k_split_combine<<<(unsigned)((h->S + 255) / 256), 256, 0, stream>>>(
+                res3, static_cast<uint64_t *>(out_dev), h->P, h->S, (uint32_t)K, len, len_last,
+                sink == CI_SINK_DIGEST);
+        if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split finish");
+    }
+    cudaFreeAsync(ws, stream);
+    return st;
+}

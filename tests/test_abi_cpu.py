@@ -79,6 +79,7 @@ def test_version_and_errors_without_gpu(L):
     assert lib.ci_init_states(ctypes.byref(q), 10, None, ctypes.byref(h)) == -1 and not h.value
     assert lib.ci_generate(None, 4, None, 0, None) == -6
     assert lib.ci_free_states(None) == 0
+    assert lib.ci_generate_split(None, 64, 0, None, 0, 2, None) == -6
 
 
 def test_bg_argument_checks_without_gpu(L):

@@ -1,0 +1,78 @@
+"""Time-parallel generation (ci_generate_split): outputs, consumer results and
+the final state equal the sequential oracle for every splittable source, group
+size, ragged stream count and segment count, and a split call continues
+exactly like a sequential one."""
+import numpy as np
+import pytest
+
+from gpu_util import cuda_or_skip, digest_rows, oracle_gen, u32
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("xor", "xor128"), ("xor", "xorshift32"), ("xor", "xor64"), ("bbs", "xor128")]
+
+
+def _states(ci, variant, xl, C, seed, S):
+    return ci.States(S, variant=variant, xl=xl, comb_size=C, seed=seed, comb_seed=seed + 7)
+
+
+@pytest.mark.parametrize("variant,xl", CASES)
+@pytest.mark.parametrize("C,S", [(32, 32), (4, 40)])
+@pytest.mark.parametrize("segments", [3, 7, 0])
+def test_written_matches_oracle_and_continues(variant, xl, C, S, segments):
+    torch, ci = cuda_or_skip()
+    n = 1000 if variant == "xor" else 300
+    seed = 11 + C + S
+    st = _states(ci, variant, xl, C, seed, S)
+    orc = oracle_gen(variant, xl, C, seed, seed + 7, S)
+    out = u32(st.generate_split(n, segments=segments))
+    assert np.array_equal(out, orc.streams(n))
+    nxt = u32(st.generate(50))  # the final state is the sequential one
+    assert np.array_equal(nxt, orc.streams(50))
+    ref = _states(ci, variant, xl, C, seed, S)
+    ref.generate(n + 50)
+    assert np.array_equal(st.export_state()[512:], ref.export_state()[512:])
+
+
+@pytest.mark.parametrize("variant,xl", [("xor", "xor128"), ("bbs", "xor128")])
+def test_consumer_sinks(variant, xl):
+    torch, ci = cuda_or_skip()
+    n, S, C = 640, 40, 8
+    st = _states(ci, variant, xl, C, 5, S)
+    orc = oracle_gen(variant, xl, C, 5, 12, S)
+    ref = orc.streams(n)
+    d = st.generate_split(n, sink="digest", segments=5).cpu().numpy().view(np.uint64)
+    assert np.array_equal(d, digest_rows(ref))
+    counts = st.generate_split(n, sink="qc", segments=4).cpu().numpy().view(np.uint64)
+    o2 = orc.streams(n)
+    hits = (((o2[:, 0::2] >> 8).astype(np.uint64) ** 2 + (o2[:, 1::2] >> 8).astype(np.uint64) ** 2)
+            < (1 << 48)).sum(axis=1)
+    assert np.array_equal(counts, hits.astype(np.uint64))
+
+
+def test_long_narrow_stream_auto_segments():
+    """One warp of BBS streams over 2^16 iterations (256 segments by the auto
+    choice) equals the oracle, and the state continues exactly."""
+    torch, ci = cuda_or_skip()
+    n, S = 1 << 16, 32
+    st = _states(ci, "bbs", "xor128", 32, 21, S)
+    orc = oracle_gen("bbs", "xor128", 32, 21, 28, S)
+    out = u32(st.generate_split(n))
+    assert np.array_equal(out, orc.streams(n))
+    assert np.array_equal(u32(st.generate(64)), orc.streams(64))
+
+
+def test_unsplittable_and_bad_arguments():
+    torch, ci = cuda_or_skip()
+    b16 = _states(ci, "bbs16", "xor128", 32, 3, 32)
+    with pytest.raises(ci.CIError) as e:
+        b16.generate_split(256, segments=2)
+    assert e.value.status == -6
+    st = _states(ci, "xor", "xor128", 32, 3, 32)
+    with pytest.raises(ci.CIError) as e:
+        st.generate_split(255, sink="qc", segments=2)
+    assert e.value.status == -1
+    small = torch.empty(32 * 100 - 1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ci.CIError) as e:
+        st.generate_split(100, out=small, segments=2)
+    assert e.value.status == -1
