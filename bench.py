@@ -415,6 +415,7 @@ def main():
         result["bbs16"] = bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["e2e"] = bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
         result["bg"] = bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
+        result["split"] = bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         if rank == 0 and world == 1:
             r, n, dt = oracle_sample(args.cpu_sample_streams)
             result["cpu_baseline"] = {"value": r, "unit": "uint32/s", "cores": 1, "kind": "oracle",
@@ -591,6 +592,44 @@ def bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, 
             "workload": "2^20 messages x 1024 chunks (w = 5 bits each, one per byte), 62-bit Blum moduli from a "
                         "pool of 4096 keys, seed %d; one Barrett squaring per chunk" % SEED_BG,
             "modsq_per_s": {"encrypt": chunks / (ms_e / 1e3), "decrypt": chunks / (ms_d / 1e3)}}
+
+
+def bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):
+    """A long narrow request: one warp of BBS streams (32) over 2^20
+    iterations, as one sequential call (one serial chain per lane) and as a
+    time-parallel split call (jump-ahead, 4096 segments); outputs compared."""
+    S, n = 32, 1 << 20
+    seq = ci.States(S, variant="bbs", comb_size=32, seed=SEED_BBS, first_stream=rank * S)
+    spl = ci.States(S, variant="bbs", comb_size=32, seed=SEED_BBS, first_stream=rank * S)
+    out_seq = torch.empty((S, n), dtype=torch.int32, device=dev)
+    out_spl = torch.empty_like(out_seq)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier_sync()
+    a.record(stream)
+    seq.generate(n, out=out_seq)
+    b.record(stream)
+    barrier_sync()
+    ms_seq = max_over_ranks(a.elapsed_time(b))
+    spl.generate_split(n, out=out_spl)  # builds the jump tables once
+    equal = bool(torch.equal(out_seq, out_spl))
+    spl.free()
+    steps = max(3, min(args.steps, 10))
+    evs = []
+    for _ in range(steps):
+        st = ci.States(S, variant="bbs", comb_size=32, seed=SEED_BBS, first_stream=rank * S)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.generate_split(n, out=out_spl)
+        e1.record(stream)
+        evs.append((e0, e1))
+        torch.cuda.synchronize()
+        st.free()
+    ms_spl = max_over_ranks(statistics.median(x.elapsed_time(y) for x, y in evs))
+    seq.free()
+    return {"workload": "32 BBS streams (one warp) x 2^20 iterations, seed 3, written (128 MiB)",
+            "sequential_ms": ms_seq, "split_ms": ms_spl, "speedup": ms_seq / ms_spl, "equal": equal,
+            "split_value": world * S * n / (ms_spl / 1e3), "unit": "uint32/s"}
 
 
 def bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world):
@@ -791,7 +830,7 @@ def _serving_run(ci, reqs, arena_gib, hold=None, **cfg):
                           "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                           "mean_ms": float(lat_ms.mean()), "waves": stats["waves"], "units": stats["units"],
                           "gpu_busy_s": stats["gpu_ns"] / 1e9, "max_wave_units": stats["max_wave_units"],
-                          "arena_peak_gib": stats["arena_peak"] / 2**30}
+                          "arena_peak_gib": stats["arena_peak"] / 2**30, "split_jobs": stats["split_jobs"]}
 
 
 def _plain_per_request(torch, ci, reqs):
@@ -861,6 +900,15 @@ def bench_serving(args):
         srv.close()
         r.update({"fraction_of_saturation": frac, "offered_req_per_s": rate})
         sweep.append(r)
+    # the same sweep points with long narrow requests sliced into waves (no
+    # time-parallel split jobs), to show what splitting does to the tail
+    no_split = []
+    for frac in [0.5, 1.0]:
+        rate = frac * sat["steady_req_per_s"]
+        srv, _, r = _serving_run(ci, at_rate(rate), 64, split_min_slices=2**64 - 1)
+        srv.close()
+        r.update({"fraction_of_saturation": frac, "offered_req_per_s": rate})
+        no_split.append(r)
     # plain form: a loop issuing, per request, the state initialisation (new
     # streams, state in torch memory) and ONE generation launch, asynchronously
     # on one stream; timed from the first issue to the end of the last launch
@@ -896,7 +944,8 @@ def bench_serving(args):
         "config": {"workload": "%d requests per rate, seed 5: lognormal sizes (median 2^16, sigma 2, cap 2^28), "
                                "S = 2^clamp(floor(log2 n) - 10, 0, 16), 30%% continuations, 80%% xor128 / 20%% BBS, "
                                "64 GiB arena" % n},
-        "saturation": sat, "sweep": sweep, "plain_per_request": plain, "single_slot_server": single,
+        "saturation": sat, "sweep": sweep, "sweep_without_split_jobs": no_split, "plain_per_request": plain,
+        "single_slot_server": single,
         "served_over_plain": sat["steady_value"] / plain["value"],
         "oracle_sample": {"requests": sorted(sample), "continuations": len(set(conts[:12])), "equal": bool(equal)},
         "clocks": clk, "autotuned_batch": tuned["batch"],

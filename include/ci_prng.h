@@ -281,7 +281,9 @@ ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, voi
  * Slicing a stream over waves is exact: each result equals the one-call
  * result whether the request runs alone or in any mix.  (CI_VAR_BBS16, whose
  * outputs depend on call boundaries, runs each request as one slice: one
- * call.)  Stream state stays
+ * call.)  Long requests over few streams run instead as one time-parallel
+ * split job on the same stream (see ci_generate_split), with the same
+ * results.  Stream state stays
  * resident in the arena between requests; a request may continue the streams
  * of an earlier request. */
 typedef struct ci_server_s *ci_server;
@@ -291,6 +293,11 @@ typedef struct {
     uint32_t max_inflight;  /* waves queued on the GPU at once, 1 or 2 (0: 2)    */
     uint64_t slice_xor;     /* outputs per stream per wave, xor (0: 16384)       */
     uint64_t slice_bbs;     /* outputs per stream per wave, BBS (0: 512)         */
+    uint64_t split_min_slices;  /* a new request of at most 16 warp groups (512
+                               streams) and at least this many slices runs as
+                               one time-parallel job (ci_generate_split) instead
+                               of slices in waves (0: 32; UINT64_MAX: never;
+                               never for CI_VAR_BBS16)                           */
 } ci_server_config;
 
 typedef struct {
@@ -323,6 +330,7 @@ typedef struct {
     uint64_t max_wave_units;          /* largest wave, in work units                 */
     uint64_t host_admit_ns;           /* worker time admitting and seeding           */
     uint64_t host_launch_ns;          /* worker time building and launching waves    */
+    uint64_t split_jobs;              /* requests run as time-parallel split jobs    */
 } ci_server_stats;
 
 /* Creates a server over caller-owned device memory `arena_dev` of arena_bytes

@@ -231,9 +231,11 @@ class Server:
     """A ``ci_server``: continuous-batching serving loop over a device arena
     (a torch uint8 tensor the server sub-allocates for outputs and states)."""
 
-    def __init__(self, arena_bytes: int, max_slots=0, max_inflight=0, slice_xor=0, slice_bbs=0):
+    def __init__(self, arena_bytes: int, max_slots=0, max_inflight=0, slice_xor=0, slice_bbs=0,
+                 split_min_slices=0):
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
-        cfg = _lib.ci_server_config(int(max_slots), int(max_inflight), int(slice_xor), int(slice_bbs))
+        cfg = _lib.ci_server_config(int(max_slots), int(max_inflight), int(slice_xor), int(slice_bbs),
+                                    int(split_min_slices) & (2**64 - 1))
         self.handle = ctypes.c_void_p()
         torch.cuda.synchronize()
         _lib.call("ci_server_create", self.arena.data_ptr(), self.arena.numel(), ctypes.byref(cfg),

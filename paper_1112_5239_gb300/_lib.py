@@ -67,6 +67,7 @@ class ci_server_config(ctypes.Structure):
         ("max_inflight", ctypes.c_uint32),
         ("slice_xor", ctypes.c_uint64),
         ("slice_bbs", ctypes.c_uint64),
+        ("split_min_slices", ctypes.c_uint64),
     ]
 
 
@@ -96,7 +97,8 @@ class ci_result(ctypes.Structure):
 class ci_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "released", "waves", "units",
                                                 "arena_bytes", "arena_used", "arena_peak", "pending", "active", "gpu_ns",
-                                                "max_wave_units", "host_admit_ns", "host_launch_ns")]
+                                                "max_wave_units", "host_admit_ns", "host_launch_ns",
+                                                "split_jobs")]
 
 
 class ci_tune_choice(ctypes.Structure):

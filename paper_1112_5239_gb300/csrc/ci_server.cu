@@ -122,6 +122,17 @@ struct Req {
     BatchTask tmpl;     // this request's queue entry; each wave sets col0 and n
 };
 
+// Requests of at most this many warp groups may run as split jobs.
+constexpr uint64_t kSplitMaxGroups = 16;
+
+// A request run whole as one time-parallel split job (captured under the lock).
+struct SplitJob {
+    uint64_t ticket;
+    ci_states h;
+    uint32_t *out;
+    uint64_t L, K;
+};
+
 // Requests of one stream set (a root request and its continuations) run one
 // at a time, in submission order: the one queued or running is `busy`; later
 // ones wait here and move to the ready queue when it finishes.
@@ -170,6 +181,11 @@ struct ci_server_s {
     std::thread worker;
     cudaStream_t stream = nullptr;       // waves
     cudaStream_t init_stream = nullptr;  // seeding of admitted stream sets, runs beside the waves
+    cudaStream_t split_stream = nullptr; // split jobs, one at a time, beside the waves
+    cudaEvent_t init_last = nullptr;     // the latest seeding pass (split jobs wait for it)
+    std::deque<SplitJob> split_queue;    // worker thread only
+    bool split_busy = false;             // worker thread only
+    Wave split_wave;                     // worker thread only: the split job in flight
     ci_batch batch = nullptr;
     std::deque<Wave> inflight;       // worker thread only
     std::vector<cudaEvent_t> spare;  // worker thread only
@@ -323,6 +339,7 @@ void admit(ci_server_s *s) {  // under lock
                                     cudaMemcpyHostToDevice, s->init_stream);
     if (e == cudaSuccess) e = launch_init_batched(s->init_dev[slot], s->init_n, s->init_lanes, s->init_stream);
     if (e == cudaSuccess) e = cudaEventRecord(s->init_done[slot], s->init_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->init_last, s->init_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->init_done[slot], 0);  // next wave waits
     if (e != cudaSuccess) {  // the new stream sets of this pass were not seeded: fail them
         cuda_fail(e, "batched state initialisation");
@@ -337,7 +354,8 @@ void admit(ci_server_s *s) {  // under lock
     s->init_slot ^= 1;
 }
 
-void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w) {  // under lock
+void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vector<SplitJob> &splits) {
+    // under lock
     for (Req *qp : s->active) {
         Req &q = *qp;
         if (q.enq >= q.L) continue;
@@ -346,6 +364,18 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w) {  // un
         const uint64_t slice = q.variant == CI_VAR_BBS16 ? q.L
                                : q.variant == CI_VAR_BBS ? s->cfg.slice_bbs
                                                          : s->cfg.slice_xor;
+        // long and narrow: the whole request as one split job on the split
+        // stream (its serial chain would otherwise take L / slice waves)
+        if (q.enq == 0 && q.variant != CI_VAR_BBS16 && q.tmpl.ngroups <= kSplitMaxGroups &&
+            q.L / slice >= s->cfg.split_min_slices) {
+            const uint64_t K = split_segments(*q.h, q.L, 0);
+            if (K > 1) {
+                splits.push_back(SplitJob{q.ticket, q.h, q.out, q.L, K});
+                q.enq = q.L;
+                s->st.split_jobs++;
+                continue;
+            }
+        }
         const uint64_t n = std::min(slice, q.L - q.enq);
         tasks.push_back(q.tmpl);
         BatchTask &tk = tasks.back();
@@ -358,11 +388,67 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w) {  // un
     }
 }
 
+// Split jobs run on their own stream, one at a time, so that waves keep
+// running beside them.  A job waits for the latest seeding pass (which covers
+// the seeding of its own streams; a continuation's streams were last advanced
+// by a request that had finished before it was admitted).  Worker thread, no
+// lock held.
+void start_split_job(ci_server_s *s) {
+    if (s->split_busy || s->split_queue.empty()) return;
+    const SplitJob j = s->split_queue.front();
+    s->split_queue.pop_front();
+    while (s->spare.size() < 2) {
+        cudaEvent_t ev;
+        cudaEventCreate(&ev);
+        s->spare.push_back(ev);
+    }
+    Wave w;
+    w.start = s->spare.back();
+    s->spare.pop_back();
+    w.ev = s->spare.back();
+    s->spare.pop_back();
+    w.members.push_back(j.ticket);
+    w.finishing.push_back(j.ticket);
+    ci_status rc = cudaStreamWaitEvent(s->split_stream, s->init_last, 0) == cudaSuccess ? CI_OK : CI_E_CUDA;
+    if (rc == CI_OK && cudaEventRecord(w.start, s->split_stream) != cudaSuccess) rc = CI_E_CUDA;
+    if (rc == CI_OK) rc = split_launch(*j.h, j.L, CI_SINK_WRITTEN, j.out, j.L, 0, nullptr, j.K, s->split_stream);
+    if (rc == CI_OK && cudaEventRecord(w.ev, s->split_stream) != cudaSuccess) rc = CI_E_CUDA;
+    if (rc != CI_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        finish_request(s, j.ticket, rc);
+        s->spare.push_back(w.ev);
+        s->spare.push_back(w.start);
+        s->cv_done.notify_all();
+        return;
+    }
+    s->split_wave = std::move(w);
+    s->split_busy = true;
+}
+
+void poll_split_job(ci_server_s *s) {
+    if (!s->split_busy || cudaEventQuery(s->split_wave.ev) != cudaSuccess) return;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->split_wave.start, s->split_wave.ev);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->st.gpu_ns += (uint64_t)(ms * 1e6);
+        for (uint64_t t : s->split_wave.finishing) finish_request(s, t, CI_OK);
+    }
+    s->cv_done.notify_all();
+    s->spare.push_back(s->split_wave.ev);
+    s->spare.push_back(s->split_wave.start);
+    s->split_wave = Wave();
+    s->split_busy = false;
+}
+
 void worker_main(ci_server_s *s) {
     cudaSetDevice(s->device);
     std::vector<BatchTask> tasks;
+    std::vector<SplitJob> splits;
     for (;;) {
         while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().ev) == cudaSuccess) retire_front(s);
+        poll_split_job(s);
+        start_split_job(s);
         tasks.clear();
         Wave w;
         {
@@ -377,22 +463,26 @@ void worker_main(ci_server_s *s) {
                     any = true;
                 }
                 if (any) s->cv_done.notify_all();
-                if (s->active.empty() && s->inflight.empty()) break;
+                if (s->active.empty() && s->inflight.empty() && !s->split_busy && s->split_queue.empty()) break;
             }
             const uint64_t ta = now_ns();
             admit(s);
             const uint64_t tb = now_ns();
             s->st.host_admit_ns += tb - ta;
-            if (s->inflight.size() < s->cfg.max_inflight) build_wave(s, tasks, w);
+            if (s->inflight.size() < s->cfg.max_inflight) build_wave(s, tasks, w, splits);
             s->st.host_launch_ns += now_ns() - tb;
-            if (tasks.empty()) {
-                if (s->inflight.empty())
+            if (tasks.empty() && splits.empty()) {
+                if (s->inflight.empty() && !s->split_busy)
                     s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
                 else
                     s->cv_work.wait_for(lk, std::chrono::microseconds(20));
                 continue;
             }
         }
+        for (const SplitJob &j : splits) s->split_queue.push_back(j);
+        splits.clear();
+        start_split_job(s);
+        if (tasks.empty()) continue;
         while (s->spare.size() < 2) {
             cudaEvent_t ev;
             cudaEventCreate(&ev);
@@ -544,13 +634,21 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     if (c.slice_bbs == 0) c.slice_bbs = 512;
     c.slice_xor = std::max<uint64_t>(4, c.slice_xor & ~3ull);  // keep 16-byte store alignment
     c.slice_bbs = std::max<uint64_t>(4, c.slice_bbs & ~3ull);
+    if (c.split_min_slices == 0) c.split_min_slices = 32;
     s->cfg = c;
     std::memset(&s->st, 0, sizeof s->st);
     s->st.arena_bytes = s->arena.size();
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->init_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->split_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->init_last, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(s->init_last, s->init_stream);
+    if (e == cudaSuccess && c.split_min_slices != UINT64_MAX) e = split_prepare(s->split_stream);
     if (e != cudaSuccess) {
         if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->init_stream) cudaStreamDestroy(s->init_stream);
+        if (s->split_stream) cudaStreamDestroy(s->split_stream);
+        if (s->init_last) cudaEventDestroy(s->init_last);
         delete s;
         return cuda_fail(e, "server streams");
     }
@@ -558,6 +656,8 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     if (rc != CI_OK) {
         cudaStreamDestroy(s->stream);
         cudaStreamDestroy(s->init_stream);
+        cudaStreamDestroy(s->split_stream);
+        cudaEventDestroy(s->init_last);
         delete s;
         return rc;
     }
@@ -577,6 +677,8 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
         ci_batch_destroy(s->batch);
         cudaStreamDestroy(s->stream);
         cudaStreamDestroy(s->init_stream);
+        cudaStreamDestroy(s->split_stream);
+        cudaEventDestroy(s->init_last);
         delete s;
         return e == cudaErrorMemoryAllocation ? fail(CI_E_NOMEM, "server buffers") : cuda_fail(e, "server buffers");
     }
@@ -736,6 +838,7 @@ ci_status ci_server_destroy(ci_server s) {
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->init_stream);
     cudaStreamSynchronize(s->stream);
+    cudaStreamSynchronize(s->split_stream);
     for (auto &kv : s->states)
         if (!kv.second.released && kv.second.h) ci_free_states(kv.second.h);
     for (cudaEvent_t ev : s->spare) cudaEventDestroy(ev);
@@ -747,6 +850,8 @@ ci_status ci_server_destroy(ci_server s) {
     ci_batch_destroy(s->batch);
     cudaStreamDestroy(s->init_stream);
     cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->split_stream);
+    cudaEventDestroy(s->init_last);
     s->magic = 0;
     delete s;
     return CI_OK;

@@ -279,31 +279,37 @@ __global__ void __launch_bounds__(128) k_split_carry(SegSpace seg, uint32_t K, u
         }
     }
     const bool bbs = s0.u64 != nullptr;
-    uint32_t cs = 0, cx = 0;  // true (slot, x) at the start of the current segment
-    uint32_t pe_s = s0.u32[F_SLOT * P + l], pe_x = s0.u32[F_X * P + l];
-    uint32_t own[kOwnWords];
-    for (int w = 0; w < kOwnWords; ++w) own[w] = s0.u32[(F_A + w) * P + l];
-    uint64_t own_y = bbs ? s0.u64[G_Y * P + l] : 0;
-    for (uint32_t k = 1; k < K; ++k) {
+    // Segment k's end values are loaded one step ahead (iteration k writes
+    // only segment k's fields), so the scan's serial chain is the two
+    // 32-shuffle products, not a global-memory round trip per segment.
+    struct End {
+        uint32_t s, x, own[kOwnWords];
+        uint64_t y;
+    };
+    auto load_end = [&](uint32_t k) {
         const DevState d = seg.at(k);
-        const uint32_t ns = pe_s ^ mat_vec(Q, cs);
-        const uint32_t nx = pe_x ^ cx ^ mat_vec(S, cs);
+        End e;
+        e.s = d.u32[F_SLOT * P + l];
+        e.x = d.u32[F_X * P + l];
+        for (int w = 0; w < kOwnWords; ++w) e.own[w] = d.u32[(F_A + w) * P + l];
+        e.y = bbs ? d.u64[G_Y * P + l] : 0;
+        return e;
+    };
+    uint32_t cs = 0, cx = 0;  // true (slot, x) at the start of the current segment
+    End prev = load_end(0), cur = load_end(1);
+    for (uint32_t k = 1; k < K; ++k) {
+        const End nxt = k + 1 < K ? load_end(k + 1) : cur;
+        const uint32_t ns = prev.s ^ mat_vec(Q, cs);
+        const uint32_t nx = prev.x ^ cx ^ mat_vec(S, cs);
         cs = ns;
         cx = nx;
-        pe_s = d.u32[F_SLOT * P + l];
-        pe_x = d.u32[F_X * P + l];
+        const DevState d = seg.at(k);
         d.u32[F_SLOT * P + l] = cs;
         d.u32[F_X * P + l] = cx;
-        for (int w = 0; w < kOwnWords; ++w) {
-            const uint32_t t = d.u32[(F_A + w) * P + l];
-            d.u32[(F_A + w) * P + l] = own[w];
-            own[w] = t;
-        }
-        if (bbs) {
-            const uint64_t t = d.u64[G_Y * P + l];
-            d.u64[G_Y * P + l] = own_y;
-            own_y = t;
-        }
+        for (int w = 0; w < kOwnWords; ++w) d.u32[(F_A + w) * P + l] = prev.own[w];
+        if (bbs) d.u64[G_Y * P + l] = prev.y;
+        prev = cur;
+        cur = nxt;
     }
 }
 
@@ -372,48 +378,50 @@ int split_block_count(uint64_t items) {
 }  // namespace
 }  // namespace ci
 
-extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, void *out_dev,
-                                       uint64_t out_capacity, uint32_t n_segments, void *cuda_stream) {
-    using namespace ci;
-    if (!valid_handle(h)) return fail(CI_E_STATE, "invalid states handle");
-    if (h->variant == CI_VAR_BBS16)
-        return fail(CI_E_STATE, "CI_VAR_BBS16 outputs depend on call boundaries; it cannot be split");
-    if (sink != CI_SINK_WRITTEN && sink != CI_SINK_QC && sink != CI_SINK_DIGEST)
-        return fail(CI_E_INVAL, "unknown sink");
-    if (n == 0) return CI_OK;
-    if (!out_dev) return fail(CI_E_INVAL, "output is NULL");
-    if (sink == CI_SINK_WRITTEN && (n > ~0ull / h->S || out_capacity < h->S * n))
-        return fail(CI_E_INVAL, "out_capacity is smaller than n_streams * n");
-    if (sink == CI_SINK_QC && (n & 1ull)) return fail(CI_E_INVAL, "quarter-circle sink needs an even length");
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
-    const uint64_t groups = h->P / 32;
+namespace ci {
 
-    uint64_t K = n_segments;
+cudaError_t split_prepare(cudaStream_t stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_split_mu);
+        if (!split_batch(dev)) return cudaErrorMemoryAllocation;
+    }
+    return ensure_jump_tables(stream);
+}
+
+uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested) {
+    const uint64_t groups = h.P / 32;
+    uint64_t K = requested;
     if (K == 0) {  // fill about four waves of resident warps
         const uint64_t target = (uint64_t)sm_count() * 64;
         K = std::max<uint64_t>(1, target / groups);
         K = std::min<uint64_t>(K, std::max<uint64_t>(1, n / kMinSegment));
     }
     K = std::min<uint64_t>(K, kMaxSegments);
-    uint64_t len = (n + K - 1) / K;
-    len = (len + 31) / 32 * 32;  // whole staging tiles and 16-byte column offsets
-    K = (n + len - 1) / len;
-    if (K <= 1) {
-        if (sink == CI_SINK_QC) return ci_generate_fused_qc(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
-        if (sink == CI_SINK_DIGEST) return ci_generate_digest(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
-        return h->variant == CI_VAR_BBS
-                   ? ci_generate_bbs(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream)
-                   : ci_generate(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream);
-    }
-    const uint64_t len_last = n - (K - 1) * len;
+    const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;  // whole staging tiles, 16-byte column offsets
+    return (n + len - 1) / len;
+}
 
+ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
+                       uint64_t *aux, uint64_t K, cudaStream_t stream) {
+    const ci_states_s *h = &hs;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     std::lock_guard<std::mutex> lk(g_split_mu);
     ci_batch batch = split_batch(dev);
     if (!batch) return fail(CI_E_NOMEM, "could not create the split batch");
+    std::vector<BatchTask> tasks;
+    if (K <= 1) {  // one segment: a single task of the batched kernel
+        tasks.push_back(make_task(*h, n, sink, out, aux, ld, col0));
+        return batch_launch_tasks(batch, tasks.data(), 1, stream, false);
+    }
     if ((e = ensure_jump_tables(stream)) != cudaSuccess) return cuda_fail(e, "jump tables");
+    const uint64_t groups = h->P / 32;
+    const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;
+    const uint64_t len_last = n - (K - 1) * len;
 
     const uint64_t stride = (h->bytes + 255) / 256 * 256;
     const uint64_t res_bytes = 8ull * K * h->P;  // per-segment consumer results
@@ -438,7 +446,6 @@ extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, vo
     k_split_setup<<<split_block_count(K * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl);
     if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split setup");
 
-    std::vector<BatchTask> tasks;
     if (st == CI_OK) {  // pass 1: particular solutions of segments 0 .. K-2
         tasks.reserve(K);
         for (uint64_t k = 0; k + 1 < K; ++k)
@@ -461,7 +468,7 @@ extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, vo
             const ci_states_s &sh = k == 0 ? *h : segs[k];
             const uint64_t nk = k + 1 == K ? len_last : len;
             if (sink == CI_SINK_WRITTEN)
-                tasks.push_back(make_task(sh, nk, sink, static_cast<uint32_t *>(out_dev), nullptr, n, k * len));
+                tasks.push_back(make_task(sh, nk, sink, out, nullptr, ld, col0 + k * len));
             else
                 tasks.push_back(make_task(sh, nk, sink, nullptr, res3 + k * h->P, nk, 0));
         }
@@ -471,10 +478,38 @@ extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, vo
         k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view());
         if (sink != CI_SINK_WRITTEN)
             k_split_combine<<<(unsigned)((h->S + 255) / 256), 256, 0, stream>>>(
-                res3, static_cast<uint64_t *>(out_dev), h->P, h->S, (uint32_t)K, len, len_last,
-                sink == CI_SINK_DIGEST);
+                res3, aux, h->P, h->S, (uint32_t)K, len, len_last, sink == CI_SINK_DIGEST);
         if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split finish");
     }
     cudaFreeAsync(ws, stream);
     return st;
+}
+
+}  // namespace ci
+
+extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, void *out_dev,
+                                       uint64_t out_capacity, uint32_t n_segments, void *cuda_stream) {
+    using namespace ci;
+    if (!valid_handle(h)) return fail(CI_E_STATE, "invalid states handle");
+    if (h->variant == CI_VAR_BBS16)
+        return fail(CI_E_STATE, "CI_VAR_BBS16 outputs depend on call boundaries; it cannot be split");
+    if (sink != CI_SINK_WRITTEN && sink != CI_SINK_QC && sink != CI_SINK_DIGEST)
+        return fail(CI_E_INVAL, "unknown sink");
+    if (n == 0) return CI_OK;
+    if (!out_dev) return fail(CI_E_INVAL, "output is NULL");
+    if (sink == CI_SINK_WRITTEN && (n > ~0ull / h->S || out_capacity < h->S * n))
+        return fail(CI_E_INVAL, "out_capacity is smaller than n_streams * n");
+    if (sink == CI_SINK_QC && (n & 1ull)) return fail(CI_E_INVAL, "quarter-circle sink needs an even length");
+    const uint64_t K = split_segments(*h, n, n_segments);
+    if (K <= 1) {  // unsplit: the tuned single-call kernels
+        if (sink == CI_SINK_QC) return ci_generate_fused_qc(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
+        if (sink == CI_SINK_DIGEST) return ci_generate_digest(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
+        return h->variant == CI_VAR_BBS
+                   ? ci_generate_bbs(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream)
+                   : ci_generate(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream);
+    }
+    if (sink == CI_SINK_WRITTEN)
+        return split_launch(*h, n, sink, static_cast<uint32_t *>(out_dev), n, 0, nullptr, K,
+                            (cudaStream_t)cuda_stream);
+    return split_launch(*h, n, sink, nullptr, n, 0, static_cast<uint64_t *>(out_dev), K, (cudaStream_t)cuda_stream);
 }

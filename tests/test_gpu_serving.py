@@ -153,3 +153,27 @@ def test_poisson_mix_with_continuations_against_oracle(env):
     lat = np.array([(x.done_ns - x.submit_ns) / 1e6 for x in results])
     assert np.all(lat > 0)
     srv.close()
+
+
+def test_long_narrow_requests_run_as_split_jobs(env):
+    """Long requests over few streams (and a long continuation of one) run as
+    time-parallel split jobs; outputs equal those of a server that slices
+    them into waves, and the oracle's."""
+    torch, ci = env
+    specs = [dict(n_per_stream=1 << 15, n_streams=32, variant="bbs", seed=31),  # 64 slices of 512
+             dict(n_per_stream=1 << 20, n_streams=40, variant="xor", seed=32),  # 64 slices of 16384
+             dict(n_per_stream=3000, n_streams=100, variant="xor", seed=33)]     # ordinary
+    outs = {}
+    for split in (0, 2**64 - 1):
+        srv = ci.Server(1 << 30, split_min_slices=split)
+        ts = [srv.submit(**sp) for sp in specs]
+        tc = srv.submit(1 << 15, continue_ticket=ts[0])
+        outs[split] = [u32(srv.output(srv.wait(t))) for t in ts + [tc]]
+        assert srv.stats()["split_jobs"] == (3 if split == 0 else 0)
+        srv.close()
+    for a, b in zip(outs[0], outs[2**64 - 1]):
+        assert np.array_equal(a, b)
+    ref = oracle_gen("bbs", "xor128", 32, 31, 0, 32).streams(2 << 15)
+    assert np.array_equal(np.concatenate([outs[0][0], outs[0][3]], axis=1), ref)
+    assert np.array_equal(outs[0][1], _oracle_rows("xor", 32, 40, 1 << 20))
+    assert np.array_equal(outs[0][2], _oracle_rows("xor", 33, 100, 3000))
