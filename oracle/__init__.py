@@ -15,7 +15,9 @@ Parity-unpinned readings (values not fixed by the paper): the splitmix64
 seeding that stands in for the paper's ISAAC host initialisation, and the
 xor128 shift triple (from Marsaglia's "Xorshift RNGs", only named by the
 paper); both are checked structurally (bijectivity and avalanche; full period
-as a GF(2)-linear map), not against printed values.
+as a GF(2)-linear map), not against printed values.  Likewise Listing 1's
+three xor-likes: their shift triples are pinned by full period on 32-bit
+words, but their 64-bit use, output functions and static seeds are readings.
 """
 from __future__ import annotations
 
@@ -49,6 +51,11 @@ LANE_DTYPE = np.dtype(
     ],
     align=True,
 )
+
+
+# Layout of the C struct orc_naive_lane (Listing 1 / Algorithm 3 state).
+NAIVE_DTYPE = np.dtype([("xs", "<u8", (5,)), ("xo", "<u8", (4,)), ("xw", "<u8", (5,)), ("d", "<u8"),
+                        ("x", "<u4"), ("pad", "<u4")], align=True)
 
 
 def build(force: bool = False) -> str:
@@ -91,12 +98,23 @@ def lib() -> ctypes.CDLL:
             "orc_bg_encrypt": (u32, [u64, u32, u64, u64, vp, vp, vp]),
             "orc_bg_recover_x0": (u64, [u64, u64, u64, u64]),
             "orc_bg_decrypt": (None, [u64, u64, u32, u64, u64, vp, vp]),
+            "orc_xs160_step32": (u32, [vp]),
+            "orc_xs160_step64": (u64, [vp]),
+            "orc_xor128w_step32": (u32, [vp]),
+            "orc_xor128w_step64": (u64, [vp]),
+            "orc_xorwow_step32": (u32, [vp, vp]),
+            "orc_xorwow_step64": (u64, [vp, vp]),
+            "orc_listing1_combine": (u32, [u32, u64, u64, u64]),
+            "orc_naive_lane_size": (u32, []),
+            "orc_listing1_run": (None, [u64, vp]),
+            "orc_naive_init_lanes": (None, [u64, u64, u64, vp]),
+            "orc_naive_run": (None, [vp, u64, u64, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
-        if L.orc_lane_size() != LANE_DTYPE.itemsize:
+        if L.orc_lane_size() != LANE_DTYPE.itemsize or L.orc_naive_lane_size() != NAIVE_DTYPE.itemsize:
             raise RuntimeError("oracle lane layout mismatch")
         _lib = L
     return _lib
@@ -199,6 +217,44 @@ def bg_decrypt(p: int, q: int, S0: int, y: int, c: np.ndarray) -> np.ndarray:
     m = np.zeros_like(c)
     lib().orc_bg_decrypt(p, q, S0, y, c.size, _ptr(c), _ptr(m))
     return m
+
+
+def naive_step(kind: str, words, bits: int = 64, d: int = 0):
+    """One step of a Listing 1 xor-like ("xs160", "xor128", "xorwow") on
+    `words` (32- or 64-bit); returns (new words, output, new d)."""
+    dt = np.uint64 if bits == 64 else np.uint32
+    w = np.array(words, dtype=dt).copy()
+    fn = getattr(lib(), {"xs160": "orc_xs160_step", "xor128": "orc_xor128w_step",
+                         "xorwow": "orc_xorwow_step"}[kind] + str(bits))
+    if kind == "xorwow":
+        dd = np.array([d], dtype=dt)
+        out = int(fn(_ptr(w), _ptr(dd)))
+        return w, out, int(dd[0])
+    return w, int(fn(_ptr(w))), d
+
+
+def listing1_combine(x: int, t1: int, t2: int, t3: int) -> int:
+    return int(lib().orc_listing1_combine(x, t1, t2, t3))
+
+
+def listing1_run(n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint32)
+    lib().orc_listing1_run(n, _ptr(out))
+    return out
+
+
+def naive_init_lanes(seed: int, lane0: int, nl: int) -> np.ndarray:
+    lanes = np.zeros(nl, dtype=NAIVE_DTYPE)
+    lib().orc_naive_init_lanes(seed & (2**64 - 1), lane0, nl, _ptr(lanes))
+    return lanes
+
+
+def naive_run(lanes: np.ndarray, n: int, want_out: bool = True):
+    """Algorithm 3: advances `lanes` by n outputs; returns out (nl, n) or None."""
+    nl = lanes.shape[0]
+    out = np.zeros((nl, n), dtype=np.uint32) if want_out else None
+    lib().orc_naive_run(_ptr(lanes), nl, n, _ptr(out) if out is not None else None)
+    return out
 
 
 # ---------------------------------------------------------------- generator

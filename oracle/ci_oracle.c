@@ -28,6 +28,9 @@
  *     from the BBS state's low bits) ............... orc_run (BBS variant)
  *   Quarter-circle consumer of output pairs ......... orc_run (counts)
  *   Chaotic Blum-Goldwasser (Sec. 9.2) ............ orc_bg_encrypt, orc_bg_decrypt
+ *   Listing 1 (sequential CIPRNG over three 64-bit
+ *     xor-likes) and Algorithm 3 (each GPU thread
+ *     runs Listing 1, no mixing) ................... orc_listing1_*, orc_naive_*
  *   Algorithm 5 as printed (8 BBS generators per
  *     thread, 16-bit moduli, 4 bits per squaring,
  *     arrays chosen per call, rotation on store) ... orc_run (variant 2)
@@ -677,4 +680,136 @@ void orc_bg_decrypt(uint64_t p, uint64_t q, uint32_t S0, uint64_t y, uint64_t L,
         m[i] = (uint8_t)(c[i] ^ k);
         x = orc_bbs_step(x, N);
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Listing 1 and Algorithm 3: the "naive" generator.  Each output XORs into   */
+/* the 32-bit x the low and the high halves of one step of each of three      */
+/* xor-like generators with 64-bit words: Marsaglia's xorshift with five      */
+/* words (output (y + y + 1) v), xor128 (four words) and xorwow (five words   */
+/* and a Weyl counter d += 362437, output d + v).  The paper names them and    */
+/* cites Marsaglia's "Xorshift RNGs" without printing them; each recurrence   */
+/* is written once, for a word type T, and the 32-bit instances (for which    */
+/* Marsaglia chose the shifts: full periods 2^160 - 1 and 2^128 - 1) pin the  */
+/* shift constants the 64-bit instances share.                                */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_DEFINE_NAIVE_XORLIKES(T, SUF)                                      \
+    T orc_xs160_step##SUF(T *s)                                                \
+    {                                                                          \
+        T t = s[0] ^ (s[0] >> 7);                                              \
+        s[0] = s[1];                                                           \
+        s[1] = s[2];                                                           \
+        s[2] = s[3];                                                           \
+        s[3] = s[4];                                                           \
+        s[4] = (s[4] ^ (s[4] << 6)) ^ (t ^ (t << 13));                         \
+        return (T)((T)(s[1] + s[1] + 1u) * s[4]);                              \
+    }                                                                          \
+    T orc_xor128w_step##SUF(T *s)                                              \
+    {                                                                          \
+        T t = s[0] ^ (s[0] << 11);                                             \
+        s[0] = s[1];                                                           \
+        s[1] = s[2];                                                           \
+        s[2] = s[3];                                                           \
+        s[3] = (s[3] ^ (s[3] >> 19)) ^ (t ^ (t >> 8));                         \
+        return s[3];                                                           \
+    }                                                                          \
+    T orc_xorwow_step##SUF(T *s, T *d)                                         \
+    {                                                                          \
+        T t = s[0] ^ (s[0] >> 2);                                              \
+        s[0] = s[1];                                                           \
+        s[1] = s[2];                                                           \
+        s[2] = s[3];                                                           \
+        s[3] = s[4];                                                           \
+        s[4] = (s[4] ^ (s[4] << 4)) ^ (t ^ (t << 1));                          \
+        *d = (T)(*d + 362437u);                                                \
+        return (T)(*d + s[4]);                                                 \
+    }
+
+ORC_DEFINE_NAIVE_XORLIKES(uint32_t, 32)
+ORC_DEFINE_NAIVE_XORLIKES(uint64_t, 64)
+
+/* Listing 1's six XORs: the low and high halves of t1, t2 and t3. */
+uint32_t orc_listing1_combine(uint32_t x, uint64_t t1, uint64_t t2, uint64_t t3)
+{
+    x ^= (uint32_t)t1;
+    x ^= (uint32_t)(t2 >> 32);
+    x ^= (uint32_t)(t3 >> 32);
+    x ^= (uint32_t)t2;
+    x ^= (uint32_t)(t1 >> 32);
+    x ^= (uint32_t)t3;
+    return x;
+}
+
+typedef struct {
+    uint64_t xs[5];   /* xorshift (five words) */
+    uint64_t xo[4];   /* xor128                */
+    uint64_t xw[5];   /* xorwow                */
+    uint64_t d;       /* xorwow's Weyl counter */
+    uint32_t x;       /* the CI state          */
+    uint32_t pad;
+} orc_naive_lane;
+
+uint32_t orc_naive_lane_size(void) { return (uint32_t)sizeof(orc_naive_lane); }
+
+static uint32_t orc_naive_next(orc_naive_lane *L)
+{
+    const uint64_t t1 = orc_xs160_step64(L->xs);
+    const uint64_t t2 = orc_xor128w_step64(L->xo);
+    const uint64_t t3 = orc_xorwow_step64(L->xw, &L->d);
+    L->x = orc_listing1_combine(L->x, t1, t2, t3);
+    return L->x;
+}
+
+/* Listing 1 as a sequential program: x starts at 123123123 and the three
+ * xor-likes at the static seeds of Marsaglia's listings (x, y, z, w, v =
+ * 123456789, 362436069, 521288629, 88675123, 5783321; d = 6615241). */
+void orc_listing1_run(uint64_t n, uint32_t *out)
+{
+    orc_naive_lane L;
+    const uint64_t seeds[5] = {123456789u, 362436069u, 521288629u, 88675123u, 5783321u};
+    for (int i = 0; i < 5; ++i) {
+        L.xs[i] = seeds[i];
+        L.xw[i] = seeds[i];
+    }
+    for (int i = 0; i < 4; ++i) L.xo[i] = seeds[i];
+    L.d = 6615241u;
+    L.x = 123123123u;
+    for (uint64_t i = 0; i < n; ++i) out[i] = orc_naive_next(&L);
+}
+
+/* Algorithm 3's per-thread parameters (ISAAC on the host in the paper; the
+ * counter-based splitmix64 draws here): lane s takes draws 0-4 for the
+ * xorshift words, 5-8 for xor128, 9-13 for xorwow, 14 for d and the low half
+ * of 15 for x.  An all-zero word set (never drawn in practice) becomes 1, 0, ... */
+void orc_naive_init_lanes(uint64_t seed, uint64_t lane0, uint64_t nl, orc_naive_lane *lanes)
+{
+    for (uint64_t i = 0; i < nl; ++i) {
+        orc_naive_lane *L = &lanes[i];
+        const uint64_t s = lane0 + i;
+        uint64_t k = 0, any;
+        any = 0;
+        for (int w = 0; w < 5; ++w) any |= (L->xs[w] = orc_lane_draw(seed, s, k++));
+        if (!any) L->xs[0] = 1;
+        any = 0;
+        for (int w = 0; w < 4; ++w) any |= (L->xo[w] = orc_lane_draw(seed, s, k++));
+        if (!any) L->xo[0] = 1;
+        any = 0;
+        for (int w = 0; w < 5; ++w) any |= (L->xw[w] = orc_lane_draw(seed, s, k++));
+        if (!any) L->xw[0] = 1;
+        L->d = orc_lane_draw(seed, s, k++);
+        L->x = (uint32_t)orc_lane_draw(seed, s, k++);
+        L->pad = 0;
+    }
+}
+
+/* Algorithm 3: every lane (thread) runs Listing 1 on its own state, with no
+ * exchange between lanes; out[l * n + i] is lane l's (i + 1)-th output. */
+void orc_naive_run(orc_naive_lane *lanes, uint64_t nl, uint64_t n, uint32_t *out)
+{
+    for (uint64_t l = 0; l < nl; ++l)
+        for (uint64_t i = 0; i < n; ++i) {
+            const uint32_t v = orc_naive_next(&lanes[l]);
+            if (out) out[l * n + i] = v;
+        }
 }
