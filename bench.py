@@ -416,6 +416,7 @@ def main():
         result["e2e"] = bench_e2e(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
         result["bg"] = bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["split"] = bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
+        result["naive"] = bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
         if rank == 0 and world == 1:
             r, n, dt = oracle_sample(args.cpu_sample_streams)
             result["cpu_baseline"] = {"value": r, "unit": "uint32/s", "cores": 1, "kind": "oracle",
@@ -592,6 +593,34 @@ def bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, 
             "workload": "2^20 messages x 1024 chunks (w = 5 bits each, one per byte), 62-bit Blum moduli from a "
                         "pool of 4096 keys, seed %d; one Barrett squaring per chunk" % SEED_BG,
             "modsq_per_s": {"encrypt": chunks / (ms_e / 1e3), "decrypt": chunks / (ms_d / 1e3)}}
+
+
+def bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world):
+    """The paper's naive generator (Listing 1 per stream, Algorithm 3) on the
+    main workload's shape: 2^20 streams x 4096 outputs written in 16 launches
+    of 256 per stream (1 GiB each)."""
+    st = ci.NaiveStates(S_MAIN, seed=SEED_MAIN, first_stream=first)
+    out = torch.empty((S_MAIN, CHUNK), dtype=torch.int32, device=dev)
+    for _ in range(min(args.warmup, 3)):
+        st.generate(CHUNK, out=out)
+    barrier_sync()
+    steps = max(1, min(args.steps, 5))
+    evs = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(L_MAIN // CHUNK):
+            st.generate(CHUNK, out=out)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.nvtx.range_pop()
+    barrier_sync()
+    ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
+    del out
+    return {"value": world * S_MAIN * L_MAIN / (ms / 1e3), "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
+            "workload": "Listing 1 run by each of 2^20 streams (Algorithm 3: three 64-bit xor-likes, no mixing), "
+                        "4096 outputs each in 16 written launches of 256"}
 
 
 def bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):

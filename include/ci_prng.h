@@ -13,7 +13,9 @@
  *     from the low bits of a Blum Blum Shub generator x_{k+1} = x_k^2 mod M,
  *     with sixteen combination arrays of which each stream uses two;
  *   - Sec. 9.2: the chaotic Blum-Goldwasser cryptosystem built on the same
- *     BBS iteration and Eq. (Oplus) (ci_bg_encrypt / ci_bg_decrypt).
+ *     BBS iteration and Eq. (Oplus) (ci_bg_encrypt / ci_bg_decrypt);
+ *   - Listing 1 / Algorithm 3: the naive generator the paper starts from
+ *     (ci_naive_*).
  *
  * Conventions shared by every call:
  *   - Every function returns a ci_status; nothing throws across the ABI.
@@ -441,6 +443,35 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out);
  * ci_tune_set rejects shapes not allowed for their class (CI_E_INVAL). */
 ci_status ci_tune_get(ci_tune_table *out);
 ci_status ci_tune_set(const ci_tune_table *in);
+
+/* ------------------------------------------------- naive generator */
+
+/* The paper's naive generator (Listing 1 and Algorithm 3, Sec. 5 and
+ * Sec. 6.1): every stream (thread) runs Listing 1 on its own state, with no
+ * exchange between streams.  One output: x ^= the low and high 32-bit halves
+ * of t1, t2, t3, one step each of three xor-likes with 64-bit words, which
+ * the paper cites to Marsaglia without printing them: xorshift with five
+ * words (t = a ^ a >> 7; shift the words; e = (e ^ e << 6) ^ (t ^ t << 13);
+ * output (b + b + 1) e, b the new second word), xor128 (t = a ^ a << 11;
+ * shift; d = (d ^ d >> 19) ^ (t ^ t >> 8); output d) and xorwow (t = a ^ a >> 2;
+ * shift; e = (e ^ e << 4) ^ (t ^ t << 1); w += 362437; output w + e).
+ * The state is caller-owned device memory of ci_naive_state_bytes() bytes
+ * (8-byte aligned; P = n_streams rounded up to 32: fifteen uint64 fields of P
+ * lanes -- xorshift words 0-4, xor128 words 5-8, xorwow words 9-13, the Weyl
+ * counter 14 -- then the uint32 field x).  ci_naive_init seeds stream s from
+ * the counter-based draws of stream first_stream + s (the paper uses ISAAC on
+ * the host): draws 0-4 xorshift, 5-8 xor128, 9-13 xorwow, 14 the counter, the
+ * low half of 15 x.  ci_naive_generate advances every stream by n_per_stream
+ * outputs into out_dev[s * n_per_stream + i] (uint32, caller-owned, at least
+ * n_streams * n_per_stream elements); a call continues where the last one
+ * stopped.  Both are asynchronous on cuda_stream.
+ * Errors: CI_E_INVAL (n_streams outside [1, 2^32], first_stream + n_streams
+ * above 2^32, NULL or short buffers, unaligned state), CI_E_CUDA. */
+ci_status ci_naive_state_bytes(uint64_t n_streams, uint64_t *bytes);
+ci_status ci_naive_init(uint64_t n_streams, uint64_t seed, uint64_t first_stream, void *state_dev,
+                        uint64_t state_bytes, void *cuda_stream);
+ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_stream, uint32_t *out_dev,
+                            uint64_t out_capacity_u32, void *cuda_stream);
 
 /* ---------------------------------------------- time-parallel generation */
 

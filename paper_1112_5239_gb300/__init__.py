@@ -383,6 +383,27 @@ def batch_run_noalloc(items, stream=None) -> None:
     _lib.call("ci_batch_run_noalloc", ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
 
 
+class NaiveStates:
+    """State of the paper's naive generator (Listing 1 run by every stream,
+    Algorithm 3), in a torch uint8 tensor."""
+
+    def __init__(self, n_streams, seed=0, first_stream=0, stream=None):
+        self.n_streams = int(n_streams)
+        nbytes = ctypes.c_uint64()
+        _lib.call("ci_naive_state_bytes", self.n_streams, ctypes.byref(nbytes))
+        self.buf = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+        _lib.call("ci_naive_init", self.n_streams, int(seed) & (2**64 - 1), int(first_stream), self.buf.data_ptr(),
+                  self.buf.numel(), stream_ptr(stream))
+
+    def generate(self, n_per_stream, out=None, stream=None) -> torch.Tensor:
+        n = int(n_per_stream)
+        if out is None:
+            out = torch.empty((self.n_streams, n), dtype=torch.int32, device="cuda")
+        _lib.call("ci_naive_generate", self.buf.data_ptr(), self.n_streams, n, out.data_ptr(), out.numel(),
+                  stream_ptr(stream))
+        return out
+
+
 def _bg_check(name, t, dtype, numel):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
         raise TypeError("%s must be a contiguous CUDA tensor" % name)

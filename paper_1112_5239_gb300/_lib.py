@@ -143,6 +143,9 @@ _SIGNATURES = {
     "ci_batch_destroy": [_VP],
     "ci_batch_run_noalloc": [_VP, _U32, _VP],
     "ci_generate_split": [_VP, _U64, _I32, _VP, _U64, _U32, _VP],
+    "ci_naive_state_bytes": [_U64, _VP],
+    "ci_naive_init": [_U64, _U64, _U64, _VP, _U64, _VP],
+    "ci_naive_generate": [_VP, _U64, _U64, _VP, _U64, _VP],
     "ci_bg_encrypt": [_U64, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "ci_bg_decrypt": [_U64, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "ci_server_create": [_VP, _U64, _VP, _VP],

@@ -80,6 +80,11 @@ def test_version_and_errors_without_gpu(L):
     assert lib.ci_generate(None, 4, None, 0, None) == -6
     assert lib.ci_free_states(None) == 0
     assert lib.ci_generate_split(None, 64, 0, None, 0, 2, None) == -6
+    assert lib.ci_naive_state_bytes(40, ctypes.byref(nbytes)) == 0 and nbytes.value == 124 * 64
+    assert lib.ci_naive_state_bytes(0, ctypes.byref(nbytes)) == -1
+    assert lib.ci_naive_init(40, 1, 0, None, 0, None) == -1
+    assert lib.ci_naive_init(40, 1, 2**32 - 10, ctypes.c_void_p(64), 124 * 64, None) == -1
+    assert lib.ci_naive_generate(ctypes.c_void_p(64), 40, 8, None, 320, None) == -1
 
 
 def test_bg_argument_checks_without_gpu(L):
