@@ -54,7 +54,7 @@ def parse_args():
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
-    ap.add_argument("--profile", choices=["written", "fused", "bbs", "batched", "bg"], default=None,
+    ap.add_argument("--profile", choices=["written", "fused", "bbs", "batched", "bg", "naive"], default=None,
                     help="small case for ncu: autotune, 2 warm-up launches, then 1 launch of one kernel inside "
                          "the NVTX range 'profile'; no timing")
     return ap.parse_args()
@@ -95,6 +95,10 @@ def run_profile_case(kind: str) -> None:
         msg = torch.randint(0, 32, (1 << 18, 1024), dtype=torch.uint8, device="cuda")
         c, y = torch.empty_like(msg), torch.empty(1 << 18, dtype=torch.int64, device="cuda")
         run = lambda: ci.bg_encrypt(N, S0, r, msg, out=c, y=y)  # noqa: E731
+    elif kind == "naive":  # Listing 1 per stream (Algorithm 3), 2^19 streams x 256 written (512 MiB)
+        st = ci.NaiveStates(1 << 19, seed=SEED_MAIN)
+        out = torch.empty((1 << 19, CHUNK), dtype=torch.int32, device="cuda")
+        run = lambda: st.generate(CHUNK, out=out)  # noqa: E731
     else:  # batched: 300 uneven requests (lengths up to 2^12), digest sink, one launch
         from paper_1112_5239_gb300.workloads import batched_requests
 
@@ -284,6 +288,14 @@ def oracle_sample(n_streams: int, reps_chunks: int = L_MAIN // CHUNK, threads: i
 
 
 def host_cpu() -> str:
+    """CPU model of the host (lscpu's model name, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:

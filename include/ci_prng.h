@@ -172,7 +172,10 @@ ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev
  * t |= BBS & {0,1,3,7}[shift] -- 11 modular squarings per output, done with
  * 64x64->128-bit multiplies and Barrett reduction.  The stream's two
  * combination arrays are comb[sel1] and comb[8 + sel2] with sel1 = v & 7,
- * sel2 = (v >> 3) & 7 of its BBS seed v.  Errors as ci_generate
+ * sel2 = (v >> 3) & 7 of its BBS seed v.  A CI_VAR_BBS state with too few
+ * streams to fill the GPU (under about two waves of resident warps) is run as
+ * time segments, as ci_generate_split does, with identical results; that
+ * form allocates a stream-ordered workspace.  Errors as ci_generate
  * (CI_E_STATE for an xor handle). */
 ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out_dev,
                           uint64_t out_capacity_u32, void *cuda_stream);

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "ci_batch.h"
 #include "ci_internal.h"
 
 namespace ci {
@@ -301,6 +302,10 @@ ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, 
     if (n == 0) return CI_OK;
     ci_status st = check_out(s, n, out, cap);
     if (st != CI_OK) return st;
+    // Few streams leave most SMs idle on their serial squaring chains: run the
+    // call as time segments instead (identical results).
+    const uint64_t K = split_auto_bbs(*s, n);
+    if (K > 1) return split_launch(*s, n, CI_SINK_WRITTEN, out, n, 0, nullptr, K, static_cast<cudaStream_t>(stream));
     cudaError_t e = launch_generate(*s, n, out, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? CI_OK : cuda_fail(e, "BBS generation kernel launch");
 }

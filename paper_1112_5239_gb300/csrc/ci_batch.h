@@ -70,6 +70,9 @@ ci_status batch_launch_tasks(ci_batch_s *b, BatchTask *tasks, uint32_t n_tasks, 
 // sequential call.  split_prepare: builds the jump tables and the shared
 // batch for the current device (blocks once on `stream`).
 uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested);
+// Segment count ci_generate_bbs uses on its own: > 1 only for CI_VAR_BBS states
+// that fill less than about two waves of resident warps.
+uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n);
 ci_status split_launch(const ci_states_s &h, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
                        uint64_t *aux, uint64_t K, cudaStream_t stream);
 cudaError_t split_prepare(cudaStream_t stream);

@@ -16,14 +16,17 @@
 //      with the own generator jumped ahead by k len iterations (GF(2) matrix
 //      powers for the xor-likes, x <- x^(2^(11 k len) mod lambda(M)) for BBS)
 //      and (s, x) = (0, 0) for k >= 1;
-//   2. one batched launch runs segments 0 .. K-2 for len iterations into a
-//      digest sink (only their end states are needed);
+//   2. one batched launch runs the segments from there: written sink, all of
+//      them into their output columns; consumer sinks, segments 0 .. K-2
+//      into a digest sink (only their end states are needed);
 //   3. k_split_carry: one warp per warp group scans the segments in order:
 //      the true start of segment k is its predecessor's particular end plus
 //      (Q s_a, x_a ^ S s_a) with Q = P^len, S = P + ... + P^len; the own words
 //      of segment k take the end of segment k-1;
-//   4. one batched launch runs every segment from its true start into the
-//      caller's sink (segment 0 is the caller's state itself);
+//   4. written sink: k_split_fixup XORs each segment's homogeneous part into
+//      its outputs (the mixing step with zero own words: two shuffles per
+//      output); consumer sinks: one batched launch runs every segment from
+//      its true start into the sink (segment 0 is the caller's state);
 //   5. the last segment's end state becomes the caller's state, and the
 //      per-segment quarter-circle counts or digests are combined.
 #include <cuda_runtime.h>
@@ -255,8 +258,13 @@ __device__ __forceinline__ uint32_t mat_vec(uint32_t m_row, uint32_t v) {
 }
 
 // One warp per warp group g of the caller's state.
+// With `starts` (written sink), the true starts go to starts[k * P + l] as
+// (slot, x) and the segment states keep their particular ends; without it,
+// they are written into segment k's state together with the own words of
+// segment k-1's end, ready to run again.
 template <class Src>
-__global__ void __launch_bounds__(128) k_split_carry(SegSpace seg, uint32_t K, uint64_t len, uint64_t groups) {
+__global__ void __launch_bounds__(128) k_split_carry(SegSpace seg, uint32_t K, uint64_t len, uint64_t groups,
+                                                     uint2 *starts) {
     const uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (g >= groups) return;  // whole warps leave together (blockDim is a multiple of 32)
     const int lane = threadIdx.x & 31;
@@ -303,13 +311,100 @@ __global__ void __launch_bounds__(128) k_split_carry(SegSpace seg, uint32_t K, u
         const uint32_t nx = prev.x ^ cx ^ mat_vec(S, cs);
         cs = ns;
         cx = nx;
-        const DevState d = seg.at(k);
-        d.u32[F_SLOT * P + l] = cs;
-        d.u32[F_X * P + l] = cx;
-        for (int w = 0; w < kOwnWords; ++w) d.u32[(F_A + w) * P + l] = prev.own[w];
-        if (bbs) d.u64[G_Y * P + l] = prev.y;
+        if (starts) {
+            starts[(uint64_t)k * P + l] = make_uint2(cs, cx);
+        } else {
+            const DevState d = seg.at(k);
+            d.u32[F_SLOT * P + l] = cs;
+            d.u32[F_X * P + l] = cx;
+            for (int w = 0; w < kOwnWords; ++w) d.u32[(F_A + w) * P + l] = prev.own[w];
+            if (bbs) d.u64[G_Y * P + l] = prev.y;
+        }
         prev = cur;
         cur = nxt;
+    }
+}
+
+// Written sink: segments k >= 1 wrote their particular outputs (zero start).
+// From the true start (s_a, x_a), the homogeneous part is h <- P h,
+// acc <- acc ^ h per iteration (two shuffles, as in the mixing step with a
+// zero own word); output i of the segment gets acc XORed in.  Work unit =
+// (segment k >= 1, warp group g); the warp stages 32 iterations of its 32
+// rows in the swizzled tile and updates the outputs as 16-byte row segments
+// (V4) or words.  The last segment also corrects its end state.
+template <class Src, bool V4>
+__global__ void __launch_bounds__(256) k_split_fixup(SegSpace seg, const uint2 *starts, uint32_t K, uint64_t len,
+                                                     uint64_t len_last, uint64_t groups, uint32_t *out, uint64_t ld,
+                                                     uint64_t col0) {
+    __shared__ uint4 tiles[8][256];
+    const int lane = threadIdx.x & 31;
+    uint4 *tile = tiles[threadIdx.x >> 5];
+    uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
+    const DevState s0 = seg.at(0);
+    const uint64_t P = s0.P, S = s0.S;
+    const uint64_t units = (uint64_t)(K - 1) * groups;
+    for (uint64_t u = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < units; u += (uint64_t)gridDim.x * 8) {
+        const uint64_t k = 1 + u / groups, g = u % groups, l = g * 32 + lane, row0 = g * 32;
+        Src src;
+        src.load(s0, l);
+        int a1, a2;
+        src.arrays(s0, l, a1, a2);
+        const int p1 = s0.table[a1 * 32 + lane], p2 = s0.table[a2 * 32 + lane];
+        const uint2 st = starts[k * P + l];
+        uint32_t h = st.x, acc = st.y;
+        auto step = [&]() {
+            h = __shfl_sync(kFull, h, p1) ^ __shfl_sync(kFull, h, p2);
+            acc ^= h;
+            return acc;
+        };
+        const uint64_t n = k + 1 == K ? len_last : len;
+        uint32_t *base = out + col0 + k * len;
+        const uint64_t nfull = n - n % 32;
+        for (uint64_t i0 = 0; i0 < nfull; i0 += 32) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint4 f;
+                f.x = step();
+                f.y = step();
+                f.z = step();
+                f.w = step();
+                tile[lane * 8 + (q ^ (lane & 7))] = f;
+            }
+            __syncwarp();
+            if (V4) {
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int r = 4 * kk + lane / 8, c = lane % 8;
+                    if (row0 + r < S) {
+                        uint4 *p = reinterpret_cast<uint4 *>(base + (row0 + r) * ld + i0 + 4 * c);
+                        const uint4 v = tile[r * 8 + (c ^ (r & 7))];
+                        uint4 o = *p;
+                        o.x ^= v.x;
+                        o.y ^= v.y;
+                        o.z ^= v.z;
+                        o.w ^= v.w;
+                        store16<0>(reinterpret_cast<uint32_t *>(p), o);
+                    }
+                }
+            } else {
+                for (int r = 0; r < 32; ++r)
+                    if (row0 + r < S) base[(row0 + r) * ld + i0 + lane] ^= tw[tile_word<32>(r, lane)];
+            }
+            __syncwarp();
+        }
+        const int rem = (int)(n - nfull);
+        if (rem) {
+            for (int kk = 0; kk < rem; ++kk) tw[tile_word<32>(lane, kk)] = step();
+            __syncwarp();
+            for (int r = 0; r < 32; ++r)
+                if (lane < rem && row0 + r < S) base[(row0 + r) * ld + nfull + lane] ^= tw[tile_word<32>(r, lane)];
+            __syncwarp();
+        }
+        if (k + 1 == K) {
+            const DevState d = seg.at(K - 1);
+            d.u32[F_SLOT * P + l] ^= h;
+            d.u32[F_X * P + l] ^= acc;
+        }
     }
 }
 
@@ -356,7 +451,8 @@ __global__ void __launch_bounds__(256) k_split_combine(const uint64_t *r, uint64
 
 // ------------------------------------------------ host side
 constexpr uint32_t kMaxSegments = 8192;
-constexpr uint64_t kMinSegment = 256;  // iterations per segment (auto choice)
+constexpr uint64_t kMinSegment = 256;       // iterations per segment (auto choice)
+constexpr uint64_t kMinAutoSegment = 1024;  // ... when ci_generate_bbs splits on its own
 
 std::mutex g_split_mu;  // the shared batch below
 ci_batch g_split_batch[64] = {};
@@ -404,6 +500,17 @@ uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested) {
     return (n + len - 1) / len;
 }
 
+uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n) {
+    const uint64_t groups = h.P / 32;
+    const uint64_t target = (uint64_t)sm_count() * 128;  // about two waves of resident BBS warps
+    if (h.variant != CI_VAR_BBS || groups * 2 > target) return 1;
+    uint64_t K = std::min<uint64_t>(target / groups, std::max<uint64_t>(1, n / kMinAutoSegment));
+    K = std::min<uint64_t>(K, kMaxSegments);
+    if (K <= 1) return 1;
+    const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;
+    return (n + len - 1) / len;
+}
+
 ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
                        uint64_t *aux, uint64_t K, cudaStream_t stream) {
     const ci_states_s *h = &hs;
@@ -446,28 +553,56 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     k_split_setup<<<split_block_count(K * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl);
     if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split setup");
 
-    if (st == CI_OK) {  // pass 1: particular solutions of segments 0 .. K-2
+    // Written BBS outputs are fixed up in place (generation is the cost);
+    // xor-like outputs are cheaper to generate again than to read back.
+    const bool written = sink == CI_SINK_WRITTEN;
+    const bool fixup = written && h->variant == CI_VAR_BBS;
+    uint2 *starts = fixup ? reinterpret_cast<uint2 *>(res1) : nullptr;  // K * P (slot, x) pairs
+    if (st == CI_OK) {  // pass 1: particular solutions (fix-up: all segments, into their columns)
         tasks.reserve(K);
-        for (uint64_t k = 0; k + 1 < K; ++k)
-            tasks.push_back(make_task(segs[k], len, CI_SINK_DIGEST, nullptr, res1 + k * h->P, len, 0));
+        for (uint64_t k = 0; k < K; ++k) {
+            if (fixup)
+                tasks.push_back(make_task(segs[k], k + 1 == K ? len_last : len, sink, out, nullptr, ld, col0 + k * len));
+            else if (k + 1 < K)
+                tasks.push_back(make_task(segs[k], len, CI_SINK_DIGEST, nullptr, res1 + k * h->P, len, 0));
+        }
         st = batch_launch_tasks(batch, tasks.data(), (uint32_t)tasks.size(), stream, false);
     }
     if (st == CI_OK) {
         const unsigned blocks = (unsigned)((groups * 32 + 127) / 128);
         if (h->variant == CI_VAR_BBS)
-            k_split_carry<SrcBbs><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups);
+            k_split_carry<SrcBbs><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups, starts);
         else
-            k_split_carry<SrcXor128><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups);
+            k_split_carry<SrcXor128><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups, starts);
         if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split carry");
+    }
+    if (st == CI_OK && fixup) {  // homogeneous parts into segments 1 .. K-1, then the final state
+        const bool v4 = (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && ld % 4 == 0 && col0 % 4 == 0;
+        const int blocks = split_block_count((K - 1) * groups * 32);
+        if (h->variant == CI_VAR_BBS)
+            v4 ? k_split_fixup<SrcBbs, true><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
+                                                                          groups, out, ld, col0)
+               : k_split_fixup<SrcBbs, false><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
+                                                                           groups, out, ld, col0);
+        else
+            v4 ? k_split_fixup<SrcXor128, true><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
+                                                                             groups, out, ld, col0)
+               : k_split_fixup<SrcXor128, false><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
+                                                                              groups, out, ld, col0);
+        if ((e = cudaGetLastError()) == cudaSuccess)
+            k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view());
+        if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split fix-up");
+        cudaFreeAsync(ws, stream);
+        return st;
     }
     if (st == CI_OK && sink == CI_SINK_QC && (e = cudaMemsetAsync(res3, 0, res_bytes, stream)) != cudaSuccess)
         st = cuda_fail(e, "clearing counts");
-    if (st == CI_OK) {  // pass 2: every segment from its true start
+    if (st == CI_OK) {  // pass 2: every segment from its true start into the sink
         tasks.clear();
         for (uint64_t k = 0; k < K; ++k) {
             const ci_states_s &sh = k == 0 ? *h : segs[k];
             const uint64_t nk = k + 1 == K ? len_last : len;
-            if (sink == CI_SINK_WRITTEN)
+            if (written)
                 tasks.push_back(make_task(sh, nk, sink, out, nullptr, ld, col0 + k * len));
             else
                 tasks.push_back(make_task(sh, nk, sink, nullptr, res3 + k * h->P, nk, 0));
@@ -476,9 +611,9 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     }
     if (st == CI_OK) {
         k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view());
-        if (sink != CI_SINK_WRITTEN)
-            k_split_combine<<<(unsigned)((h->S + 255) / 256), 256, 0, stream>>>(
-                res3, aux, h->P, h->S, (uint32_t)K, len, len_last, sink == CI_SINK_DIGEST);
+        if (!written)
+            k_split_combine<<<(unsigned)((h->S + 255) / 256), 256, 0, stream>>>(res3, aux, h->P, h->S, (uint32_t)K,
+                                                                                len, len_last, sink == CI_SINK_DIGEST);
         if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split finish");
     }
     cudaFreeAsync(ws, stream);
