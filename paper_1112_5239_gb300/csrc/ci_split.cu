@@ -19,10 +19,11 @@
 //   2. one batched launch runs the segments from there: written sink, all of
 //      them into their output columns; consumer sinks, segments 0 .. K-2
 //      into a digest sink (only their end states are needed);
-//   3. k_split_carry: one warp per warp group scans the segments in order:
-//      the true start of segment k is its predecessor's particular end plus
-//      (Q s_a, x_a ^ S s_a) with Q = P^len, S = P + ... + P^len; the own words
-//      of segment k take the end of segment k-1;
+//   3. k_split_carry: one block per warp group scans the segments: the true
+//      start of segment k is its predecessor's particular end plus
+//      (Q s_a, x_a ^ S s_a) with Q = P^len, S = P + ... + P^len (a chunked
+//      parallel scan over up to 16 warps); the own words of segment k are
+//      those k_split_setup jumped to;
 //   4. written sink: k_split_fixup XORs each segment's homogeneous part into
 //      its outputs (the mixing step with zero own words: two shuffles per
 //      output); consumer sinks: one batched launch runs every segment from
@@ -191,11 +192,18 @@ struct SegSpace {
 
 constexpr int kOwnWords = 4;  // F_A .. F_D
 
+// Own words of every segment's start (k >= 1), saved by k_split_setup for the
+// regenerate form: field f of segment k, lane l at u32[(f * K + k) * P + l].
+struct OwnSave {
+    uint32_t *u32;  // kOwnWords fields (nullptr: not saved)
+    uint64_t *u64;  // the BBS state (CI_VAR_BBS)
+};
+
 // Thread (k, l): segment k's lane l.  Copies the caller's lane (and the
 // partner table), jumps the own generator by k * len iterations and, for
 // k >= 1, clears slot and x.
 __global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg, uint32_t K, uint64_t len,
-                                                     int variant, int xl) {
+                                                     int variant, int xl, OwnSave own) {
     const uint64_t total = (uint64_t)K * src.P;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
@@ -230,6 +238,10 @@ __global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg,
             jump_words<1>(v, dist, g_jump_xs32);
             d.u32[F_A * src.P + l] = v[0];
         }
+        if (own.u32) {
+            for (int f = 0; f < kOwnWords; ++f) own.u32[((uint64_t)f * K + k) * src.P + l] = d.u32[(F_A + f) * src.P + l];
+            if (own.u64) own.u64[k * src.P + l] = d.u64[G_Y * src.P + l];
+        }
     }
 }
 
@@ -257,17 +269,25 @@ __device__ __forceinline__ uint32_t mat_vec(uint32_t m_row, uint32_t v) {
     return r;
 }
 
-// One warp per warp group g of the caller's state.
-// With `starts` (written sink), the true starts go to starts[k * P + l] as
-// (slot, x) and the segment states keep their particular ends; without it,
-// they are written into segment k's state together with the own words of
-// segment k-1's end, ready to run again.
+// The carry scan over the segments of one warp group, with one block of NW
+// (up to 16) warps per group.  c_j, the true (slot, x) at the start of segment j, obeys
+// c_j = e_{j-1} ^ H(c_{j-1}), c_0 = 0 (segment 0 ran from the true state),
+// with e_{j-1} the particular end of segment j-1 and H(s, x) = (Q s, x ^ S s).
+// Warp w owns steps j in [j0, j1) (m = ceil((K-1) / NW) each):
+//   1. local scan from zero: d_j = e_{j-1} ^ H(d_{j-1}), d_{j0-1} = 0, kept in
+//      starts[j]; its end goes to shared memory;
+//   2. carry-in c_{j0-1}: fold the earlier warps' local ends through H^m,
+//      whose pair (Q_m, T_m) follows from (Q, S) by the binary method on m
+//      (H^(a+b) = (Q_a Q_b, T_b ^ T_a Q_b));
+//   3. c_j = d_j ^ H^(j - j0 + 1)(c_{j0-1}).
+// Fix-up form (`own` == nullptr): c_j goes to starts[j].  Regenerate form:
+// c_j and the saved own words of segment j's start go into its state.
 template <class Src>
-__global__ void __launch_bounds__(128) k_split_carry(SegSpace seg, uint32_t K, uint64_t len, uint64_t groups,
-                                                     uint2 *starts) {
-    const uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    if (g >= groups) return;  // whole warps leave together (blockDim is a multiple of 32)
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(512) k_split_carry(SegSpace seg, uint32_t K, uint64_t len, uint2 *starts,
+                                                      OwnSave own) {
+    __shared__ uint32_t end_s[16][32], end_x[16][32];
+    const uint64_t g = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, NW = blockDim.x >> 5;
     const DevState s0 = seg.at(0);
     const uint64_t P = s0.P, l = g * 32 + lane;
     Src src;
@@ -286,42 +306,63 @@ __global__ void __launch_bounds__(128) k_split_carry(SegSpace seg, uint32_t K, u
             S ^= Q;
         }
     }
-    const bool bbs = s0.u64 != nullptr;
-    // Segment k's end values are loaded one step ahead (iteration k writes
-    // only segment k's fields), so the scan's serial chain is the two
-    // 32-shuffle products, not a global-memory round trip per segment.
-    struct End {
-        uint32_t s, x, own[kOwnWords];
-        uint64_t y;
-    };
-    auto load_end = [&](uint32_t k) {
-        const DevState d = seg.at(k);
-        End e;
-        e.s = d.u32[F_SLOT * P + l];
-        e.x = d.u32[F_X * P + l];
-        for (int w = 0; w < kOwnWords; ++w) e.own[w] = d.u32[(F_A + w) * P + l];
-        e.y = bbs ? d.u64[G_Y * P + l] : 0;
-        return e;
-    };
-    uint32_t cs = 0, cx = 0;  // true (slot, x) at the start of the current segment
-    End prev = load_end(0), cur = load_end(1);
-    for (uint32_t k = 1; k < K; ++k) {
-        const End nxt = k + 1 < K ? load_end(k + 1) : cur;
-        const uint32_t ns = prev.s ^ mat_vec(Q, cs);
-        const uint32_t nx = prev.x ^ cx ^ mat_vec(S, cs);
-        cs = ns;
-        cx = nx;
-        if (starts) {
-            starts[(uint64_t)k * P + l] = make_uint2(cs, cx);
-        } else {
-            const DevState d = seg.at(k);
-            d.u32[F_SLOT * P + l] = cs;
-            d.u32[F_X * P + l] = cx;
-            for (int w = 0; w < kOwnWords; ++w) d.u32[(F_A + w) * P + l] = prev.own[w];
-            if (bbs) d.u64[G_Y * P + l] = prev.y;
+    const uint32_t m = (K - 1 + NW - 1) / NW;
+    const uint32_t j0 = 1 + w * m, j1 = min(K, j0 + m);
+    // 1. local scan; segment ends loaded one step ahead
+    uint32_t ds = 0, dx = 0;
+    if (j0 < j1) {
+        DevState d = seg.at(j0 - 1);
+        uint32_t es = d.u32[F_SLOT * P + l], ex = d.u32[F_X * P + l];
+        for (uint32_t j = j0; j < j1; ++j) {
+            uint32_t ns_e = 0, nx_e = 0;
+            if (j + 1 < j1) {
+                d = seg.at(j);
+                ns_e = d.u32[F_SLOT * P + l];
+                nx_e = d.u32[F_X * P + l];
+            }
+            const uint32_t ns = es ^ mat_vec(Q, ds);
+            dx = ex ^ dx ^ mat_vec(S, ds);
+            ds = ns;
+            starts[(uint64_t)j * P + l] = make_uint2(ds, dx);
+            es = ns_e;
+            ex = nx_e;
         }
-        prev = cur;
-        cur = nxt;
+    }
+    end_s[w][lane] = ds;
+    end_x[w][lane] = dx;
+    __syncthreads();
+    // 2. H^m and this warp's carry-in
+    uint32_t Qm = 1u << lane, Tm = 0;
+    for (int b = 31; b >= 0; --b) {
+        Tm ^= mat_mul(Tm, Qm);
+        Qm = mat_mul(Qm, Qm);
+        if ((m >> b) & 1u) {
+            Qm = mat_mul(Qm, Q);
+            Tm = S ^ mat_mul(Tm, Q);
+        }
+    }
+    uint32_t cs = 0, cx = 0;
+    for (int v = 0; v < w; ++v) {
+        const uint32_t ns = end_s[v][lane] ^ mat_vec(Qm, cs);
+        cx = end_x[v][lane] ^ cx ^ mat_vec(Tm, cs);
+        cs = ns;
+    }
+    // 3. true starts of this warp's segments
+    for (uint32_t j = j0; j < j1; ++j) {
+        const uint32_t ns = mat_vec(Q, cs);
+        cx ^= mat_vec(S, cs);
+        cs = ns;
+        const uint2 dj = starts[(uint64_t)j * P + l];
+        const uint32_t ts = dj.x ^ cs, tx = dj.y ^ cx;
+        if (!own.u32) {
+            starts[(uint64_t)j * P + l] = make_uint2(ts, tx);
+        } else {
+            const DevState d = seg.at(j);
+            d.u32[F_SLOT * P + l] = ts;
+            d.u32[F_X * P + l] = tx;
+            for (int f = 0; f < kOwnWords; ++f) d.u32[(F_A + f) * P + l] = own.u32[((uint64_t)f * K + j) * P + l];
+            if (own.u64) d.u64[G_Y * P + l] = own.u64[(uint64_t)j * P + l];
+        }
     }
 }
 
@@ -531,12 +572,24 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     const uint64_t len_last = n - (K - 1) * len;
 
     const uint64_t stride = (h->bytes + 255) / 256 * 256;
+    // Written BBS outputs are fixed up in place (generation is the cost);
+    // xor-like outputs are cheaper to generate again than to read back.
+    const bool written = sink == CI_SINK_WRITTEN;
+    const bool fixup = written && h->variant == CI_VAR_BBS;
     const uint64_t res_bytes = 8ull * K * h->P;  // per-segment consumer results
+    const uint64_t own_bytes = fixup ? 0 : (4ull * kOwnWords + 8ull) * K * h->P;
     uint8_t *ws = nullptr;
-    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&ws), stride * K + 2 * res_bytes, stream)) != cudaSuccess)
+    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&ws), stride * K + 2 * res_bytes + own_bytes, stream)) !=
+        cudaSuccess)
         return cuda_fail(e, "workspace");
     uint64_t *res1 = reinterpret_cast<uint64_t *>(ws + stride * K);
     uint64_t *res3 = res1 + K * h->P;
+    OwnSave own{nullptr, nullptr};
+    if (!fixup) {
+        own.u32 = reinterpret_cast<uint32_t *>(res3 + K * h->P);
+        own.u64 = h->variant == CI_VAR_BBS ? reinterpret_cast<uint64_t *>(own.u32 + (uint64_t)kOwnWords * K * h->P)
+                                           : nullptr;
+    }
 
     // Handles over the segment states (host copies of the caller's, moved).
     std::vector<ci_states_s> segs(K, *h);
@@ -550,14 +603,11 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     const DevState src = h->view();
 
     ci_status st = CI_OK;
-    k_split_setup<<<split_block_count(K * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl);
+    k_split_setup<<<split_block_count(K * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl,
+                                                                   own);
     if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split setup");
 
-    // Written BBS outputs are fixed up in place (generation is the cost);
-    // xor-like outputs are cheaper to generate again than to read back.
-    const bool written = sink == CI_SINK_WRITTEN;
-    const bool fixup = written && h->variant == CI_VAR_BBS;
-    uint2 *starts = fixup ? reinterpret_cast<uint2 *>(res1) : nullptr;  // K * P (slot, x) pairs
+    uint2 *starts = reinterpret_cast<uint2 *>(res1);  // K * P (slot, x) pairs, after pass 1
     if (st == CI_OK) {  // pass 1: particular solutions (fix-up: all segments, into their columns)
         tasks.reserve(K);
         for (uint64_t k = 0; k < K; ++k) {
@@ -569,11 +619,11 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
         st = batch_launch_tasks(batch, tasks.data(), (uint32_t)tasks.size(), stream, false);
     }
     if (st == CI_OK) {
-        const unsigned blocks = (unsigned)((groups * 32 + 127) / 128);
+        const unsigned threads = 32u * (unsigned)std::min<uint64_t>(16, K - 1);
         if (h->variant == CI_VAR_BBS)
-            k_split_carry<SrcBbs><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups, starts);
+            k_split_carry<SrcBbs><<<(unsigned)groups, threads, 0, stream>>>(sp, (uint32_t)K, len, starts, own);
         else
-            k_split_carry<SrcXor128><<<blocks, 128, 0, stream>>>(sp, (uint32_t)K, len, groups, starts);
+            k_split_carry<SrcXor128><<<(unsigned)groups, threads, 0, stream>>>(sp, (uint32_t)K, len, starts, own);
         if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split carry");
     }
     if (st == CI_OK && fixup) {  // homogeneous parts into segments 1 .. K-1, then the final state
