@@ -674,17 +674,19 @@ def bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
 
 def bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):
     """A long narrow request: one warp of BBS streams (32) over 2^20
-    iterations, as one sequential call (one serial chain per lane) and as a
+    iterations, as one sequential chain per lane (a single task of the batched
+    kernel; ci_generate_bbs itself would split this call) and as a
     time-parallel split call (jump-ahead, 4096 segments); outputs compared."""
     S, n = 32, 1 << 20
     seq = ci.States(S, variant="bbs", comb_size=32, seed=SEED_BBS, first_stream=rank * S)
     spl = ci.States(S, variant="bbs", comb_size=32, seed=SEED_BBS, first_stream=rank * S)
     out_seq = torch.empty((S, n), dtype=torch.int32, device=dev)
     out_spl = torch.empty_like(out_seq)
+    one = ci.Batch(1)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier_sync()
     a.record(stream)
-    seq.generate(n, out=out_seq)
+    one.run([(seq, n, "written", out_seq)], stream=stream)
     b.record(stream)
     barrier_sync()
     ms_seq = max_over_ranks(a.elapsed_time(b))

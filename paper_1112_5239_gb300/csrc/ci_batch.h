@@ -73,8 +73,12 @@ uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested);
 // Segment count ci_generate_bbs uses on its own: > 1 only for CI_VAR_BBS states
 // that fill less than about two waves of resident warps.
 uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n);
+// `own_batch` (max_items >= kSplitMaxSegments, used by one caller at a time)
+// replaces the shared batch and its lock, so that split calls on different
+// streams do not wait for each other.
+constexpr uint32_t kSplitMaxSegments = 8192;
 ci_status split_launch(const ci_states_s &h, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
-                       uint64_t *aux, uint64_t K, cudaStream_t stream);
+                       uint64_t *aux, uint64_t K, cudaStream_t stream, ci_batch own_batch = nullptr);
 cudaError_t split_prepare(cudaStream_t stream);
 
 // Sorts tasks longest-first, assigns prefixes, writes header + tasks to

@@ -79,14 +79,17 @@ __device__ __forceinline__ bool bg_setup_decrypt(uint64_t p, uint64_t q, uint64_
                     p * q < (1ull << 62) && is_prime_u32(p) && is_prime_u32(q);
     uint64_t x0 = 0, N = 3;
     if (ok) {
-        const Barrett32 Bp(p), Bq(q), Bp1(p - 1), Bq1(q - 1);
+        const Barrett32 Bp1(p - 1), Bq1(q - 1);      // even moduli: Barrett
+        const Mont32 Mp(p), Mq(q);                    // odd primes: Montgomery
         const uint64_t ep = Bp1.pow((p + 1) / 4, L);  // ((p+1)/4)^L mod (p-1)
         const uint64_t eq = Bq1.pow((q + 1) / 4, L);
-        const uint64_t rp = Bp.pow(Bp.reduce(y), ep);
-        const uint64_t rq = Bq.pow(Bq.reduce(y), eq);
-        const uint64_t pinv = Bq.pow(p, q - 2);      // Fermat: p^(q-2) = p^-1 mod q
-        const uint64_t t = Bq.mul(Bq.reduce(rq + q - Bq.reduce(rp)), pinv);
-        x0 = rp + p * t;                             // < p + p (q - 1) = N
+        const uint64_t rp = Mp.pow(y, ep);
+        const uint64_t rq_m = Mq.pow_m(Mq.to(y), eq);  // Montgomery forms mod q from here
+        const uint64_t pinv_m = Mq.pow_m(Mq.to(p), q - 2);  // Fermat: p^(q-2) = p^-1 mod q
+        const uint64_t rp_m = Mq.to(rp);
+        const uint64_t diff_m = rq_m >= rp_m ? rq_m - rp_m : rq_m + q - rp_m;
+        const uint64_t t = Mq.from(Mq.mul(diff_m, pinv_m));  // (r_q - r_p) p^-1 mod q
+        x0 = rp + p * t;                              // < p + p (q - 1) = N
         N = p * q;
     }
     s.B.set(N, barrett_mu(N));

@@ -122,8 +122,10 @@ struct Req {
     BatchTask tmpl;     // this request's queue entry; each wave sets col0 and n
 };
 
-// Requests of at most this many warp groups may run as split jobs.
+// Requests of at most this many warp groups may run as split jobs, at most
+// kSplitSlots of them at a time.
 constexpr uint64_t kSplitMaxGroups = 16;
+constexpr int kSplitSlots = 4;
 
 // A request run whole as one time-parallel split job (captured under the lock).
 struct SplitJob {
@@ -181,11 +183,14 @@ struct ci_server_s {
     std::thread worker;
     cudaStream_t stream = nullptr;       // waves
     cudaStream_t init_stream = nullptr;  // seeding of admitted stream sets, runs beside the waves
-    cudaStream_t split_stream = nullptr; // split jobs, one at a time, beside the waves
+    // split jobs: up to kSplitSlots at once beside the waves, each slot with
+    // its own stream and batch (worker thread only, apart from creation)
+    cudaStream_t split_stream[kSplitSlots] = {};
+    ci_batch split_batch[kSplitSlots] = {};
+    bool split_busy[kSplitSlots] = {};
+    Wave split_wave[kSplitSlots];
     cudaEvent_t init_last = nullptr;     // the latest seeding pass (split jobs wait for it)
-    std::deque<SplitJob> split_queue;    // worker thread only
-    bool split_busy = false;             // worker thread only
-    Wave split_wave;                     // worker thread only: the split job in flight
+    std::deque<SplitJob> split_queue;
     ci_batch batch = nullptr;
     std::deque<Wave> inflight;       // worker thread only
     std::vector<cudaEvent_t> spare;  // worker thread only
@@ -388,57 +393,70 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vec
     }
 }
 
-// Split jobs run on their own stream, one at a time, so that waves keep
-// running beside them.  A job waits for the latest seeding pass (which covers
-// the seeding of its own streams; a continuation's streams were last advanced
-// by a request that had finished before it was admitted).  Worker thread, no
-// lock held.
-void start_split_job(ci_server_s *s) {
-    if (s->split_busy || s->split_queue.empty()) return;
-    const SplitJob j = s->split_queue.front();
-    s->split_queue.pop_front();
-    while (s->spare.size() < 2) {
-        cudaEvent_t ev;
-        cudaEventCreate(&ev);
-        s->spare.push_back(ev);
-    }
-    Wave w;
-    w.start = s->spare.back();
-    s->spare.pop_back();
-    w.ev = s->spare.back();
-    s->spare.pop_back();
-    w.members.push_back(j.ticket);
-    w.finishing.push_back(j.ticket);
-    ci_status rc = cudaStreamWaitEvent(s->split_stream, s->init_last, 0) == cudaSuccess ? CI_OK : CI_E_CUDA;
-    if (rc == CI_OK && cudaEventRecord(w.start, s->split_stream) != cudaSuccess) rc = CI_E_CUDA;
-    if (rc == CI_OK) rc = split_launch(*j.h, j.L, CI_SINK_WRITTEN, j.out, j.L, 0, nullptr, j.K, s->split_stream);
-    if (rc == CI_OK && cudaEventRecord(w.ev, s->split_stream) != cudaSuccess) rc = CI_E_CUDA;
-    if (rc != CI_OK) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        finish_request(s, j.ticket, rc);
-        s->spare.push_back(w.ev);
-        s->spare.push_back(w.start);
-        s->cv_done.notify_all();
-        return;
-    }
-    s->split_wave = std::move(w);
-    s->split_busy = true;
+// Split jobs run on their own streams, up to kSplitSlots at a time, so that
+// waves keep running beside them.  A job waits for the latest seeding pass
+// (which covers the seeding of its own streams; a continuation's streams were
+// last advanced by a request that had finished before it was admitted).
+// Worker thread, no lock held.
+bool split_idle(const ci_server_s *s) {
+    for (int i = 0; i < kSplitSlots; ++i)
+        if (s->split_busy[i]) return false;
+    return s->split_queue.empty();
 }
 
-void poll_split_job(ci_server_s *s) {
-    if (!s->split_busy || cudaEventQuery(s->split_wave.ev) != cudaSuccess) return;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, s->split_wave.start, s->split_wave.ev);
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->st.gpu_ns += (uint64_t)(ms * 1e6);
-        for (uint64_t t : s->split_wave.finishing) finish_request(s, t, CI_OK);
+void start_split_jobs(ci_server_s *s) {
+    for (int slot = 0; slot < kSplitSlots && !s->split_queue.empty(); ++slot) {
+        if (s->split_busy[slot]) continue;
+        const SplitJob j = s->split_queue.front();
+        s->split_queue.pop_front();
+        while (s->spare.size() < 2) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            s->spare.push_back(ev);
+        }
+        Wave w;
+        w.start = s->spare.back();
+        s->spare.pop_back();
+        w.ev = s->spare.back();
+        s->spare.pop_back();
+        w.members.push_back(j.ticket);
+        w.finishing.push_back(j.ticket);
+        cudaStream_t st = s->split_stream[slot];
+        ci_status rc = cudaStreamWaitEvent(st, s->init_last, 0) == cudaSuccess ? CI_OK : CI_E_CUDA;
+        if (rc == CI_OK && cudaEventRecord(w.start, st) != cudaSuccess) rc = CI_E_CUDA;
+        if (rc == CI_OK)
+            rc = split_launch(*j.h, j.L, CI_SINK_WRITTEN, j.out, j.L, 0, nullptr, j.K, st, s->split_batch[slot]);
+        if (rc == CI_OK && cudaEventRecord(w.ev, st) != cudaSuccess) rc = CI_E_CUDA;
+        if (rc != CI_OK) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            finish_request(s, j.ticket, rc);
+            s->spare.push_back(w.ev);
+            s->spare.push_back(w.start);
+            s->cv_done.notify_all();
+            continue;
+        }
+        s->split_wave[slot] = std::move(w);
+        s->split_busy[slot] = true;
     }
-    s->cv_done.notify_all();
-    s->spare.push_back(s->split_wave.ev);
-    s->spare.push_back(s->split_wave.start);
-    s->split_wave = Wave();
-    s->split_busy = false;
+}
+
+void poll_split_jobs(ci_server_s *s) {
+    for (int slot = 0; slot < kSplitSlots; ++slot) {
+        if (!s->split_busy[slot] || cudaEventQuery(s->split_wave[slot].ev) != cudaSuccess) continue;
+        Wave &w = s->split_wave[slot];
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, w.start, w.ev);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->st.gpu_ns += (uint64_t)(ms * 1e6);
+            for (uint64_t t : w.finishing) finish_request(s, t, CI_OK);
+        }
+        s->cv_done.notify_all();
+        s->spare.push_back(w.ev);
+        s->spare.push_back(w.start);
+        w = Wave();
+        s->split_busy[slot] = false;
+    }
 }
 
 void worker_main(ci_server_s *s) {
@@ -447,8 +465,8 @@ void worker_main(ci_server_s *s) {
     std::vector<SplitJob> splits;
     for (;;) {
         while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().ev) == cudaSuccess) retire_front(s);
-        poll_split_job(s);
-        start_split_job(s);
+        poll_split_jobs(s);
+        start_split_jobs(s);
         tasks.clear();
         Wave w;
         {
@@ -463,7 +481,7 @@ void worker_main(ci_server_s *s) {
                     any = true;
                 }
                 if (any) s->cv_done.notify_all();
-                if (s->active.empty() && s->inflight.empty() && !s->split_busy && s->split_queue.empty()) break;
+                if (s->active.empty() && s->inflight.empty() && split_idle(s)) break;
             }
             const uint64_t ta = now_ns();
             admit(s);
@@ -472,7 +490,7 @@ void worker_main(ci_server_s *s) {
             if (s->inflight.size() < s->cfg.max_inflight) build_wave(s, tasks, w, splits);
             s->st.host_launch_ns += now_ns() - tb;
             if (tasks.empty() && splits.empty()) {
-                if (s->inflight.empty() && !s->split_busy)
+                if (s->inflight.empty() && split_idle(s))
                     s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
                 else
                     s->cv_work.wait_for(lk, std::chrono::microseconds(20));
@@ -481,7 +499,7 @@ void worker_main(ci_server_s *s) {
         }
         for (const SplitJob &j : splits) s->split_queue.push_back(j);
         splits.clear();
-        start_split_job(s);
+        start_split_jobs(s);
         if (tasks.empty()) continue;
         while (s->spare.size() < 2) {
             cudaEvent_t ev;
@@ -640,26 +658,26 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     s->st.arena_bytes = s->arena.size();
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->init_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->split_stream, cudaStreamNonBlocking);
+    const bool splits = c.split_min_slices != UINT64_MAX;
+    for (int i = 0; i < kSplitSlots && splits && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&s->split_stream[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess && ci_batch_create(kSplitMaxSegments, &s->split_batch[i]) != CI_OK)
+            e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->init_last, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(s->init_last, s->init_stream);
-    if (e == cudaSuccess && c.split_min_slices != UINT64_MAX) e = split_prepare(s->split_stream);
-    if (e != cudaSuccess) {
+    if (e == cudaSuccess && splits) e = split_prepare(s->split_stream[0]);
+    ci_status rc = e == cudaSuccess ? ci_batch_create(c.max_slots, &s->batch) : CI_E_CUDA;
+    if (e != cudaSuccess || rc != CI_OK) {
         if (s->stream) cudaStreamDestroy(s->stream);
         if (s->init_stream) cudaStreamDestroy(s->init_stream);
-        if (s->split_stream) cudaStreamDestroy(s->split_stream);
+        for (int i = 0; i < kSplitSlots; ++i) {
+            if (s->split_batch[i]) ci_batch_destroy(s->split_batch[i]);
+            if (s->split_stream[i]) cudaStreamDestroy(s->split_stream[i]);
+        }
         if (s->init_last) cudaEventDestroy(s->init_last);
         delete s;
-        return cuda_fail(e, "server streams");
-    }
-    ci_status rc = ci_batch_create(c.max_slots, &s->batch);
-    if (rc != CI_OK) {
-        cudaStreamDestroy(s->stream);
-        cudaStreamDestroy(s->init_stream);
-        cudaStreamDestroy(s->split_stream);
-        cudaEventDestroy(s->init_last);
-        delete s;
-        return rc;
+        return e != cudaSuccess ? cuda_fail(e, "server streams") : rc;
     }
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaHostAlloc(reinterpret_cast<void **>(&s->init_host[i]), sizeof(InitTask) * c.max_slots,
@@ -677,7 +695,10 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
         ci_batch_destroy(s->batch);
         cudaStreamDestroy(s->stream);
         cudaStreamDestroy(s->init_stream);
-        cudaStreamDestroy(s->split_stream);
+        for (int i = 0; i < kSplitSlots; ++i) {
+            if (s->split_batch[i]) ci_batch_destroy(s->split_batch[i]);
+            if (s->split_stream[i]) cudaStreamDestroy(s->split_stream[i]);
+        }
         cudaEventDestroy(s->init_last);
         delete s;
         return e == cudaErrorMemoryAllocation ? fail(CI_E_NOMEM, "server buffers") : cuda_fail(e, "server buffers");
@@ -838,7 +859,8 @@ ci_status ci_server_destroy(ci_server s) {
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->init_stream);
     cudaStreamSynchronize(s->stream);
-    cudaStreamSynchronize(s->split_stream);
+    for (int i = 0; i < kSplitSlots; ++i)
+        if (s->split_stream[i]) cudaStreamSynchronize(s->split_stream[i]);
     for (auto &kv : s->states)
         if (!kv.second.released && kv.second.h) ci_free_states(kv.second.h);
     for (cudaEvent_t ev : s->spare) cudaEventDestroy(ev);
@@ -850,7 +872,10 @@ ci_status ci_server_destroy(ci_server s) {
     ci_batch_destroy(s->batch);
     cudaStreamDestroy(s->init_stream);
     cudaStreamDestroy(s->stream);
-    cudaStreamDestroy(s->split_stream);
+    for (int i = 0; i < kSplitSlots; ++i) {
+        if (s->split_batch[i]) ci_batch_destroy(s->split_batch[i]);
+        if (s->split_stream[i]) cudaStreamDestroy(s->split_stream[i]);
+    }
     cudaEventDestroy(s->init_last);
     s->magic = 0;
     delete s;

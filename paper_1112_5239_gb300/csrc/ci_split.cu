@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(256) k_split_combine(const uint64_t *r, uint64
 }
 
 // ------------------------------------------------ host side
-constexpr uint32_t kMaxSegments = 8192;
+constexpr uint32_t kMaxSegments = kSplitMaxSegments;
 constexpr uint64_t kMinSegment = 256;       // iterations per segment (auto choice)
 constexpr uint64_t kMinAutoSegment = 1024;  // ... when ci_generate_bbs splits on its own
 
@@ -553,13 +553,14 @@ uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n) {
 }
 
 ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
-                       uint64_t *aux, uint64_t K, cudaStream_t stream) {
+                       uint64_t *aux, uint64_t K, cudaStream_t stream, ci_batch own_batch) {
     const ci_states_s *h = &hs;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    std::lock_guard<std::mutex> lk(g_split_mu);
-    ci_batch batch = split_batch(dev);
+    std::unique_lock<std::mutex> lk(g_split_mu, std::defer_lock);
+    if (!own_batch) lk.lock();  // the shared batch of this device
+    ci_batch batch = own_batch ? own_batch : split_batch(dev);
     if (!batch) return fail(CI_E_NOMEM, "could not create the split batch");
     std::vector<BatchTask> tasks;
     if (K <= 1) {  // one segment: a single task of the batched kernel
