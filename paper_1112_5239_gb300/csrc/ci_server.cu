@@ -184,9 +184,8 @@ struct ci_server_s {
     cudaStream_t stream = nullptr;       // waves
     cudaStream_t init_stream = nullptr;  // seeding of admitted stream sets, runs beside the waves
     // split jobs: up to kSplitSlots at once beside the waves, each slot with
-    // its own stream and batch (worker thread only, apart from creation)
+    // its own stream (worker thread only, apart from creation)
     cudaStream_t split_stream[kSplitSlots] = {};
-    ci_batch split_batch[kSplitSlots] = {};
     bool split_busy[kSplitSlots] = {};
     Wave split_wave[kSplitSlots];
     cudaEvent_t init_last = nullptr;     // the latest seeding pass (split jobs wait for it)
@@ -394,7 +393,7 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vec
 }
 
 // Split jobs run on their own streams, up to kSplitSlots at a time, so that
-// waves keep running beside them.  A job waits for the latest seeding pass
+// waves keep running beside them (split calls share no queue or lock).  A job waits for the latest seeding pass
 // (which covers the seeding of its own streams; a continuation's streams were
 // last advanced by a request that had finished before it was admitted).
 // Worker thread, no lock held.
@@ -425,7 +424,7 @@ void start_split_jobs(ci_server_s *s) {
         ci_status rc = cudaStreamWaitEvent(st, s->init_last, 0) == cudaSuccess ? CI_OK : CI_E_CUDA;
         if (rc == CI_OK && cudaEventRecord(w.start, st) != cudaSuccess) rc = CI_E_CUDA;
         if (rc == CI_OK)
-            rc = split_launch(*j.h, j.L, CI_SINK_WRITTEN, j.out, j.L, 0, nullptr, j.K, st, s->split_batch[slot]);
+            rc = split_launch(*j.h, j.L, CI_SINK_WRITTEN, j.out, j.L, 0, nullptr, j.K, st);
         if (rc == CI_OK && cudaEventRecord(w.ev, st) != cudaSuccess) rc = CI_E_CUDA;
         if (rc != CI_OK) {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -659,11 +658,8 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->init_stream, cudaStreamNonBlocking);
     const bool splits = c.split_min_slices != UINT64_MAX;
-    for (int i = 0; i < kSplitSlots && splits && e == cudaSuccess; ++i) {
+    for (int i = 0; i < kSplitSlots && splits && e == cudaSuccess; ++i)
         e = cudaStreamCreateWithFlags(&s->split_stream[i], cudaStreamNonBlocking);
-        if (e == cudaSuccess && ci_batch_create(kSplitMaxSegments, &s->split_batch[i]) != CI_OK)
-            e = cudaErrorMemoryAllocation;
-    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->init_last, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(s->init_last, s->init_stream);
     if (e == cudaSuccess && splits) e = split_prepare(s->split_stream[0]);
@@ -671,10 +667,8 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     if (e != cudaSuccess || rc != CI_OK) {
         if (s->stream) cudaStreamDestroy(s->stream);
         if (s->init_stream) cudaStreamDestroy(s->init_stream);
-        for (int i = 0; i < kSplitSlots; ++i) {
-            if (s->split_batch[i]) ci_batch_destroy(s->split_batch[i]);
+        for (int i = 0; i < kSplitSlots; ++i)
             if (s->split_stream[i]) cudaStreamDestroy(s->split_stream[i]);
-        }
         if (s->init_last) cudaEventDestroy(s->init_last);
         delete s;
         return e != cudaSuccess ? cuda_fail(e, "server streams") : rc;
@@ -695,10 +689,8 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
         ci_batch_destroy(s->batch);
         cudaStreamDestroy(s->stream);
         cudaStreamDestroy(s->init_stream);
-        for (int i = 0; i < kSplitSlots; ++i) {
-            if (s->split_batch[i]) ci_batch_destroy(s->split_batch[i]);
+        for (int i = 0; i < kSplitSlots; ++i)
             if (s->split_stream[i]) cudaStreamDestroy(s->split_stream[i]);
-        }
         cudaEventDestroy(s->init_last);
         delete s;
         return e == cudaErrorMemoryAllocation ? fail(CI_E_NOMEM, "server buffers") : cuda_fail(e, "server buffers");
@@ -872,10 +864,8 @@ ci_status ci_server_destroy(ci_server s) {
     ci_batch_destroy(s->batch);
     cudaStreamDestroy(s->init_stream);
     cudaStreamDestroy(s->stream);
-    for (int i = 0; i < kSplitSlots; ++i) {
-        if (s->split_batch[i]) ci_batch_destroy(s->split_batch[i]);
+    for (int i = 0; i < kSplitSlots; ++i)
         if (s->split_stream[i]) cudaStreamDestroy(s->split_stream[i]);
-    }
     cudaEventDestroy(s->init_last);
     s->magic = 0;
     delete s;

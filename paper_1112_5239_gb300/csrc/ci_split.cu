@@ -495,17 +495,85 @@ constexpr uint32_t kMaxSegments = kSplitMaxSegments;
 constexpr uint64_t kMinSegment = 256;       // iterations per segment (auto choice)
 constexpr uint64_t kMinAutoSegment = 1024;  // ... when ci_generate_bbs splits on its own
 
-std::mutex g_split_mu;  // the shared batch below
-ci_batch g_split_batch[64] = {};
-
-ci_batch split_batch(int dev) {
-    if (dev < 0 || dev >= 64) return nullptr;
-    if (!g_split_batch[dev]) {
-        ci_batch b = nullptr;
-        if (ci_batch_create(kMaxSegments, &b) != CI_OK) return nullptr;
-        g_split_batch[dev] = b;
+// One pass over segments [k_begin, k_end): work unit u is segment
+// k_begin + u / groups, warp group u % groups, run for its length (len, the
+// last segment len_last) by the generator's warp loop into SINK: written
+// outputs at column col0 + k len of rows of stride ld; consumer results into
+// aux + k P.  Segment 0 is the caller's own state when `caller0` is set.
+// Instantiated per source and sink, with at most 64 registers (4 blocks of 8
+// warps per SM): the all-source batched kernel needs 128, which held the
+// BBS segments to 16 resident warps per SM.
+template <class Src, int SINK>
+__global__ void __launch_bounds__(256, 4) k_split_run(SegSpace seg, DevState caller, int caller0, uint32_t k_begin,
+                                                   uint32_t k_end, uint32_t K, uint64_t len, uint64_t len_last,
+                                                   uint64_t groups, uint32_t *out, uint64_t ld, uint64_t col0,
+                                                   uint64_t *aux) {
+    __shared__ uint4 tiles[8][256];
+    uint4 *tile = tiles[threadIdx.x >> 5];
+    const uint64_t units = (uint64_t)(k_end - k_begin) * groups;
+    for (uint64_t u = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < units; u += (uint64_t)gridDim.x * 8) {
+        const uint64_t k = k_begin + u / groups, g = u % groups;
+        const DevState st = (k == 0 && caller0) ? caller : seg.at(k);
+        const uint64_t n = k + 1 == K ? len_last : len;
+        if (SINK == SINK_V4 || SINK == SINK_SCALAR)
+            warp_task<Src, SINK>(st, g, n, out, ld, col0 + k * len, nullptr, tile);
+        else
+            warp_task<Src, SINK>(st, g, n, nullptr, 0, 0, aux + k * caller.P, tile);
     }
-    return g_split_batch[dev];
+}
+
+template <class Src, int SINK>
+cudaError_t launch_split_run(const SegSpace &sp, const DevState &caller, bool caller0, uint32_t kb, uint32_t ke,
+                             uint32_t K, uint64_t len, uint64_t len_last, uint32_t *out, uint64_t ld, uint64_t col0,
+                             uint64_t *aux, cudaStream_t stream) {
+    static int per_sm = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_split_run<Src, SINK>, 256, 0);
+        if (per_sm <= 0) per_sm = 1;
+    });
+    const uint64_t groups = caller.P / 32, units = (uint64_t)(ke - kb) * groups;
+    if (units == 0) return cudaSuccess;
+    const int blocks = (int)std::min<uint64_t>((units + 7) / 8, (uint64_t)sm_count() * per_sm);
+    k_split_run<Src, SINK><<<blocks, 256, 0, stream>>>(sp, caller, caller0 ? 1 : 0, kb, ke, K, len, len_last, groups,
+                                                       out, ld, col0, aux);
+    return cudaGetLastError();
+}
+
+template <int SINK>
+cudaError_t split_run_sink(int variant, int xl, const SegSpace &sp, const DevState &caller, bool caller0, uint32_t kb,
+                           uint32_t ke, uint32_t K, uint64_t len, uint64_t len_last, uint32_t *out, uint64_t ld,
+                           uint64_t col0, uint64_t *aux, cudaStream_t stream) {
+    if (variant == CI_VAR_BBS)
+        return launch_split_run<SrcBbs, SINK>(sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0, aux, stream);
+    if (xl == CI_XL_XORSHIFT32)
+        return launch_split_run<SrcXorshift32, SINK>(sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0, aux,
+                                                     stream);
+    if (xl == CI_XL_XOR64)
+        return launch_split_run<SrcXor64, SINK>(sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0, aux,
+                                                stream);
+    return launch_split_run<SrcXor128, SINK>(sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0, aux,
+                                             stream);
+}
+
+// Runs segments [kb, ke) into the caller's sink (CI_SINK_*); written outputs
+// take 16-byte stores when out, ld and col0 allow it.
+cudaError_t split_run(const ci_states_s &h, int sink, const SegSpace &sp, bool caller0, uint32_t kb, uint32_t ke,
+                      uint32_t K, uint64_t len, uint64_t len_last, uint32_t *out, uint64_t ld, uint64_t col0,
+                      uint64_t *aux, cudaStream_t stream) {
+    const DevState caller = h.view();
+    if (sink == CI_SINK_QC)
+        return split_run_sink<SINK_QC>(h.variant, h.xl, sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0,
+                                       aux, stream);
+    if (sink == CI_SINK_DIGEST)
+        return split_run_sink<SINK_DIGEST>(h.variant, h.xl, sp, caller, caller0, kb, ke, K, len, len_last, out, ld,
+                                           col0, aux, stream);
+    const bool v4 = (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && ld % 4 == 0 && col0 % 4 == 0 && len % 4 == 0;
+    if (v4)
+        return split_run_sink<SINK_V4>(h.variant, h.xl, sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0,
+                                       aux, stream);
+    return split_run_sink<SINK_SCALAR>(h.variant, h.xl, sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0,
+                                       aux, stream);
 }
 
 int split_block_count(uint64_t items) {
@@ -517,16 +585,7 @@ int split_block_count(uint64_t items) {
 
 namespace ci {
 
-cudaError_t split_prepare(cudaStream_t stream) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    {
-        std::lock_guard<std::mutex> lk(g_split_mu);
-        if (!split_batch(dev)) return cudaErrorMemoryAllocation;
-    }
-    return ensure_jump_tables(stream);
-}
+cudaError_t split_prepare(cudaStream_t stream) { return ensure_jump_tables(stream); }
 
 uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested) {
     const uint64_t groups = h.P / 32;
@@ -553,19 +612,13 @@ uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n) {
 }
 
 ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
-                       uint64_t *aux, uint64_t K, cudaStream_t stream, ci_batch own_batch) {
+                       uint64_t *aux, uint64_t K, cudaStream_t stream) {
     const ci_states_s *h = &hs;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    std::unique_lock<std::mutex> lk(g_split_mu, std::defer_lock);
-    if (!own_batch) lk.lock();  // the shared batch of this device
-    ci_batch batch = own_batch ? own_batch : split_batch(dev);
-    if (!batch) return fail(CI_E_NOMEM, "could not create the split batch");
-    std::vector<BatchTask> tasks;
-    if (K <= 1) {  // one segment: a single task of the batched kernel
-        tasks.push_back(make_task(*h, n, sink, out, aux, ld, col0));
-        return batch_launch_tasks(batch, tasks.data(), 1, stream, false);
+    cudaError_t e;
+    if (K <= 1) {  // one segment: the caller's state, straight into the sink
+        SegSpace none{};
+        e = split_run(*h, sink, none, true, 0, 1, 1, n, n, out, ld, col0, aux, stream);
+        return e == cudaSuccess ? CI_OK : cuda_fail(e, "split run");
     }
     if ((e = ensure_jump_tables(stream)) != cudaSuccess) return cuda_fail(e, "jump tables");
     const uint64_t groups = h->P / 32;
@@ -610,14 +663,11 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
 
     uint2 *starts = reinterpret_cast<uint2 *>(res1);  // K * P (slot, x) pairs, after pass 1
     if (st == CI_OK) {  // pass 1: particular solutions (fix-up: all segments, into their columns)
-        tasks.reserve(K);
-        for (uint64_t k = 0; k < K; ++k) {
-            if (fixup)
-                tasks.push_back(make_task(segs[k], k + 1 == K ? len_last : len, sink, out, nullptr, ld, col0 + k * len));
-            else if (k + 1 < K)
-                tasks.push_back(make_task(segs[k], len, CI_SINK_DIGEST, nullptr, res1 + k * h->P, len, 0));
-        }
-        st = batch_launch_tasks(batch, tasks.data(), (uint32_t)tasks.size(), stream, false);
+        e = fixup ? split_run(*h, sink, sp, false, 0, (uint32_t)K, (uint32_t)K, len, len_last, out, ld, col0, nullptr,
+                              stream)
+                  : split_run(*h, CI_SINK_DIGEST, sp, false, 0, (uint32_t)K - 1, (uint32_t)K, len, len_last, nullptr,
+                              0, 0, res1, stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "split pass 1");
     }
     if (st == CI_OK) {
         const unsigned threads = 32u * (unsigned)std::min<uint64_t>(16, K - 1);
@@ -649,16 +699,8 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     if (st == CI_OK && sink == CI_SINK_QC && (e = cudaMemsetAsync(res3, 0, res_bytes, stream)) != cudaSuccess)
         st = cuda_fail(e, "clearing counts");
     if (st == CI_OK) {  // pass 2: every segment from its true start into the sink
-        tasks.clear();
-        for (uint64_t k = 0; k < K; ++k) {
-            const ci_states_s &sh = k == 0 ? *h : segs[k];
-            const uint64_t nk = k + 1 == K ? len_last : len;
-            if (written)
-                tasks.push_back(make_task(sh, nk, sink, out, nullptr, ld, col0 + k * len));
-            else
-                tasks.push_back(make_task(sh, nk, sink, nullptr, res3 + k * h->P, nk, 0));
-        }
-        st = batch_launch_tasks(batch, tasks.data(), (uint32_t)tasks.size(), stream, false);
+        e = split_run(*h, sink, sp, true, 0, (uint32_t)K, (uint32_t)K, len, len_last, out, ld, col0, res3, stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "split pass 2");
     }
     if (st == CI_OK) {
         k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view());
