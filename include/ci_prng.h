@@ -489,7 +489,9 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * mod M), the segments run from a zero mixing state, a per-warp scan restores
  * their true starts from the linearity of Algorithm 4/5's mixing and Eq.
  * (Oplus) over the lanes, and the segments run again from those starts into
- * the sink.  Cost: about twice the generator work, spread over up to
+ * the sink (written BBS outputs are corrected in place instead: the
+ * homogeneous part is XORed in, two shuffles per output).  Cost: about twice
+ * the generator work (once for written BBS outputs), spread over up to
  * n_segments times more warps.
  * out_dev: uint32 outputs (CI_SINK_WRITTEN, out_capacity elements, layout as
  * ci_generate) or uint64[n_streams] (counts INCREMENTED for CI_SINK_QC,

@@ -177,3 +177,30 @@ def test_long_narrow_requests_run_as_split_jobs(env):
     assert np.array_equal(np.concatenate([outs[0][0], outs[0][3]], axis=1), ref)
     assert np.array_equal(outs[0][1], _oracle_rows("xor", 32, 40, 1 << 20))
     assert np.array_equal(outs[0][2], _oracle_rows("xor", 33, 100, 3000))
+
+
+def test_many_split_jobs_queue_over_the_slots(env):
+    """Ten long narrow requests (more than the concurrent split slots) of
+    both variants, among ordinary ones: every output equals the one of a
+    server that slices them into waves, and a sample equals the oracle."""
+    torch, ci = env
+    rng = np.random.default_rng(8)
+    specs = []
+    for i in range(10):
+        v = "bbs" if i % 2 else "xor"
+        specs.append(dict(n_per_stream=(1 << 14) if v == "bbs" else (1 << 19), n_streams=int(rng.integers(1, 100)),
+                          variant=v, seed=100 + i))
+        specs.append(dict(n_per_stream=int(rng.integers(1, 2000)), n_streams=int(rng.integers(1, 500)), seed=200 + i))
+    outs = {}
+    for split in (0, 2**64 - 1):
+        srv = ci.Server(2 << 30, split_min_slices=split)
+        ts = [srv.submit(**sp) for sp in specs]
+        outs[split] = [u32(srv.output(srv.wait(t))) for t in ts]
+        assert srv.stats()["split_jobs"] == (10 if split == 0 else 0)
+        srv.close()
+    for a, b in zip(outs[0], outs[2**64 - 1]):
+        assert np.array_equal(a, b)
+    for i in (0, 2):  # one xor and one BBS split job against the oracle (first 4096 outputs)
+        sp = specs[i]
+        ref = oracle_gen(sp["variant"], "xor128", 32, sp["seed"], 0, sp["n_streams"]).streams(4096)
+        assert np.array_equal(outs[0][i][:, :4096], ref)
