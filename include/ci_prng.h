@@ -51,7 +51,8 @@ enum {
     CI_E_CUDA = -3,     /* a CUDA runtime call failed                       */
     CI_E_BUSY = -4,     /* server queue full / admission refused            */
     CI_E_TIMEOUT = -5,  /* a bounded wait gave up                           */
-    CI_E_STATE = -6     /* handle of the wrong variant, or freed            */
+    CI_E_STATE = -6,    /* handle of the wrong variant, or freed            */
+    CI_E_CANCELED = -7  /* the request was cancelled (ci_cancel)            */
 };
 
 /* --------------------------------------------------------------- params */
@@ -348,6 +349,16 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
  * CI_E_INVAL (bad parameters, sizes, unknown or released continue_ticket),
  * CI_E_NOMEM (output plus state can never fit the arena), CI_E_STATE. */
 ci_status ci_submit(ci_server server, const ci_request *req, uint64_t *ticket);
+
+/* Cancels a request (thread-safe).  A queued request is dropped.  An
+ * admitted one gets no further slices and finishes with CI_E_CANCELED once its
+ * slices on the GPU have completed (a request running as one split job, or
+ * whose last slice is already queued, completes first; the split job then
+ * reports CI_E_CANCELED, the other CI_OK).  A request cancelled or failed
+ * after admission leaves its stream set part-way, so later continuations of
+ * it fail with CI_E_STATE (the set can still be released).  Cancelling a
+ * finished request returns its status.  Errors: CI_E_INVAL (unknown ticket). */
+ci_status ci_cancel(ci_server server, uint64_t ticket);
 
 /* Non-blocking: CI_PENDING while queued or running; CI_OK and *result once
  * done; the request's error status if it failed; CI_E_INVAL for an unknown

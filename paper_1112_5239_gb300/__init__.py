@@ -282,6 +282,11 @@ class Server:
     def release_states(self, ticket) -> None:
         _lib.call("ci_release_states", self.handle, int(ticket))
 
+    def cancel(self, ticket) -> int:
+        """Cancels a request; returns the status ci_cancel reports (0, or the
+        status of a request that had already finished)."""
+        return int(_lib.lib().ci_cancel(self.handle, int(ticket)))
+
     def stats(self) -> dict:
         st = _lib.ci_server_stats()
         _lib.call("ci_server_get_stats", self.handle, ctypes.byref(st))

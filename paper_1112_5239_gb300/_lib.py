@@ -12,14 +12,15 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libci_prng.so")
 
 CI_OK, CI_PENDING = 0, 1
-CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE = -1, -2, -3, -4, -5, -6
+CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE, CI_E_CANCELED = -1, -2, -3, -4, -5, -6, -7
 CI_VAR_XOR, CI_VAR_BBS, CI_VAR_BBS16 = 0, 1, 2
 CI_SINK_WRITTEN, CI_SINK_QC, CI_SINK_DIGEST = 0, 1, 2
 CI_NOALLOC_MAX_ITEMS = 1024
 CI_XL_XOR128, CI_XL_XORSHIFT32, CI_XL_XOR64 = 0, 1, 2
 
 STATUS_NAMES = {0: "CI_OK", 1: "CI_PENDING", -1: "CI_E_INVAL", -2: "CI_E_NOMEM", -3: "CI_E_CUDA",
-                -4: "CI_E_BUSY", -5: "CI_E_TIMEOUT", -6: "CI_E_STATE"}
+                -4: "CI_E_BUSY", -5: "CI_E_TIMEOUT", -6: "CI_E_STATE",
+                -7: "CI_E_CANCELED"}
 
 
 class ci_params(ctypes.Structure):
@@ -154,6 +155,7 @@ _SIGNATURES = {
     "ci_wait": [_VP, _U64, _U32, _VP],
     "ci_release": [_VP, _U64],
     "ci_release_states": [_VP, _U64],
+    "ci_cancel": [_VP, _U64],
     "ci_server_get_stats": [_VP, _VP],
     "ci_server_drive": [_VP, _VP, _VP, _VP, _VP, _U32, _VP, _VP],
     "ci_server_destroy": [_VP],

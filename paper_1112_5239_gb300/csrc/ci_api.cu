@@ -10,6 +10,7 @@
 
 #include "ci_batch.h"
 #include "ci_internal.h"
+#include "ci_trace.h"
 
 namespace ci {
 
@@ -287,6 +288,7 @@ static ci_status check_out(ci_states s, uint64_t n, const void *out, uint64_t ca
 }
 
 ci_status ci_generate(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void *stream) {
+    TraceRange trace("ci_generate");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (s->variant != CI_VAR_XOR) return fail(CI_E_STATE, "ci_generate needs an xor-variant state (use ci_generate_bbs)");
     if (n == 0) return CI_OK;
@@ -297,6 +299,7 @@ ci_status ci_generate(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void
 }
 
 ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void *stream) {
+    TraceRange trace("ci_generate_bbs");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (s->variant == CI_VAR_XOR) return fail(CI_E_STATE, "ci_generate_bbs needs a BBS-variant state (use ci_generate)");
     if (n == 0) return CI_OK;
@@ -311,6 +314,7 @@ ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, 
 }
 
 ci_status ci_generate_fused_qc(ci_states s, uint64_t n, uint64_t *counts, void *stream) {
+    TraceRange trace("ci_generate_fused_qc");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (n & 1ull) return fail(CI_E_INVAL, "n_per_stream must be even (outputs are consumed in pairs)");
     if (n == 0) return CI_OK;
@@ -320,6 +324,7 @@ ci_status ci_generate_fused_qc(ci_states s, uint64_t n, uint64_t *counts, void *
 }
 
 ci_status ci_generate_digest(ci_states s, uint64_t n, uint64_t *digest, void *stream) {
+    TraceRange trace("ci_generate_digest");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (n == 0) return CI_OK;
     if (!digest) return fail(CI_E_INVAL, "digest_dev is NULL");

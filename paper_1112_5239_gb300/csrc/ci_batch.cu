@@ -14,6 +14,7 @@
 
 #include "ci_batch.h"
 #include "ci_device.cuh"
+#include "ci_trace.h"
 #include "ci_tune.h"
 
 namespace ci {
@@ -213,6 +214,7 @@ static cudaError_t build_graph(ci_batch_s *b, int i) {
 namespace ci {
 
 ci_status batch_launch_tasks(ci_batch_s *b, BatchTask *tasks, uint32_t n_tasks, cudaStream_t cs, bool sort) {
+    TraceRange trace("batch launch");
     if (n_tasks == 0) return CI_OK;
     if (n_tasks > b->max_items) return fail(CI_E_INVAL, "more tasks than the batch's max_items");
     const int s = b->slot;

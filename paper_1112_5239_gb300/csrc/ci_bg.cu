@@ -22,6 +22,7 @@
 
 #include "ci_device.cuh"
 #include "ci_internal.h"
+#include "ci_trace.h"
 #include "ci_modarith.cuh"
 
 namespace ci {
@@ -176,6 +177,7 @@ extern "C" {
 ci_status ci_bg_encrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *N_dev, const uint8_t *S0_dev,
                         const uint64_t *r_dev, const uint8_t *msg_dev, uint8_t *cipher_dev, uint64_t *y_dev,
                         uint32_t *n_rejected_dev, void *cuda_stream) {
+    ci::TraceRange trace("bg encrypt");
     using namespace ci;
     if (n_msgs == 0) return CI_OK;
     const ci_status st = bg_check(n_msgs, n_chunks, N_dev, r_dev, S0_dev, y_dev, msg_dev, cipher_dev);
@@ -189,6 +191,7 @@ ci_status ci_bg_encrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *N_de
 ci_status ci_bg_decrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *p_dev, const uint64_t *q_dev,
                         const uint8_t *S0_dev, const uint64_t *y_dev, const uint8_t *cipher_dev, uint8_t *msg_dev,
                         uint32_t *n_rejected_dev, void *cuda_stream) {
+    ci::TraceRange trace("bg decrypt");
     using namespace ci;
     if (n_msgs == 0 || n_chunks == 0) return CI_OK;
     const ci_status st = bg_check(n_msgs, n_chunks, p_dev, q_dev, S0_dev, y_dev, cipher_dev, msg_dev);

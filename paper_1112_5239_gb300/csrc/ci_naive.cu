@@ -17,6 +17,7 @@
 
 #include "ci_device.cuh"
 #include "ci_internal.h"
+#include "ci_trace.h"
 
 namespace ci {
 namespace {
@@ -215,6 +216,7 @@ ci_status ci_naive_init(uint64_t n_streams, uint64_t seed, uint64_t first_stream
 
 ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_stream, uint32_t *out_dev,
                             uint64_t out_capacity_u32, void *cuda_stream) {
+    ci::TraceRange trace("naive generate");
     using namespace ci;
     uint64_t need = 0;
     const ci_status st = ci_naive_state_bytes(n_streams, &need);

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -23,6 +24,7 @@
 #include <vector>
 
 #include "ci_batch.h"
+#include "ci_trace.h"
 
 namespace ci {
 
@@ -120,6 +122,9 @@ struct Req {
     uint64_t ticket;
     size_t active_idx;  // position in ci_server_s::active while admitted
     BatchTask tmpl;     // this request's queue entry; each wave sets col0 and n
+    uint32_t waves;     // waves in flight holding a slice of it
+    bool split;         // runs as one split job
+    bool cancel;        // ci_cancel was called while it was admitted
 };
 
 // Requests of at most this many warp groups may run as split jobs, at most
@@ -148,7 +153,39 @@ struct StatesRec {
     uint64_t off, bytes;
     bool busy;
     bool released;
+    bool poisoned;  // a request that advanced it failed or was cancelled part-way
 };
+
+// Host-side fault injection for tests (environment variable CI_FAULT, read
+// when a server is created): "queue_full@N" makes the N-th submission return
+// CI_E_BUSY, "reject_admit@N" fails the N-th admission with CI_E_NOMEM, and
+// "launch_fail@N" treats the N-th wave launch as failed (nothing launched),
+// several separated by commas.  Nothing reaches the GPU.
+struct Faults {
+    uint64_t queue_full = 0, reject_admit = 0, launch_fail = 0;
+    uint64_t n_submit = 0, n_admit = 0, n_launch = 0;
+};
+
+Faults parse_faults(const char *spec) {
+    Faults f;
+    if (!spec) return f;
+    std::string all(spec);
+    size_t pos = 0;
+    while (pos <= all.size()) {
+        const size_t end = std::min(all.find(',', pos), all.size());
+        const std::string item = all.substr(pos, end - pos);
+        const size_t at = item.find('@');
+        if (at != std::string::npos) {
+            const std::string kind = item.substr(0, at);
+            const uint64_t n = std::strtoull(item.c_str() + at + 1, nullptr, 10);
+            if (kind == "queue_full") f.queue_full = n;
+            if (kind == "reject_admit") f.reject_admit = n;
+            if (kind == "launch_fail") f.launch_fail = n;
+        }
+        pos = end + 1;
+    }
+    return f;
+}
 
 struct Wave {
     cudaEvent_t ev;
@@ -204,6 +241,7 @@ struct ci_server_s {
     uint64_t init_lanes = 0;
     std::vector<uint64_t> init_tickets;
     ci_server_stats st;
+    Faults faults;
 };
 
 static constexpr uint32_t kServerMagic = 0x5E2BE200u;
@@ -219,7 +257,10 @@ void finish_request(ci_server_s *s, uint64_t t, ci_status status) {  // under lo
     q.status = status;
     q.t_done = now_ns();
     auto sit = s->states.find(q.root);
-    if (held_states && sit != s->states.end()) sit->second.busy = false;
+    if (held_states && sit != s->states.end()) {
+        sit->second.busy = false;
+        if (status != CI_OK) sit->second.poisoned = true;  // advanced part-way: continuations fail
+    }
     if (status != CI_OK && q.out) {
         s->arena.release(q.out_off, q.out_bytes);
         q.out = nullptr;
@@ -250,7 +291,16 @@ void retire_front(ci_server_s *s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->st.gpu_ns += (uint64_t)(ms * 1e6);
-        for (uint64_t t : w.finishing) finish_request(s, t, CI_OK);
+        for (uint64_t t : w.members) {
+            Req &q = s->reqs[t];
+            if (q.waves) --q.waves;
+        }
+        for (uint64_t t : w.finishing)
+            if (s->reqs[t].state == RQ_ACTIVE) finish_request(s, t, CI_OK);
+        for (uint64_t t : w.members) {  // cancelled, and no slice of it left on the GPU
+            Req &q = s->reqs[t];
+            if (q.cancel && q.waves == 0 && q.state == RQ_ACTIVE) finish_request(s, t, CI_E_CANCELED);
+        }
     }
     s->cv_done.notify_all();
     s->spare.push_back(w.ev);
@@ -262,11 +312,16 @@ void retire_front(ci_server_s *s) {
 // its queue (no overtaking by smaller requests).
 bool admit_one(ci_server_s *s, uint64_t t) {  // under lock; false: no room now
     Req &q = s->reqs[t];
+    if (s->faults.reject_admit && ++s->faults.n_admit == s->faults.reject_admit) {
+        finish_request(s, t, fail(CI_E_NOMEM, "admission rejected (injected fault)"));
+        return true;
+    }
     const bool cont = q.r.continue_ticket != 0;
     StatesRec *sr = nullptr;
     if (cont) {
         auto sit = s->states.find(q.root);
-        if (sit == s->states.end() || sit->second.released) {  // its stream set failed or was released
+        if (sit == s->states.end() || sit->second.released || sit->second.poisoned) {
+            // its stream set failed, was cancelled part-way or was released
             finish_request(s, t, CI_E_STATE);
             return true;
         }
@@ -300,6 +355,7 @@ bool admit_one(ci_server_s *s, uint64_t t) {  // under lock; false: no room now
         r.bytes = need;
         r.busy = true;
         r.released = false;
+        r.poisoned = false;
         s->states[t] = r;
         q.h = h;
     } else {
@@ -362,7 +418,7 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vec
     // under lock
     for (Req *qp : s->active) {
         Req &q = *qp;
-        if (q.enq >= q.L) continue;
+        if (q.enq >= q.L || q.cancel) continue;
         // CI_VAR_BBS16 outputs depend on call boundaries (per-call arrays and
         // rotation): such a request runs as a single slice, i.e. one call
         const uint64_t slice = q.variant == CI_VAR_BBS16 ? q.L
@@ -376,6 +432,7 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vec
             if (K > 1) {
                 splits.push_back(SplitJob{q.ticket, q.h, q.out, q.L, K});
                 q.enq = q.L;
+                q.split = true;
                 s->st.split_jobs++;
                 continue;
             }
@@ -387,6 +444,7 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vec
         tk.n = n;
         s->st.units += tk.ngroups;
         q.enq += n;
+        ++q.waves;
         w.members.push_back(q.ticket);
         if (q.enq == q.L) w.finishing.push_back(q.ticket);
     }
@@ -408,6 +466,7 @@ void start_split_jobs(ci_server_s *s) {
         if (s->split_busy[slot]) continue;
         const SplitJob j = s->split_queue.front();
         s->split_queue.pop_front();
+        TraceRange trace("server split job");
         while (s->spare.size() < 2) {
             cudaEvent_t ev;
             cudaEventCreate(&ev);
@@ -448,7 +507,7 @@ void poll_split_jobs(ci_server_s *s) {
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->st.gpu_ns += (uint64_t)(ms * 1e6);
-            for (uint64_t t : w.finishing) finish_request(s, t, CI_OK);
+            for (uint64_t t : w.finishing) finish_request(s, t, s->reqs[t].cancel ? CI_E_CANCELED : CI_OK);
         }
         s->cv_done.notify_all();
         s->spare.push_back(w.ev);
@@ -483,7 +542,10 @@ void worker_main(ci_server_s *s) {
                 if (s->active.empty() && s->inflight.empty() && split_idle(s)) break;
             }
             const uint64_t ta = now_ns();
-            admit(s);
+            {
+                TraceRange trace("server admit");
+                admit(s);
+            }
             const uint64_t tb = now_ns();
             s->st.host_admit_ns += tb - ta;
             if (s->inflight.size() < s->cfg.max_inflight) build_wave(s, tasks, w, splits);
@@ -513,12 +575,25 @@ void worker_main(ci_server_s *s) {
         uint64_t wave_units = 0;
         for (const BatchTask &tk : tasks) wave_units += tk.ngroups;
         const uint64_t tl = now_ns();
-        ci_status rc = batch_launch_tasks(s->batch, tasks.data(), (uint32_t)tasks.size(), s->stream, false);
+        ci_status rc;
+        if (s->faults.launch_fail && ++s->faults.n_launch == s->faults.launch_fail) {
+            rc = fail(CI_E_CUDA, "wave launch failed (injected fault)");
+        } else {
+            TraceRange trace("server wave");
+            rc = batch_launch_tasks(s->batch, tasks.data(), (uint32_t)tasks.size(), s->stream, false);
+        }
         const uint64_t tl_end = now_ns();
         if (rc == CI_OK && cudaEventRecord(w.ev, s->stream) != cudaSuccess) rc = CI_E_CUDA;
         if (rc != CI_OK) {
+            // earlier waves may still write the members' outputs: let them
+            // finish before the outputs' arena bytes are released
+            cudaStreamSynchronize(s->stream);
             std::lock_guard<std::mutex> lk(s->mu);
-            for (uint64_t t : w.members) finish_request(s, t, rc);
+            for (uint64_t t : w.members) {
+                Req &q = s->reqs[t];
+                q.waves = 0;
+                if (q.state == RQ_ACTIVE) finish_request(s, t, rc);
+            }
             s->spare.push_back(w.ev);
             s->spare.push_back(w.start);
             s->cv_done.notify_all();
@@ -570,6 +645,8 @@ ci_status release_locked(ci_server_s *s, uint64_t ticket) {
 }
 
 ci_status submit_locked(ci_server_s *s, const ci_request *req, uint64_t *ticket) {
+    if (s->faults.queue_full && ++s->faults.n_submit == s->faults.queue_full)
+        return fail(CI_E_BUSY, "queue full (injected fault)");
     Req q;
     std::memset(&q, 0, sizeof q);
     q.r = *req;
@@ -582,6 +659,8 @@ ci_status submit_locked(ci_server_s *s, const ci_request *req, uint64_t *ticket)
         if (base.state == RQ_FAILED) return fail(CI_E_STATE, "continue_ticket failed");
         auto sit = s->states.find(base.root);
         if (sit != s->states.end() && sit->second.released) return fail(CI_E_INVAL, "its streams were released");
+        if (sit != s->states.end() && sit->second.poisoned)
+            return fail(CI_E_STATE, "its streams were left part-way by a failed or cancelled request");
         q.root = base.root;
         q.S = base.S;
         q.variant = base.variant;
@@ -653,6 +732,7 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     c.slice_bbs = std::max<uint64_t>(4, c.slice_bbs & ~3ull);
     if (c.split_min_slices == 0) c.split_min_slices = 32;
     s->cfg = c;
+    s->faults = parse_faults(std::getenv("CI_FAULT"));
     std::memset(&s->st, 0, sizeof s->st);
     s->st.arena_bytes = s->arena.size();
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
@@ -736,6 +816,42 @@ ci_status ci_release(ci_server s, uint64_t ticket) {
     if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
     std::lock_guard<std::mutex> lk(s->mu);
     return release_locked(s, ticket);
+}
+
+ci_status ci_cancel(ci_server s, uint64_t ticket) {
+    if (!valid_server(s)) return fail(CI_E_STATE, "not a live server");
+    ci_status rc = CI_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end() || it->second.state == RQ_RELEASED) return fail(CI_E_INVAL, "unknown ticket");
+        Req &q = it->second;
+        if (q.state == RQ_DONE || q.state == RQ_FAILED) return q.status;  // already finished
+        if (q.state == RQ_PENDING) {
+            Chain &ch = s->chains[q.root];
+            auto wit = std::find(ch.waiting.begin(), ch.waiting.end(), ticket);
+            if (wit != ch.waiting.end()) {  // behind another request of its stream set
+                ch.waiting.erase(wit);
+                q.state = RQ_FAILED;
+                q.status = CI_E_CANCELED;
+                q.t_done = now_ns();
+                if (s->feed_completed) s->completed.push_back(ticket);
+            } else {  // queued for admission: it holds its stream set's turn
+                for (std::deque<uint64_t> *dq : {&s->pending, &s->ready}) {
+                    auto qit = std::find(dq->begin(), dq->end(), ticket);
+                    if (qit != dq->end()) dq->erase(qit);
+                }
+                finish_request(s, ticket, CI_E_CANCELED);
+            }
+        } else {  // admitted
+            q.cancel = true;
+            if (!q.split && q.waves == 0) finish_request(s, ticket, CI_E_CANCELED);
+        }
+        rc = CI_OK;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();
+    return rc;
 }
 
 ci_status ci_release_states(ci_server s, uint64_t ticket) {

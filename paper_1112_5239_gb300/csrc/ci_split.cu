@@ -40,6 +40,7 @@
 
 #include "ci_batch.h"
 #include "ci_device.cuh"
+#include "ci_trace.h"
 
 namespace ci {
 namespace {
@@ -613,6 +614,7 @@ uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n) {
 
 ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
                        uint64_t *aux, uint64_t K, cudaStream_t stream) {
+    TraceRange trace("split");
     const ci_states_s *h = &hs;
     cudaError_t e;
     if (K <= 1) {  // one segment: the caller's state, straight into the sink

@@ -204,3 +204,60 @@ def test_many_split_jobs_queue_over_the_slots(env):
         sp = specs[i]
         ref = oracle_gen(sp["variant"], "xor128", 32, sp["seed"], 0, sp["n_streams"]).streams(4096)
         assert np.array_equal(outs[0][i][:, :4096], ref)
+
+
+def test_cancel_queued_and_admitted_requests(env):
+    """A queued request is dropped; an admitted long one finishes with
+    CI_E_CANCELED, its queued continuation then fails (its streams were left
+    part-way), and unrelated requests still equal the oracle."""
+    torch, ci = env
+    srv = ci.Server(1 << 30, max_slots=1, slice_xor=64, split_min_slices=2**64 - 1)
+    long_t = srv.submit(1 << 16, 64, seed=41)          # 1024 slices of 64 outputs
+    cont_t = srv.submit(128, continue_ticket=long_t)   # waits behind it
+    queued = srv.submit(500, 40, seed=42)              # waits for the only slot
+    ok_t = srv.submit(300, 33, seed=43)
+    assert srv.cancel(queued) == 0
+    with pytest.raises(ci.CIError) as e:
+        srv.wait(queued)
+    assert e.value.status == -7
+    assert srv.cancel(long_t) == 0
+    with pytest.raises(ci.CIError) as e:
+        srv.wait(long_t)
+    assert e.value.status == -7
+    with pytest.raises(ci.CIError) as e:
+        srv.wait(cont_t)
+    assert e.value.status == -6
+    res = srv.wait(ok_t)
+    assert np.array_equal(u32(srv.output(res)), _oracle_rows("xor", 43, 33, 300))
+    with pytest.raises(ci.CIError):  # a new continuation of the cancelled set is refused
+        srv.submit(10, continue_ticket=long_t)
+    assert srv.cancel(ok_t) == 0  # finished: its status
+    srv.close()
+
+
+def test_injected_host_faults(env, monkeypatch):
+    """CI_FAULT hooks fail the 2nd submission (CI_E_BUSY), the 3rd admission
+    (CI_E_NOMEM) and the 2nd wave launch (CI_E_CUDA) on the host; every
+    other request completes and equals the oracle."""
+    torch, ci = env
+    monkeypatch.setenv("CI_FAULT", "queue_full@2,reject_admit@3,launch_fail@2")
+    srv = ci.Server(1 << 28, max_slots=1, max_inflight=1, split_min_slices=2**64 - 1)
+    tickets, statuses = [], []
+    for i in range(6):
+        try:
+            tickets.append((i, srv.submit(200 + i, 40 + i, seed=60 + i)))
+        except ci.CIError as e:
+            statuses.append((i, e.status))
+    assert statuses == [(1, -4)]
+    results = {}
+    for i, t in tickets:
+        try:
+            results[i] = u32(srv.output(srv.wait(t)))
+        except ci.CIError as e:
+            results[i] = e.status
+    failed = {i: r for i, r in results.items() if isinstance(r, int)}
+    assert sorted(failed.values()) == [-3, -2]
+    for i, r in results.items():
+        if not isinstance(r, int):
+            assert np.array_equal(r, _oracle_rows("xor", 60 + i, 40 + i, 200 + i))
+    srv.close()
