@@ -409,7 +409,7 @@ ci_status ci_server_destroy(ci_server server);
  *     BBS1..BBS8 (each < its modulus), 17..24 their moduli (>= 2, < 2^16);
  *   then (CI_VAR_BBS only) 3 uint64 fields of P lanes: 0 y (canonical
  *     residue, BBS state), 1 M (odd, bit length n <= 62), 2 the Barrett
- *     reciprocal floor(2^(2n) / M) << (63 - n).
+ *     reciprocal floor(2^(2n+1) / M), shifted left by 61 - n when n <= 61.
  * Importing replaces the state of a handle with the same parameters and
  * n_streams; an imported BBS state must hold y < M and the reciprocal of M.
  * Errors: CI_E_INVAL (size mismatch), CI_E_CUDA. */

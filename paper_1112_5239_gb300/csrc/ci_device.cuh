@@ -113,16 +113,19 @@ struct SrcXor64 {
 };
 
 // ------------------------------------------------ Barrett arithmetic
-// x^2 mod M for odd M of bit length n, 2 <= n <= 62, and canonical x < M, by
+// a b mod M for M of bit length n, 2 <= n <= 62, and canonical a, b < M, by
 // Barrett reduction (Barrett 1986; base-2 form of Menezes et al., Handbook of
-// Applied Cryptography, Alg. 14.42): q1 = floor(x^2 / 2^(n-1)),
-// q3 = floor(q1 mu / 2^(n+1)) with mu = floor(2^(2n) / M), and
-// r = x^2 - q3 M lies in [0, 3M), so at most two subtractions give the
-// canonical residue.  As mu < 2^(n+1), q3 = mulhi(q1, mu << (63 - n)) exactly;
-// that shifted reciprocal is what the state stores.  The result is canonical
-// at every step, so the BBS low bits need no conversion (a Montgomery square
-// plus the reduction to canonical form measured 22 % slower at full
-// occupancy on sm_103a).
+// Applied Cryptography, Alg. 14.42) with one bit more precision on both sides
+// of the quotient estimate: X = a b, q1 = floor(X / 2^(n-2)),
+// mu = floor(2^(2n+1) / M), q = floor(q1 mu / 2^(n+3)).  Each floor then
+// costs less than 1/2 (X < 2^(2n), M >= 2^(n-1)), so q >= floor(X / M) - 1
+// and r = X - q M lies in [0, 2M): one subtraction gives the canonical
+// residue (the textbook estimate needs two).  q1 < 2^(n+2) and
+// mu < 2^(n+2) fit 64 bits; the state stores mu << (61 - n) for n <= 61 and
+// mu itself for n = 62, where one shift of the product's high half follows.
+// Canonical at every step, so the BBS low bits need no conversion (a
+// Montgomery square plus the reduction to canonical form measured 22 % slower
+// at full occupancy on sm_103a).
 __host__ __device__ __forceinline__ uint64_t mul_hi64(uint64_t a, uint64_t b) {
 #ifdef __CUDA_ARCH__
     return __umul64hi(a, b);
@@ -139,12 +142,12 @@ __host__ __device__ __forceinline__ uint32_t bit_length64(uint64_t M) {
 #endif
 }
 
-// floor(2^(2n) / M) << (63 - n) by restoring long division of 2^(2n)
-// (remainders stay below M < 2^62).
+// The stored reciprocal: floor(2^(2n+1) / M) by restoring long division of
+// 2^(2n+1) (remainders stay below M < 2^62), shifted as described above.
 __host__ __device__ __forceinline__ uint64_t barrett_mu(uint64_t M) {
     const uint32_t n = bit_length64(M);
     uint64_t r = 1, q = 0;
-    for (uint32_t i = 0; i < 2 * n; ++i) {
+    for (uint32_t i = 0; i < 2 * n + 1; ++i) {
         r <<= 1;
         q <<= 1;
         if (r >= M) {
@@ -152,34 +155,27 @@ __host__ __device__ __forceinline__ uint64_t barrett_mu(uint64_t M) {
             q |= 1;
         }
     }
-    return q << (63 - n);
+    return n <= 61 ? q << (61 - n) : q;
 }
 
 struct Barrett62 {
-    uint64_t M, mu;  // mu: barrett_mu(M)
-    uint32_t s1, s2;  // n - 1, 65 - n
-    __host__ __device__ __forceinline__ void set(uint64_t mod, uint64_t mu_shifted) {
+    uint64_t M, mu;      // mu: barrett_mu(M)
+    uint32_t s1, s2, t;  // n - 2; 66 - n (at most 63: below n = 4, X < 2^64 and the high half is 0); n == 62
+    __host__ __device__ __forceinline__ void set(uint64_t mod, uint64_t mu_stored) {
         M = mod;
-        mu = mu_shifted;
+        mu = mu_stored;
         const uint32_t n = bit_length64(mod);
-        s1 = n - 1;
-        s2 = 65 - n;
+        s1 = n - 2;
+        s2 = 66 - n < 63 ? 66 - n : 63;
+        t = n == 62 ? 1u : 0u;
     }
-    __host__ __device__ __forceinline__ uint64_t sqr(uint64_t x) const {
-        const uint64_t lo = x * x, hi = mul_hi64(x, x);
-        const uint64_t q3 = mul_hi64((hi << s2) | (lo >> s1), mu);
-        uint64_t r = lo - q3 * M;
-        r = r >= M ? r - M : r;
-        return r >= M ? r - M : r;
-    }
-    // a b mod M for a, b < M (the same reduction; any M of bit length 2..62).
     __host__ __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) const {
         const uint64_t lo = a * b, hi = mul_hi64(a, b);
-        const uint64_t q3 = mul_hi64((hi << s2) | (lo >> s1), mu);
-        uint64_t r = lo - q3 * M;
-        r = r >= M ? r - M : r;
+        const uint64_t q = mul_hi64((hi << s2) | (lo >> s1), mu) >> t;
+        const uint64_t r = lo - q * M;
         return r >= M ? r - M : r;
     }
+    __host__ __device__ __forceinline__ uint64_t sqr(uint64_t x) const { return mul(x, x); }
 };
 
 // Blum Blum Shub strategy source (Algorithm 5 generalised to w = 5 bits per

@@ -151,15 +151,17 @@ def test_bbs_small(env, C):
 
 
 def test_bbs_barrett_reciprocals(env):
-    """The stored reciprocal of each modulus is floor(2^(2n) / M) << (63 - n),
-    n = bit length of M, and the state stays canonical (y < M)."""
+    """The stored reciprocal of each modulus is floor(2^(2n+1) / M), shifted
+    left by 61 - n when n <= 61 (n = bit length of M), and the state stays
+    canonical (y < M)."""
     torch, ci = env
     st = _states(ci, "bbs", "xor128", 32, 3, 0, 256)
     st.generate(40)
     s = ci.unpack_state(st.export_state(), 256, 1)
     for M, mu, y in zip(s["M"].tolist(), s["mu"].tolist(), s["y"].tolist()):
         n = M.bit_length()
-        assert mu == (2 ** (2 * n) // M) << (63 - n)
+        q = 2 ** (2 * n + 1) // M
+        assert mu == (q << (61 - n) if n <= 61 else q)
         assert y < M
 
 

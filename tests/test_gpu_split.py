@@ -76,3 +76,21 @@ def test_unsplittable_and_bad_arguments():
     with pytest.raises(ci.CIError) as e:
         st.generate_split(100, out=small, segments=2)
     assert e.value.status == -1
+
+
+def test_segment_cap():
+    """At the cap of 8192 segments: one xor128 warp over 2^21 iterations (the
+    auto choice reaches the cap; written and digest forms) and one BBS warp
+    over 2^20 iterations in 8192 segments of 128 equal the oracle."""
+    torch, ci = cuda_or_skip()
+    n = 1 << 21
+    st = _states(ci, "xor", "xor128", 32, 71, 32)
+    out = u32(st.generate_split(n))
+    orc = oracle_gen("xor", "xor128", 32, 71, 78, 32)
+    assert np.array_equal(out, orc.streams(n))
+    d = st.generate_split(n, sink="digest").cpu().numpy().view(np.uint64)
+    assert np.array_equal(d, digest_rows(orc.streams(n)))
+    n = 1 << 20
+    bb = _states(ci, "bbs", "xor128", 32, 72, 32)
+    out = u32(bb.generate_split(n, segments=8192))
+    assert np.array_equal(out, oracle_gen("bbs", "xor128", 32, 72, 79, 32).streams(n))
