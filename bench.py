@@ -54,7 +54,7 @@ def parse_args():
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
-    ap.add_argument("--profile", choices=["written", "fused", "bbs", "batched", "bg", "naive"], default=None,
+    ap.add_argument("--profile", choices=["written", "fused", "bbs", "bbs16", "batched", "bg", "naive"], default=None,
                     help="small case for ncu: autotune, 2 warm-up launches, then 1 launch of one kernel inside "
                          "the NVTX range 'profile'; no timing")
     return ap.parse_args()
@@ -84,6 +84,10 @@ def run_profile_case(kind: str) -> None:
         run = lambda: st.generate_fused_qc(L_MAIN, counts=counts)  # noqa: E731
     elif kind == "bbs":
         st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
+        out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
+        run = lambda: st.generate(1024, out=out)  # noqa: E731
+    elif kind == "bbs16":  # Algorithm 5 as printed, 2^16 streams x 1024 written (256 MiB)
+        st = ci.States(S_BBS, variant="bbs16", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
         run = lambda: st.generate(1024, out=out)  # noqa: E731
     elif kind == "bg":  # chaotic Blum-Goldwasser encryption, 2^18 messages x 1024 chunks (256 MiB each way)
