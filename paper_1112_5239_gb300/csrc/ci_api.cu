@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ci_batch.h"
+#include "ci_split.h"
 #include "ci_internal.h"
 #include "ci_trace.h"
 

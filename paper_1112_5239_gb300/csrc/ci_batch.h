@@ -63,22 +63,6 @@ BatchTask make_task(const ci_states_s &h, uint64_t n, int sink_abi, uint32_t *ou
 ci_status batch_launch_tasks(ci_batch_s *b, BatchTask *tasks, uint32_t n_tasks, cudaStream_t stream,
                              bool sort = true);
 
-// Time-parallel generation (ci_split.cu).  split_segments: the segment count
-// used for n iterations of h (requested == 0: from the GPU size); 1 means
-// unsplit.  split_launch: n iterations of h as K segments into `sink`
-// (written: out[r * ld + col0 + i]; consumers: aux[r]), results equal to one
-// sequential call.  split_prepare: builds the jump tables for the current
-// device (blocks once on `stream`).
-uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested);
-// Segment count ci_generate_bbs uses on its own: > 1 only for CI_VAR_BBS states
-// that fill less than about two waves of resident warps.
-uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n);
-// Split calls on different streams are independent (no shared queue).
-constexpr uint32_t kSplitMaxSegments = 8192;
-ci_status split_launch(const ci_states_s &h, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
-                       uint64_t *aux, uint64_t K, cudaStream_t stream);
-cudaError_t split_prepare(cudaStream_t stream);
-
 // Sorts tasks longest-first, assigns prefixes, writes header + tasks to
 // `staging` (capacity checked by the caller) and returns the bytes to upload.
 uint64_t pack_queue(BatchTask *tasks, uint32_t n_tasks, void *staging, bool sort = true);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "ci_batch.h"
+#include "ci_split.h"
 #include "ci_trace.h"
 
 namespace ci {

@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "ci_batch.h"
+#include "ci_split.h"
 #include "ci_device.cuh"
 #include "ci_trace.h"
 

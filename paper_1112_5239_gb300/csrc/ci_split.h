@@ -1,0 +1,34 @@
+// ci_split.h -- time-parallel generation (ci_split.cu), shared by the C ABI
+// (ci_generate_split, ci_generate_bbs) and the serving loop's split jobs (not
+// part of the C ABI).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "ci_internal.h"
+
+namespace ci {
+
+constexpr uint32_t kSplitMaxSegments = 8192;
+
+// Segment count for n iterations of h (requested == 0: from the GPU size);
+// 1 means unsplit.
+uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested);
+
+// Segment count ci_generate_bbs uses on its own: > 1 only for CI_VAR_BBS
+// states that fill less than about two waves of resident warps.
+uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n);
+
+// n iterations of h as K segments into `sink` (written: out[r * ld + col0 + i];
+// consumers: aux[r]), with results equal to one sequential call.  Calls on
+// different streams are independent (no shared queue or lock).
+
+ci_status split_launch(const ci_states_s &h, uint64_t n, int sink, uint32_t *out, uint64_t ld, uint64_t col0,
+                       uint64_t *aux, uint64_t K, cudaStream_t stream);
+
+// Builds the jump tables for the current device (blocks once on `stream`).
+cudaError_t split_prepare(cudaStream_t stream);
+
+}  // namespace ci
