@@ -8,7 +8,6 @@
 #include <string>
 #include <vector>
 
-#include "ci_batch.h"
 #include "ci_split.h"
 #include "ci_internal.h"
 #include "ci_trace.h"

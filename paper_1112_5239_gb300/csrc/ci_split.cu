@@ -38,7 +38,6 @@
 #include <new>
 #include <vector>
 
-#include "ci_batch.h"
 #include "ci_split.h"
 #include "ci_device.cuh"
 #include "ci_trace.h"
