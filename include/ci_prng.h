@@ -302,7 +302,7 @@ typedef struct {
     uint64_t split_min_slices;  /* a new request of at most 16 warp groups (512
                                streams) and at least this many slices runs as
                                one time-parallel job (ci_generate_split) instead
-                               of slices in waves (0: 32; UINT64_MAX: never;
+                               of slices in waves (0: 16; UINT64_MAX: never;
                                never for CI_VAR_BBS16)                           */
 } ci_server_config;
 

@@ -731,7 +731,7 @@ ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_serve
     if (c.slice_bbs == 0) c.slice_bbs = 512;
     c.slice_xor = std::max<uint64_t>(4, c.slice_xor & ~3ull);  // keep 16-byte store alignment
     c.slice_bbs = std::max<uint64_t>(4, c.slice_bbs & ~3ull);
-    if (c.split_min_slices == 0) c.split_min_slices = 32;
+    if (c.split_min_slices == 0) c.split_min_slices = 16;  // swept over 4, 8, 16, 32: the lowest p99 at half load
     s->cfg = c;
     s->faults = parse_faults(std::getenv("CI_FAULT"));
     std::memset(&s->st, 0, sizeof s->st);
