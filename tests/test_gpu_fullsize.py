@@ -14,13 +14,28 @@ def env():
     return cuda_or_skip()
 
 
-def test_plain_2e20x4096_written_chunks_prefix(env):
+@pytest.mark.parametrize("shape", ["default", "tma16"])
+def test_plain_2e20x4096_written_chunks_prefix(env, shape):
     """2^20 streams x 4096 outputs, seed 2, written as 16 chunks of 256
     outputs per stream (1 GiB each): the 2^14-stream prefix of every chunk and
-    the last group's rows equal the oracle's."""
+    the last group's rows equal the oracle's.  Run with the default launch
+    shape and with the one the benchmark's autotuner picks (TMA bulk tensor
+    stores, 16 warps per block)."""
     torch, ci = env
     from paper_1112_5239_gb300.workloads import PLAIN_2E20x4096 as W
 
+    saved = ci.tune_table()
+    if shape == "tma16":
+        t = dict(saved)
+        t["xor128/written"] = {"warps_per_block": 16, "tile_depth": 32, "cache_policy": 2}
+        ci.set_tune_table(t)
+    try:
+        _written_chunks(torch, ci, W)
+    finally:
+        ci.set_tune_table(saved)
+
+
+def _written_chunks(torch, ci, W):
     S, chunk = W.n_streams, W.chunk
     st = ci.States(S, variant=W.variant, xl=W.xl, comb_size=W.comb_size, seed=W.seed, comb_seed=W.comb_seed)
     out = torch.empty((S, chunk), dtype=torch.int32, device="cuda")
