@@ -261,3 +261,64 @@ def test_injected_host_faults(env, monkeypatch):
         if not isinstance(r, int):
             assert np.array_equal(r, _oracle_rows("xor", 60 + i, 40 + i, 200 + i))
     srv.close()
+
+
+def test_concurrent_clients_submit_continue_cancel(env):
+    """Four client threads submit requests and continuations and cancel some
+    of them at the same time.  Cancelled requests end CI_E_CANCELED or, if they
+    finished first, CI_OK; every other request completes, and a sample of
+    roots and continuations equals the oracle."""
+    import threading
+
+    torch, ci = env
+    srv = ci.Server(2 << 30, slice_xor=256, slice_bbs=32)
+    records, errors = [], []
+    lock = threading.Lock()
+
+    def client(k):
+        rng = np.random.default_rng(100 + k)
+        try:
+            for i in range(40):
+                v = "bbs" if rng.random() < 0.2 else "xor"
+                S, L = int(rng.integers(1, 200)), int(rng.integers(1, 3000))
+                seed = 1000 * k + i
+                t = srv.submit(L, S, variant=v, seed=seed)
+                rec = {"t": t, "v": v, "S": S, "L": L, "seed": seed, "cancel": False, "cont": None}
+                if rng.random() < 0.3:
+                    L2 = int(rng.integers(1, 2000))
+                    rec["cont"] = (srv.submit(L2, continue_ticket=t), L2)
+                elif rng.random() < 0.15:
+                    srv.cancel(t)
+                    rec["cancel"] = True
+                with lock:
+                    records.append(rec)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    threads = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    checked = 0
+    for n, rec in enumerate(sorted(records, key=lambda r: r["t"])):
+        if rec["cancel"]:
+            try:
+                srv.wait(rec["t"])
+            except ci.CIError as e:
+                assert e.status == -7
+            continue
+        res = srv.wait(rec["t"])
+        out = u32(srv.output(res))
+        cont = None
+        if rec["cont"]:
+            cont = u32(srv.output(srv.wait(rec["cont"][0])))
+        if n % 6 == 0:
+            g = oracle_gen(rec["v"], "xor128", 32, rec["seed"], 0, rec["S"])
+            assert np.array_equal(out, g.streams(rec["L"]))
+            if cont is not None:
+                assert np.array_equal(cont, g.streams(rec["cont"][1]))
+            checked += 1
+    assert checked >= 20
+    srv.close()
