@@ -221,8 +221,8 @@ cudaError_t launch_init(const ci_states_s &h, uint64_t seed, uint64_t first, cud
     return cudaGetLastError();
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library).
+// cuTensorMapEncodeTiled through the runtime's entry-point lookup, so the
+// library does not link libcuda itself.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
