@@ -303,7 +303,7 @@ typedef struct {
                                streams) and at least this many slices runs as
                                one time-parallel job (ci_generate_split) instead
                                of slices in waves (0: 16; UINT64_MAX: never;
-                               never for CI_VAR_BBS16)                           */
+                               CI_VAR_BBS16 lengths count in BBS slices)          */
 } ci_server_config;
 
 typedef struct {
@@ -510,9 +510,13 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * picks the count from the GPU size; the count is capped at 8192 and
  * segments hold a multiple of 32 iterations, so small calls run unsplit.
  * Allocates a stream-ordered workspace of about n_segments state copies.
- * Errors: CI_E_STATE (invalid handle, or CI_VAR_BBS16, whose outputs depend
- * on call boundaries), CI_E_INVAL (unknown sink, NULL output, capacity, odd
- * length for CI_SINK_QC), CI_E_NOMEM, CI_E_CUDA. */
+ * CI_VAR_BBS16, whose outputs depend on call boundaries, is split within the
+ * one call: every segment uses the arrays the call chose at its start, each of
+ * the eight generators jumps by its own squaring count (x <- x^(2^(c k len)
+ * mod lambda(M)) mod M, lambda from the factors of the 16-bit modulus), and
+ * the generators rotate once, at the end.
+ * Errors: CI_E_STATE (invalid handle), CI_E_INVAL (unknown sink, NULL output,
+ * capacity, odd length for CI_SINK_QC), CI_E_NOMEM, CI_E_CUDA. */
 ci_status ci_generate_split(ci_states states, uint64_t n_per_stream, int32_t sink, void *out_dev,
                            uint64_t out_capacity, uint32_t n_segments, void *cuda_stream);
 

@@ -427,8 +427,9 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vec
                                                          : s->cfg.slice_xor;
         // long and narrow: the whole request as one split job on the split
         // stream (its serial chain would otherwise take L / slice waves)
-        if (q.enq == 0 && q.variant != CI_VAR_BBS16 && q.tmpl.ngroups <= kSplitMaxGroups &&
-            q.L / slice >= s->cfg.split_min_slices) {
+        // (CI_VAR_BBS16 runs as one call anyway: its length counts in BBS slices)
+        const uint64_t measure = q.variant == CI_VAR_BBS16 ? s->cfg.slice_bbs : slice;
+        if (q.enq == 0 && q.tmpl.ngroups <= kSplitMaxGroups && q.L / measure >= s->cfg.split_min_slices) {
             const uint64_t K = split_segments(*q.h, q.L, 0);
             if (K > 1) {
                 splits.push_back(SplitJob{q.ticket, q.h, q.out, q.L, K});

@@ -191,21 +191,79 @@ struct SegSpace {
     }
 };
 
-constexpr int kOwnWords = 4;  // F_A .. F_D
+constexpr int kOwnWords = 4;  // F_A .. F_D (CI_VAR_BBS16: the eight states F_Y16 ..)
 
 // Own words of every segment's start (k >= 1), saved by k_split_setup for the
 // regenerate form: field f of segment k, lane l at u32[(f * K + k) * P + l].
 struct OwnSave {
-    uint32_t *u32;  // kOwnWords fields (nullptr: not saved)
+    uint32_t *u32;  // `count` fields from `first` (nullptr: not saved)
     uint64_t *u64;  // the BBS state (CI_VAR_BBS)
+    int first, count;
 };
+
+// Algorithm 5 as printed, run as a segment of one call: the arrays are the
+// ones the call chose when it started (stored in the sel field by
+// k_split_setup, as sel1 | sel2 << 8), and the generators are not rotated at
+// the segment's end (the call rotates them once, when its last segment
+// becomes the caller's state).
+struct SrcBbs16Seg : SrcBbs16 {
+    __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
+        SrcBbs16::load(s, l);
+        const uint32_t sel = s.u32[F_SEL * s.P + l];
+        sel1 = sel & 7u;
+        sel2 = (sel >> 8) & 7u;
+    }
+    __device__ __forceinline__ void store(const DevState &s, uint64_t l) const {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s.u32[(F_Y16 + k) * s.P + l] = y[k];
+    }
+};
+
+// Squarings of generator k (BBS1 .. BBS8) per output of Algorithm 5 as printed:
+// one chunk each, then BBS3 and BBS1, BBS7 and BBS2 for the two shift steps.
+__constant__ uint32_t c_bbs16_squarings[8] = {2, 2, 2, 1, 1, 1, 2, 1};
+
+// lambda(M) = lcm(p - 1, q - 1) of each 16-bit modulus M = p q (p != q primes,
+// as seeded), by trial division; lam[k * P + l] for generator k of lane l.
+__global__ void __launch_bounds__(256) k_split_lambda16(DevState src, uint32_t *lam) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < src.P; l += stride)
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t M = src.u32[(F_M16 + k) * src.P + l];
+            uint32_t p = M;  // a prime M (not seeded) gets lambda = M - 1
+            for (uint32_t d = 3; d * d <= M; d += 2)
+                if (M % d == 0) {
+                    p = d;
+                    break;
+                }
+            const uint32_t q = p == M ? 2u : M / p;
+            uint32_t a = p - 1, b = q - 1;
+            while (b) {
+                const uint32_t t = a % b;
+                a = b;
+                b = t;
+            }
+            lam[(uint64_t)k * src.P + l] = (p - 1) / a * (q - 1);
+        }
+}
+
+__device__ __forceinline__ uint32_t pow_mod32(uint32_t a, uint64_t e, uint32_t m) {
+    uint64_t r = 1 % m, b = a % m;
+    while (e) {
+        if (e & 1ull) r = r * b % m;
+        b = b * b % m;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
 
 // Thread (k, l): segment k's lane l.  Copies the caller's lane (and the
 // partner table), jumps the own generator by k * len iterations and, for
 // k >= 1, clears slot and x.
 __global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg, uint32_t K, uint64_t len,
-                                                     int variant, int xl, OwnSave own) {
-    const uint64_t total = (uint64_t)K * src.P;
+                                                     int variant, int xl, OwnSave own, const uint32_t *lam16) {
+    const int nf = variant == CI_VAR_BBS16 ? kU32FieldsBbs16 : kU32Fields;
+    const uint64_t total = (uint64_t)(K + (variant == CI_VAR_BBS16 ? 1 : 0)) * src.P;  // BBS16: slot K, a copy of the start
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
         const uint64_t k = t / src.P, l = t % src.P;
@@ -213,14 +271,22 @@ __global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg,
         for (uint64_t w = l; w < kTableBytes / 4; w += src.P)
             reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(d.table))[w] =
                 reinterpret_cast<const uint32_t *>(src.table)[w];
-        for (int f = 0; f < kU32Fields; ++f) d.u32[f * src.P + l] = src.u32[f * src.P + l];
+        for (int f = 0; f < nf; ++f) d.u32[f * src.P + l] = src.u32[f * src.P + l];
         if (variant == CI_VAR_BBS)
             for (int f = 0; f < kU64Fields; ++f) d.u64[f * src.P + l] = src.u64[f * src.P + l];
-        if (k == 0) continue;
+        if (variant == CI_VAR_BBS16)  // the arrays the call chose at its start, for every segment
+            d.u32[F_SEL * src.P + l] = (src.u32[F_Y16 * src.P + l] & 7u) | ((src.u32[(F_Y16 + 1) * src.P + l] & 7u) << 8);
+        if (k == 0 || k == K) continue;
         d.u32[F_X * src.P + l] = 0;
         d.u32[F_SLOT * src.P + l] = 0;
         const uint64_t dist = k * len;
-        if (variant == CI_VAR_BBS) {
+        if (variant == CI_VAR_BBS16) {
+            for (int g = 0; g < 8; ++g) {  // x <- x^(2^(c_g dist) mod lambda(M)) mod M
+                const uint32_t M = src.u32[(F_M16 + g) * src.P + l], lam = lam16[(uint64_t)g * src.P + l];
+                const uint32_t e = pow_mod32(2, c_bbs16_squarings[g] * dist, lam);
+                d.u32[(F_Y16 + g) * src.P + l] = pow_mod32(src.u32[(F_Y16 + g) * src.P + l], e, M);
+            }
+        } else if (variant == CI_VAR_BBS) {
             d.u64[G_Y * src.P + l] = bbs_jump(src.u64[G_Y * src.P + l], src.u64[G_M * src.P + l],
                                               src.u64[G_MU * src.P + l], src.u32[F_P * src.P + l],
                                               src.u32[F_Q * src.P + l], 11ull * dist);
@@ -240,7 +306,8 @@ __global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg,
             d.u32[F_A * src.P + l] = v[0];
         }
         if (own.u32) {
-            for (int f = 0; f < kOwnWords; ++f) own.u32[((uint64_t)f * K + k) * src.P + l] = d.u32[(F_A + f) * src.P + l];
+            for (int f = 0; f < own.count; ++f)
+                own.u32[((uint64_t)f * K + k) * src.P + l] = d.u32[(own.first + f) * src.P + l];
             if (own.u64) own.u64[k * src.P + l] = d.u64[G_Y * src.P + l];
         }
     }
@@ -361,7 +428,7 @@ __global__ void __launch_bounds__(512) k_split_carry(SegSpace seg, uint32_t K, u
             const DevState d = seg.at(j);
             d.u32[F_SLOT * P + l] = ts;
             d.u32[F_X * P + l] = tx;
-            for (int f = 0; f < kOwnWords; ++f) d.u32[(F_A + f) * P + l] = own.u32[((uint64_t)f * K + j) * P + l];
+            for (int f = 0; f < own.count; ++f) d.u32[(own.first + f) * P + l] = own.u32[((uint64_t)f * K + j) * P + l];
             if (own.u64) d.u64[G_Y * P + l] = own.u64[(uint64_t)j * P + l];
         }
     }
@@ -450,11 +517,19 @@ __global__ void __launch_bounds__(256) k_split_fixup(SegSpace seg, const uint2 *
     }
 }
 
-// The last segment's state becomes the caller's state.
-__global__ void __launch_bounds__(256) k_split_copy_back(DevState dst, DevState last) {
+// The last segment's state becomes the caller's state (the sel field, which
+// generation never changes, stays the caller's).  CI_VAR_BBS16: generator k
+// (state and modulus) moves to place k + 1, the call's one rotation.
+__global__ void __launch_bounds__(256) k_split_copy_back(DevState dst, DevState last, int variant) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < dst.P; l += stride) {
-        for (int f = 0; f < kU32Fields; ++f) dst.u32[f * dst.P + l] = last.u32[f * dst.P + l];
+        for (int f = 0; f < kU32Fields; ++f)
+            if (f != F_SEL) dst.u32[f * dst.P + l] = last.u32[f * dst.P + l];
+        if (variant == CI_VAR_BBS16)
+            for (int k = 0; k < 8; ++k) {
+                dst.u32[(F_Y16 + (k + 1) % 8) * dst.P + l] = last.u32[(F_Y16 + k) * dst.P + l];
+                dst.u32[(F_M16 + (k + 1) % 8) * dst.P + l] = last.u32[(F_M16 + k) * dst.P + l];
+            }
         if (dst.u64)
             for (int f = 0; f < kU64Fields; ++f) dst.u64[f * dst.P + l] = last.u64[f * dst.P + l];
     }
@@ -500,12 +575,13 @@ constexpr uint64_t kMinAutoSegment = 1024;  // ... when ci_generate_bbs splits o
 // k_begin + u / groups, warp group u % groups, run for its length (len, the
 // last segment len_last) by the generator's warp loop into SINK: written
 // outputs at column col0 + k len of rows of stride ld; consumer results into
-// aux + k P.  Segment 0 is the caller's own state when `caller0` is set.
+// aux + k P.  Segment 0 is the caller's own state when `zero` < 0, else the
+// segment state with that index.
 // Instantiated per source and sink, with at most 64 registers (4 blocks of 8
 // warps per SM): the all-source batched kernel needs 128, which held the
 // BBS segments to 16 resident warps per SM.
 template <class Src, int SINK>
-__global__ void __launch_bounds__(256, 4) k_split_run(SegSpace seg, DevState caller, int caller0, uint32_t k_begin,
+__global__ void __launch_bounds__(256, 4) k_split_run(SegSpace seg, DevState caller, int zero, uint32_t k_begin,
                                                    uint32_t k_end, uint32_t K, uint64_t len, uint64_t len_last,
                                                    uint64_t groups, uint32_t *out, uint64_t ld, uint64_t col0,
                                                    uint64_t *aux) {
@@ -514,7 +590,7 @@ __global__ void __launch_bounds__(256, 4) k_split_run(SegSpace seg, DevState cal
     const uint64_t units = (uint64_t)(k_end - k_begin) * groups;
     for (uint64_t u = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < units; u += (uint64_t)gridDim.x * 8) {
         const uint64_t k = k_begin + u / groups, g = u % groups;
-        const DevState st = (k == 0 && caller0) ? caller : seg.at(k);
+        const DevState st = k != 0 ? seg.at(k) : zero < 0 ? caller : seg.at((uint64_t)zero);
         const uint64_t n = k + 1 == K ? len_last : len;
         if (SINK == SINK_V4 || SINK == SINK_SCALAR)
             warp_task<Src, SINK>(st, g, n, out, ld, col0 + k * len, nullptr, tile);
@@ -524,7 +600,7 @@ __global__ void __launch_bounds__(256, 4) k_split_run(SegSpace seg, DevState cal
 }
 
 template <class Src, int SINK>
-cudaError_t launch_split_run(const SegSpace &sp, const DevState &caller, bool caller0, uint32_t kb, uint32_t ke,
+cudaError_t launch_split_run(const SegSpace &sp, const DevState &caller, int zero, uint32_t kb, uint32_t ke,
                              uint32_t K, uint64_t len, uint64_t len_last, uint32_t *out, uint64_t ld, uint64_t col0,
                              uint64_t *aux, cudaStream_t stream) {
     static int per_sm = 0;
@@ -536,17 +612,20 @@ cudaError_t launch_split_run(const SegSpace &sp, const DevState &caller, bool ca
     const uint64_t groups = caller.P / 32, units = (uint64_t)(ke - kb) * groups;
     if (units == 0) return cudaSuccess;
     const int blocks = (int)std::min<uint64_t>((units + 7) / 8, (uint64_t)sm_count() * per_sm);
-    k_split_run<Src, SINK><<<blocks, 256, 0, stream>>>(sp, caller, caller0 ? 1 : 0, kb, ke, K, len, len_last, groups,
-                                                       out, ld, col0, aux);
+    k_split_run<Src, SINK><<<blocks, 256, 0, stream>>>(sp, caller, zero, kb, ke, K, len, len_last, groups, out, ld,
+                                                       col0, aux);
     return cudaGetLastError();
 }
 
 template <int SINK>
-cudaError_t split_run_sink(int variant, int xl, const SegSpace &sp, const DevState &caller, bool caller0, uint32_t kb,
+cudaError_t split_run_sink(int variant, int xl, const SegSpace &sp, const DevState &caller, int caller0, uint32_t kb,
                            uint32_t ke, uint32_t K, uint64_t len, uint64_t len_last, uint32_t *out, uint64_t ld,
                            uint64_t col0, uint64_t *aux, cudaStream_t stream) {
     if (variant == CI_VAR_BBS)
         return launch_split_run<SrcBbs, SINK>(sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0, aux, stream);
+    if (variant == CI_VAR_BBS16)
+        return launch_split_run<SrcBbs16Seg, SINK>(sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0, aux,
+                                                   stream);
     if (xl == CI_XL_XORSHIFT32)
         return launch_split_run<SrcXorshift32, SINK>(sp, caller, caller0, kb, ke, K, len, len_last, out, ld, col0, aux,
                                                      stream);
@@ -558,8 +637,9 @@ cudaError_t split_run_sink(int variant, int xl, const SegSpace &sp, const DevSta
 }
 
 // Runs segments [kb, ke) into the caller's sink (CI_SINK_*); written outputs
-// take 16-byte stores when out, ld and col0 allow it.
-cudaError_t split_run(const ci_states_s &h, int sink, const SegSpace &sp, bool caller0, uint32_t kb, uint32_t ke,
+// take 16-byte stores when out, ld and col0 allow it.  Segment 0: the caller's
+// state (zero < 0) or segment state `zero`.
+cudaError_t split_run(const ci_states_s &h, int sink, const SegSpace &sp, int caller0, uint32_t kb, uint32_t ke,
                       uint32_t K, uint64_t len, uint64_t len_last, uint32_t *out, uint64_t ld, uint64_t col0,
                       uint64_t *aux, cudaStream_t stream) {
     const DevState caller = h.view();
@@ -616,10 +696,18 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
                        uint64_t *aux, uint64_t K, cudaStream_t stream) {
     TraceRange trace("split");
     const ci_states_s *h = &hs;
+    const bool b16 = h->variant == CI_VAR_BBS16, bbs = h->variant == CI_VAR_BBS;
     cudaError_t e;
     if (K <= 1) {  // one segment: the caller's state, straight into the sink
-        SegSpace none{};
-        e = split_run(*h, sink, none, true, 0, 1, 1, n, n, out, ld, col0, aux, stream);
+        if (b16) {  // one whole call, with its array choice and rotation
+            if (sink == CI_SINK_QC) e = launch_fused_qc(*h, n, aux, stream);
+            else if (sink == CI_SINK_DIGEST) e = launch_digest(*h, n, aux, stream);
+            else if (ld == n && col0 == 0) e = launch_generate(*h, n, out, stream);
+            else return fail(CI_E_INVAL, "unsplit CI_VAR_BBS16 output needs ld == n and col0 == 0");
+        } else {
+            SegSpace none{};
+            e = split_run(*h, sink, none, -1, 0, 1, 1, n, n, out, ld, col0, aux, stream);
+        }
         return e == cudaSuccess ? CI_OK : cuda_fail(e, "split run");
     }
     if ((e = ensure_jump_tables(stream)) != cudaSuccess) return cuda_fail(e, "jump tables");
@@ -628,28 +716,32 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     const uint64_t len_last = n - (K - 1) * len;
 
     const uint64_t stride = (h->bytes + 255) / 256 * 256;
+    const uint64_t slots = K + (b16 ? 1 : 0);  // BBS16: slot K keeps the call's start (for pass 2)
     // Written BBS outputs are fixed up in place (generation is the cost);
     // xor-like outputs are cheaper to generate again than to read back.
     const bool written = sink == CI_SINK_WRITTEN;
-    const bool fixup = written && h->variant == CI_VAR_BBS;
+    const bool fixup = written && (bbs || b16);
+    const int own_first = b16 ? (int)F_Y16 : (int)F_A, own_count = b16 ? 8 : kOwnWords;
     const uint64_t res_bytes = 8ull * K * h->P;  // per-segment consumer results
-    const uint64_t own_bytes = fixup ? 0 : (4ull * kOwnWords + 8ull) * K * h->P;
+    const uint64_t own_bytes = fixup ? 0 : (4ull * own_count + (bbs ? 8ull : 0ull)) * K * h->P;
+    const uint64_t lam_bytes = b16 ? 4ull * 8 * h->P : 0;
     uint8_t *ws = nullptr;
-    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&ws), stride * K + 2 * res_bytes + own_bytes, stream)) !=
-        cudaSuccess)
+    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&ws), stride * slots + 2 * res_bytes + own_bytes + lam_bytes,
+                             stream)) != cudaSuccess)
         return cuda_fail(e, "workspace");
-    uint64_t *res1 = reinterpret_cast<uint64_t *>(ws + stride * K);
+    uint64_t *res1 = reinterpret_cast<uint64_t *>(ws + stride * slots);
     uint64_t *res3 = res1 + K * h->P;
-    OwnSave own{nullptr, nullptr};
+    uint8_t *after = reinterpret_cast<uint8_t *>(res3 + K * h->P);
+    OwnSave own{nullptr, nullptr, own_first, own_count};
     if (!fixup) {
-        own.u32 = reinterpret_cast<uint32_t *>(res3 + K * h->P);
-        own.u64 = h->variant == CI_VAR_BBS ? reinterpret_cast<uint64_t *>(own.u32 + (uint64_t)kOwnWords * K * h->P)
-                                           : nullptr;
+        own.u32 = reinterpret_cast<uint32_t *>(after);
+        own.u64 = bbs ? reinterpret_cast<uint64_t *>(own.u32 + (uint64_t)own_count * K * h->P) : nullptr;
     }
+    uint32_t *lam16 = b16 ? reinterpret_cast<uint32_t *>(after + own_bytes) : nullptr;
 
     // Handles over the segment states (host copies of the caller's, moved).
-    std::vector<ci_states_s> segs(K, *h);
-    for (uint64_t k = 0; k < K; ++k) {
+    std::vector<ci_states_s> segs(slots, *h);
+    for (uint64_t k = 0; k < slots; ++k) {
         segs[k].dev = ws + k * stride;
         segs[k].owns = false;
     }
@@ -659,22 +751,25 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     const DevState src = h->view();
 
     ci_status st = CI_OK;
-    k_split_setup<<<split_block_count(K * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl,
-                                                                   own);
+    if (b16) k_split_lambda16<<<split_block_count(h->P), 256, 0, stream>>>(src, lam16);
+    k_split_setup<<<split_block_count(slots * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl,
+                                                                       own, lam16);
     if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split setup");
 
     uint2 *starts = reinterpret_cast<uint2 *>(res1);  // K * P (slot, x) pairs, after pass 1
     if (st == CI_OK) {  // pass 1: particular solutions (fix-up: all segments, into their columns)
-        e = fixup ? split_run(*h, sink, sp, false, 0, (uint32_t)K, (uint32_t)K, len, len_last, out, ld, col0, nullptr,
+        e = fixup ? split_run(*h, sink, sp, 0, 0, (uint32_t)K, (uint32_t)K, len, len_last, out, ld, col0, nullptr,
                               stream)
-                  : split_run(*h, CI_SINK_DIGEST, sp, false, 0, (uint32_t)K - 1, (uint32_t)K, len, len_last, nullptr,
-                              0, 0, res1, stream);
+                  : split_run(*h, CI_SINK_DIGEST, sp, 0, 0, (uint32_t)K - 1, (uint32_t)K, len, len_last, nullptr, 0,
+                              0, res1, stream);
         if (e != cudaSuccess) st = cuda_fail(e, "split pass 1");
     }
     if (st == CI_OK) {
         const unsigned threads = 32u * (unsigned)std::min<uint64_t>(16, K - 1);
-        if (h->variant == CI_VAR_BBS)
+        if (bbs)
             k_split_carry<SrcBbs><<<(unsigned)groups, threads, 0, stream>>>(sp, (uint32_t)K, len, starts, own);
+        else if (b16)
+            k_split_carry<SrcBbs16Seg><<<(unsigned)groups, threads, 0, stream>>>(sp, (uint32_t)K, len, starts, own);
         else
             k_split_carry<SrcXor128><<<(unsigned)groups, threads, 0, stream>>>(sp, (uint32_t)K, len, starts, own);
         if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split carry");
@@ -682,18 +777,18 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     if (st == CI_OK && fixup) {  // homogeneous parts into segments 1 .. K-1, then the final state
         const bool v4 = (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && ld % 4 == 0 && col0 % 4 == 0;
         const int blocks = split_block_count((K - 1) * groups * 32);
-        if (h->variant == CI_VAR_BBS)
+        if (bbs)
             v4 ? k_split_fixup<SrcBbs, true><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
                                                                           groups, out, ld, col0)
                : k_split_fixup<SrcBbs, false><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
                                                                            groups, out, ld, col0);
         else
-            v4 ? k_split_fixup<SrcXor128, true><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
-                                                                             groups, out, ld, col0)
-               : k_split_fixup<SrcXor128, false><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
-                                                                              groups, out, ld, col0);
+            v4 ? k_split_fixup<SrcBbs16Seg, true><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len, len_last,
+                                                                               groups, out, ld, col0)
+               : k_split_fixup<SrcBbs16Seg, false><<<blocks, 256, 0, stream>>>(sp, starts, (uint32_t)K, len,
+                                                                                len_last, groups, out, ld, col0);
         if ((e = cudaGetLastError()) == cudaSuccess)
-            k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view());
+            k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view(), h->variant);
         if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split fix-up");
         cudaFreeAsync(ws, stream);
         return st;
@@ -701,11 +796,12 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     if (st == CI_OK && sink == CI_SINK_QC && (e = cudaMemsetAsync(res3, 0, res_bytes, stream)) != cudaSuccess)
         st = cuda_fail(e, "clearing counts");
     if (st == CI_OK) {  // pass 2: every segment from its true start into the sink
-        e = split_run(*h, sink, sp, true, 0, (uint32_t)K, (uint32_t)K, len, len_last, out, ld, col0, res3, stream);
+        e = split_run(*h, sink, sp, b16 ? (int)K : -1, 0, (uint32_t)K, (uint32_t)K, len, len_last, out, ld, col0,
+                      res3, stream);
         if (e != cudaSuccess) st = cuda_fail(e, "split pass 2");
     }
     if (st == CI_OK) {
-        k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view());
+        k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view(), h->variant);
         if (!written)
             k_split_combine<<<(unsigned)((h->S + 255) / 256), 256, 0, stream>>>(res3, aux, h->P, h->S, (uint32_t)K,
                                                                                 len, len_last, sink == CI_SINK_DIGEST);
@@ -721,8 +817,6 @@ extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, vo
                                        uint64_t out_capacity, uint32_t n_segments, void *cuda_stream) {
     using namespace ci;
     if (!valid_handle(h)) return fail(CI_E_STATE, "invalid states handle");
-    if (h->variant == CI_VAR_BBS16)
-        return fail(CI_E_STATE, "CI_VAR_BBS16 outputs depend on call boundaries; it cannot be split");
     if (sink != CI_SINK_WRITTEN && sink != CI_SINK_QC && sink != CI_SINK_DIGEST)
         return fail(CI_E_INVAL, "unknown sink");
     if (n == 0) return CI_OK;
@@ -734,7 +828,7 @@ extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, vo
     if (K <= 1) {  // unsplit: the tuned single-call kernels
         if (sink == CI_SINK_QC) return ci_generate_fused_qc(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
         if (sink == CI_SINK_DIGEST) return ci_generate_digest(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
-        return h->variant == CI_VAR_BBS
+        return h->variant != CI_VAR_XOR
                    ? ci_generate_bbs(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream)
                    : ci_generate(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream);
     }

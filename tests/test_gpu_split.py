@@ -1,7 +1,8 @@
 """Time-parallel generation (ci_generate_split): outputs, consumer results and
-the final state equal the sequential oracle for every splittable source, group
-size, ragged stream count and segment count, and a split call continues
-exactly like a sequential one."""
+the final state equal the sequential oracle for every source (Algorithm 5 as
+printed included: a split call keeps its one array choice and its one
+rotation), group size, ragged stream count and segment count, and a split
+call continues exactly like a sequential one."""
 import numpy as np
 import pytest
 
@@ -9,7 +10,7 @@ from gpu_util import cuda_or_skip, digest_rows, oracle_gen, u32
 
 pytestmark = pytest.mark.gpu
 
-CASES = [("xor", "xor128"), ("xor", "xorshift32"), ("xor", "xor64"), ("bbs", "xor128")]
+CASES = [("xor", "xor128"), ("xor", "xorshift32"), ("xor", "xor64"), ("bbs", "xor128"), ("bbs16", "xor128")]
 
 
 def _states(ci, variant, xl, C, seed, S):
@@ -21,7 +22,7 @@ def _states(ci, variant, xl, C, seed, S):
 @pytest.mark.parametrize("segments", [3, 7, 0])
 def test_written_matches_oracle_and_continues(variant, xl, C, S, segments):
     torch, ci = cuda_or_skip()
-    n = 1000 if variant == "xor" else 300
+    n = 1000 if variant == "xor" else 300 if variant == "bbs" else 640
     seed = 11 + C + S
     st = _states(ci, variant, xl, C, seed, S)
     orc = oracle_gen(variant, xl, C, seed, seed + 7, S)
@@ -30,11 +31,12 @@ def test_written_matches_oracle_and_continues(variant, xl, C, S, segments):
     nxt = u32(st.generate(50))  # the final state is the sequential one
     assert np.array_equal(nxt, orc.streams(50))
     ref = _states(ci, variant, xl, C, seed, S)
-    ref.generate(n + 50)
+    ref.generate(n)  # the same two calls (Algorithm 5 as printed depends on call boundaries)
+    ref.generate(50)
     assert np.array_equal(st.export_state()[512:], ref.export_state()[512:])
 
 
-@pytest.mark.parametrize("variant,xl", [("xor", "xor128"), ("bbs", "xor128")])
+@pytest.mark.parametrize("variant,xl", [("xor", "xor128"), ("bbs", "xor128"), ("bbs16", "xor128")])
 def test_consumer_sinks(variant, xl):
     torch, ci = cuda_or_skip()
     n, S, C = 640, 40, 8
@@ -62,12 +64,8 @@ def test_long_narrow_stream_auto_segments():
     assert np.array_equal(u32(st.generate(64)), orc.streams(64))
 
 
-def test_unsplittable_and_bad_arguments():
+def test_bad_arguments():
     torch, ci = cuda_or_skip()
-    b16 = _states(ci, "bbs16", "xor128", 32, 3, 32)
-    with pytest.raises(ci.CIError) as e:
-        b16.generate_split(256, segments=2)
-    assert e.value.status == -6
     st = _states(ci, "xor", "xor128", 32, 3, 32)
     with pytest.raises(ci.CIError) as e:
         st.generate_split(255, sink="qc", segments=2)
@@ -94,3 +92,15 @@ def test_segment_cap():
     bb = _states(ci, "bbs", "xor128", 32, 72, 32)
     out = u32(bb.generate_split(n, segments=8192))
     assert np.array_equal(out, oracle_gen("bbs", "xor128", 32, 72, 79, 32).streams(n))
+
+
+def test_bbs16_long_narrow():
+    """One warp of Algorithm 5 as printed over 2^16 iterations in 512 segments
+    equals the oracle's single call, and the next call (new array choice after
+    the rotation) continues it."""
+    torch, ci = cuda_or_skip()
+    n, S = 1 << 16, 32
+    st = _states(ci, "bbs16", "xor128", 32, 81, S)
+    orc = oracle_gen("bbs16", "xor128", 32, 81, 88, S)
+    assert np.array_equal(u32(st.generate_split(n, segments=512)), orc.streams(n))
+    assert np.array_equal(u32(st.generate(100)), orc.streams(100))
