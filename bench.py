@@ -7,8 +7,10 @@ to HBM as 16 time chunks of 256 outputs per stream (1 GiB per launch).
 Alongside: the same workload fused into the quarter-circle consumer (no
 stores), the BBS-driven secure variant on 2^16 streams x 16384, the
 end-to-end figure through the public API with host buffers, the chaotic
-Blum-Goldwasser cryptosystem (Sec. 9.2) on 2^20 messages x 1024 chunks, and
-the CPU oracle timed on the host cores.
+Blum-Goldwasser cryptosystem (Sec. 9.2) on 2^20 messages x 1024 chunks,
+samples of the batched (one launch vs one per request) and serving
+(saturation, p50 / p99 at half load) suites, and the CPU oracle timed on the
+host cores.
 
 Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): each rank generates its
 own slice of a global stream range (first_stream = rank * 2^20), no exchange;
@@ -465,6 +467,9 @@ def main():
         result["split"] = bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["naive"] = bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
         if rank == 0 and world == 1:
+            result["batched_sample"] = bench_batched_sample(torch, ci)
+            result["serving_sample"] = bench_serving_sample(ci)
+        if rank == 0 and world == 1:
             threads = os.cpu_count() or 1
             r, n, dt = oracle_sample(args.cpu_sample_streams, threads=threads)
             r1, n1, dt1 = oracle_sample(args.cpu_sample_streams // 16)
@@ -674,6 +679,68 @@ def bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
     return {"value": world * S_MAIN * L_MAIN / (ms / 1e3), "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
             "workload": "Listing 1 run by each of 2^20 streams (Algorithm 3: three 64-bit xor-likes, no mixing), "
                         "4096 outputs each in 16 written launches of 256"}
+
+
+def bench_batched_sample(torch, ci):
+    """A smaller form of --suite batched inside the default run: 2000 requests
+    (seed 4; streams log-uniform [1, 2^16], lengths log-uniform [2^6, 2^16],
+    80 % xor128 / 20 % BBS) into the digest sink, as ONE persistent batched
+    launch and as one launch per request; digests compared."""
+    from paper_1112_5239_gb300.workloads import batched_requests
+
+    reqs = batched_requests(seed=4, count=2000, max_len_log2=16)
+    specs = [dict(n_streams=r.n_streams, variant=r.variant, seed=r.seed) for r in reqs]
+    A = ci.States.many(specs)
+    B = ci.States.many(specs)
+    dA = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+    dB = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+    b = ci.Batch(len(reqs))
+    w = ci.States(64, seed=99)
+    wd = torch.zeros(64, dtype=torch.int64, device="cuda")
+    b.run([(w, 64, "digest", wd)])  # loads the kernel, instantiates the graph
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    b.run([(st, r.n_per_stream, "digest", d) for st, r, d in zip(A, reqs, dA)])
+    e[1].record()
+    torch.cuda.synchronize()
+    e[2].record()
+    for st, r, d in zip(B, reqs, dB):
+        st.generate_digest(r.n_per_stream, digest=d)
+    e[3].record()
+    torch.cuda.synchronize()
+    sec_b, sec_p = e[0].elapsed_time(e[1]) / 1e3, e[2].elapsed_time(e[3]) / 1e3
+    n_out = sum(r.n_streams * r.n_per_stream for r in reqs)
+    identical = all(torch.equal(x, y) for x, y in zip(dA, dB))
+    b.close()
+    return {"workload": "2000 requests, seed 4, streams log-uniform [1, 2^16], lengths log-uniform [2^6, 2^16], "
+                        "80%% xor128 / 20%% BBS, digest sink (%d outputs)" % n_out,
+            "batched": {"value": n_out / sec_b, "seconds": sec_b, "launches": 1},
+            "per_request": {"value": n_out / sec_p, "seconds": sec_p, "launches": len(reqs)},
+            "batched_over_per_request": sec_p / sec_b, "identical_digests": bool(identical), "unit": "uint32/s"}
+
+
+def bench_serving_sample(ci):
+    """A smaller form of --suite serving inside the default run: 5000 requests
+    of the serving mix (seed 5) all at t = 0 (saturation), then as Poisson
+    arrivals at half that rate; p50 / p99 from submission to completion."""
+    import dataclasses
+
+    from paper_1112_5239_gb300.workloads import serving_requests
+
+    base = serving_requests(seed=5, count=5000, rate=1.0)
+    srv, _, _ = _serving_run(ci, [dataclasses.replace(r, arrival=0.0) for r in base[:300]], 64)  # warm-up
+    srv.close()
+    srv, _, sat = _serving_run(ci, [dataclasses.replace(r, arrival=0.0) for r in base], 64)
+    srv.close()
+    rate = 0.5 * sat["steady_req_per_s"]
+    srv, _, half = _serving_run(ci, [dataclasses.replace(r, arrival=r.arrival / rate) for r in base], 64)
+    srv.close()
+    keys = ("value", "req_per_s", "steady_value", "steady_req_per_s", "p50_ms", "p99_ms", "split_jobs", "ok")
+    return {"workload": "5000 requests of the serving mix (seed 5: lognormal sizes, median 2^16, sigma 2, cap 2^28; "
+                        "30% continuations; 80% xor128 / 20% BBS), 64 GiB arena",
+            "saturation": {k: sat[k] for k in keys},
+            "half_load": dict({k: half[k] for k in keys}, offered_req_per_s=rate), "unit": "uint32/s"}
 
 
 def bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):
