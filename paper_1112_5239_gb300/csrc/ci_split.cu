@@ -14,20 +14,21 @@
 // Steps of one call (all on the caller's stream):
 //   1. k_split_setup: segment states k = 0 .. K-1 are copies of the state
 //      with the own generator jumped ahead by k len iterations (GF(2) matrix
-//      powers for the xor-likes, x <- x^(2^(11 k len) mod lambda(M)) for BBS)
-//      and (s, x) = (0, 0) for k >= 1;
-//   2. one batched launch runs the segments from there: written sink, all of
-//      them into their output columns; consumer sinks, segments 0 .. K-2
-//      into a digest sink (only their end states are needed);
+//      powers for the xor-likes, x <- x^(2^(11 k len) mod lambda(M)) for BBS,
+//      each of the eight 16-bit generators by its own squaring count for
+//      Algorithm 5 as printed) and (s, x) = (0, 0) for k >= 1;
+//   2. pass 1 (k_split_run): written BBS outputs: every segment from there
+//      into its output columns; otherwise segments 0 .. K-2 into a digest
+//      sink (only their end states are needed);
 //   3. k_split_carry: one block per warp group scans the segments: the true
 //      start of segment k is its predecessor's particular end plus
 //      (Q s_a, x_a ^ S s_a) with Q = P^len, S = P + ... + P^len (a chunked
-//      parallel scan over up to 16 warps); the own words of segment k are
-//      those k_split_setup jumped to;
-//   4. written sink: k_split_fixup XORs each segment's homogeneous part into
-//      its outputs (the mixing step with zero own words: two shuffles per
-//      output); consumer sinks: one batched launch runs every segment from
-//      its true start into the sink (segment 0 is the caller's state);
+//      parallel scan over up to 16 warps);
+//   4. written BBS outputs: k_split_fixup XORs each segment's homogeneous
+//      part into its outputs (the mixing step with zero own words: two
+//      shuffles per output); otherwise pass 2 (k_split_run) runs every
+//      segment from its true start, with the own words k_split_setup jumped
+//      to, into the sink;
 //   5. the last segment's end state becomes the caller's state, and the
 //      per-segment quarter-circle counts or digests are combined.
 #include <cuda_runtime.h>
