@@ -156,7 +156,9 @@ ci_status ci_states_query(ci_states states, ci_states_desc *out);
  * o = group base + comb[s % C]); slot[s] = t; x ^= t; output x.
  * Errors: CI_E_STATE (BBS handle), CI_E_INVAL (null output, or
  * out_capacity_u32 < n_streams * n_per_stream), CI_E_CUDA.
- * n_per_stream == 0 is a no-op. */
+ * n_per_stream == 0 is a no-op.  A state of at most one warp group (32
+ * streams) per SM is run as time segments, as ci_generate_split does, with
+ * identical results; that form allocates a stream-ordered workspace. */
 ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev,
                       uint64_t out_capacity_u32, void *cuda_stream);
 
@@ -188,7 +190,8 @@ ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out
  * caller-owned, n_streams elements) is INCREMENTED by the number of points
  * with a^2 + b^2 < 1 (exact integer test (o0>>8)^2 + (o1>>8)^2 < 2^48).
  * Works for both variants; the state advances exactly as in the written
- * form.  n_per_stream must be even (CI_E_INVAL otherwise). */
+ * form.  n_per_stream must be even (CI_E_INVAL otherwise).  Narrow states run
+ * as time segments as in ci_generate / ci_generate_bbs (identical counts). */
 ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t *counts_dev,
                                void *cuda_stream);
 
@@ -198,7 +201,8 @@ ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t
  * K = 0xD1342543DE82EF95 (D <- D * K + o_i from D = 0).  No outputs are
  * stored; the state advances as in the written form.  Not a construct of the
  * paper: it lets very large runs be compared without holding their outputs.
- * n_per_stream == 0 is a no-op.
+ * n_per_stream == 0 is a no-op.  Narrow states run as time segments as in
+ * ci_generate / ci_generate_bbs (identical digests).
  * Errors: CI_E_STATE, CI_E_INVAL (digest_dev NULL with n > 0), CI_E_CUDA. */
 ci_status ci_generate_digest(ci_states states, uint64_t n_per_stream, uint64_t *digest_dev,
                              void *cuda_stream);
@@ -494,7 +498,10 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * and the final state IDENTICAL to the sequential call (ci_generate /
  * ci_generate_bbs for CI_SINK_WRITTEN, ci_generate_fused_qc for CI_SINK_QC,
  * ci_generate_digest for CI_SINK_DIGEST).  For states with few streams and
- * long lengths, whose sequential chains leave most of the GPU idle.
+ * long lengths, whose sequential chains leave most of the GPU idle.  (Those
+ * single-call entry points split such states on their own: CI_VAR_BBS states
+ * under about two waves of resident warps, xor-like states of at most one
+ * warp group per SM, with segments of at least 1024 iterations.)
  * Method: each segment's own generator is jumped ahead (xor-likes: GF(2)
  * matrix powers of their step; BBS: x <- x^(2^(11 k len) mod lcm(p-1, q-1))
  * mod M), the segments run from a zero mixing state, a per-warp scan restores

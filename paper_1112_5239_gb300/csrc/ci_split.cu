@@ -569,8 +569,8 @@ __global__ void __launch_bounds__(256) k_split_combine(const uint64_t *r, uint64
 
 // ------------------------------------------------ host side
 constexpr uint32_t kMaxSegments = kSplitMaxSegments;
-constexpr uint64_t kMinSegment = 256;       // iterations per segment (auto choice)
-constexpr uint64_t kMinAutoSegment = 1024;  // ... when ci_generate_bbs splits on its own
+constexpr uint64_t kMinSegment = 256;       // iterations per segment (auto choice, BBS)
+constexpr uint64_t kMinAutoSegment = 1024;  // ... xor-likes, and when a single call splits on its own
 
 // One pass over segments [k_begin, k_end): work unit u is segment
 // k_begin + u / groups, warp group u % groups, run for its length (len, the
@@ -674,8 +674,11 @@ uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested) {
     uint64_t K = requested;
     if (K == 0) {  // fill about four waves of resident warps
         const uint64_t target = (uint64_t)sm_count() * 64;
+        // cheap xor-like segments: fewer, longer ones (the setup's GF(2) jumps
+        // cost more than their generation)
+        const uint64_t min_len = h.variant == CI_VAR_XOR ? kMinAutoSegment : kMinSegment;
         K = std::max<uint64_t>(1, target / groups);
-        K = std::min<uint64_t>(K, std::max<uint64_t>(1, n / kMinSegment));
+        K = std::min<uint64_t>(K, std::max<uint64_t>(1, n / min_len));
     }
     K = std::min<uint64_t>(K, kMaxSegments);
     const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;  // whole staging tiles, 16-byte column offsets
@@ -687,6 +690,20 @@ uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n) {
     const uint64_t target = (uint64_t)sm_count() * 128;  // about two waves of resident BBS warps
     if (h.variant != CI_VAR_BBS || groups * 2 > target) return 1;
     uint64_t K = std::min<uint64_t>(target / groups, std::max<uint64_t>(1, n / kMinAutoSegment));
+    K = std::min<uint64_t>(K, kMaxSegments);
+    if (K <= 1) return 1;
+    const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;
+    return (n + len - 1) / len;
+}
+
+uint64_t split_auto(const ci_states_s &h, uint64_t n) {
+    if (h.variant == CI_VAR_BBS) return split_auto_bbs(h, n);
+    const uint64_t groups = h.P / 32, sms = (uint64_t)sm_count();
+    // xor-likes: only states with no more warp groups than SMs (measured:
+    // 4-11x faster up to 128 groups, slower from 512 groups on, where the
+    // setup's GF(2) jumps outweigh the parallelism)
+    if (h.variant != CI_VAR_XOR || groups > sms) return 1;
+    uint64_t K = std::min<uint64_t>(sms * 64 / groups, std::max<uint64_t>(1, n / kMinAutoSegment));
     K = std::min<uint64_t>(K, kMaxSegments);
     if (K <= 1) return 1;
     const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;

@@ -21,6 +21,11 @@ uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested);
 // states that fill less than about two waves of resident warps.
 uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n);
 
+// Segment count the single-call entry points use on their own: split_auto_bbs
+// for CI_VAR_BBS; for xor-like states only with no more warp groups than SMs
+// (and segments of at least 1024 iterations); 1 otherwise.
+uint64_t split_auto(const ci_states_s &h, uint64_t n);
+
 // n iterations of h as K segments into `sink` (written: out[r * ld + col0 + i];
 // consumers: aux[r]), with results equal to one sequential call.  Calls on
 // different streams are independent (no shared queue or lock).
