@@ -77,16 +77,16 @@ def test_bad_arguments():
 
 
 def test_segment_cap():
-    """At the cap of 8192 segments: one xor128 warp over 2^21 iterations (the
-    auto choice reaches the cap; written and digest forms) and one BBS warp
-    over 2^20 iterations in 8192 segments of 128 equal the oracle."""
+    """At the cap of 8192 segments: one xor128 warp over 2^21 iterations in
+    8192 segments of 256 (written and digest forms) and one BBS warp over 2^20
+    iterations in 8192 segments of 128 equal the oracle."""
     torch, ci = cuda_or_skip()
     n = 1 << 21
     st = _states(ci, "xor", "xor128", 32, 71, 32)
-    out = u32(st.generate_split(n))
+    out = u32(st.generate_split(n, segments=8192))
     orc = oracle_gen("xor", "xor128", 32, 71, 78, 32)
     assert np.array_equal(out, orc.streams(n))
-    d = st.generate_split(n, sink="digest").cpu().numpy().view(np.uint64)
+    d = st.generate_split(n, sink="digest", segments=8192).cpu().numpy().view(np.uint64)
     assert np.array_equal(d, digest_rows(orc.streams(n)))
     n = 1 << 20
     bb = _states(ci, "bbs", "xor128", 32, 72, 32)
@@ -104,3 +104,20 @@ def test_bbs16_long_narrow():
     orc = oracle_gen("bbs16", "xor128", 32, 81, 88, S)
     assert np.array_equal(u32(st.generate_split(n, segments=512)), orc.streams(n))
     assert np.array_equal(u32(st.generate(100)), orc.streams(100))
+
+
+def test_single_calls_split_narrow_states_on_their_own():
+    """ci_generate, ci_generate_fused_qc and ci_generate_digest on one warp of
+    xor128 streams over 2^13 iterations (split on their own into 8 segments)
+    equal the oracle, call after call."""
+    torch, ci = cuda_or_skip()
+    n = 1 << 13
+    st = _states(ci, "xor", "xor128", 32, 91, 32)
+    orc = oracle_gen("xor", "xor128", 32, 91, 98, 32)
+    assert np.array_equal(u32(st.generate(n)), orc.streams(n))
+    d = st.generate_digest(n).cpu().numpy().view(np.uint64)
+    assert np.array_equal(d, digest_rows(orc.streams(n)))
+    c = st.generate_fused_qc(n).cpu().numpy().view(np.uint64)
+    o = orc.streams(n)
+    hits = (((o[:, 0::2] >> 8).astype(np.uint64) ** 2 + (o[:, 1::2] >> 8).astype(np.uint64) ** 2) < (1 << 48)).sum(axis=1)
+    assert np.array_equal(c, hits.astype(np.uint64))
