@@ -292,10 +292,18 @@ __device__ __forceinline__ uint32_t ci_step(Src &src, uint32_t &x, uint32_t &slo
     return x;
 }
 
-// Quarter-circle test of one output pair in 24-bit fixed point.
-__device__ __forceinline__ uint32_t qc_hit(uint32_t o0, uint32_t o1) {
-    const uint64_t a = o0 >> 8, b = o1 >> 8;
-    return (a * a + b * b < (1ull << 48)) ? 1u : 0u;
+// Quarter-circle test of one output pair in 24-bit fixed point, as a miss:
+// a = o0 >> 8, b = o1 >> 8, and the pair misses iff a^2 + b^2 >= 2^48, i.e.
+// iff bit 16 of the high word of the (at most 49-bit) sum is set.  The two
+// shifts and the bit test are written as high halves of products by 2^24 and
+// 2^16, which keep them on the FMA pipe: the fused loop is otherwise bound by
+// the integer ALU pipe (xor-like shifts, mixing XORs).  The multipliers sit in
+// constant memory so that they stay multiplies.
+static __constant__ uint32_t c_qc_mul[2] = {1u << 24, 1u << 16};
+__device__ __forceinline__ uint32_t qc_miss(uint32_t o0, uint32_t o1) {
+    const uint32_t a = __umulhi(o0, c_qc_mul[0]), b = __umulhi(o1, c_qc_mul[0]);
+    const uint64_t s = (uint64_t)a * a + (uint64_t)b * b;
+    return __umulhi((uint32_t)(s >> 32), c_qc_mul[1]);
 }
 
 // Launch-shape choices of the written sinks, picked by the autotuner:
@@ -367,14 +375,14 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
 #pragma unroll(Src::kHeavy ? 1 : 32)
             for (int k = 0; k < 32; ++k) hits = hits * kDigestMul + ci_step(src, x, slot, p1, p2);
         } else if (SINK == SINK_QC) {
-            uint32_t h = 0;
+            uint32_t m = 0;
 #pragma unroll(Src::kHeavy ? 1 : 16)
             for (int k = 0; k < 16; ++k) {
                 const uint32_t o0 = ci_step(src, x, slot, p1, p2);
                 const uint32_t o1 = ci_step(src, x, slot, p1, p2);
-                h += qc_hit(o0, o1);
+                m += qc_miss(o0, o1);
             }
-            hits += h;
+            hits += 16u - m;
         } else {
 #pragma unroll(Src::kHeavy ? 1 : CH)
             for (int q = 0; q < CH; ++q) {
@@ -414,13 +422,13 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
         if (SINK == SINK_DIGEST) {
             for (int k = 0; k < rem; ++k) hits = hits * kDigestMul + ci_step(src, x, slot, p1, p2);
         } else if (SINK == SINK_QC) {
-            uint32_t h = 0;
+            uint32_t m = 0;
             for (int k = 0; k < rem / 2; ++k) {
                 const uint32_t o0 = ci_step(src, x, slot, p1, p2);
                 const uint32_t o1 = ci_step(src, x, slot, p1, p2);
-                h += qc_hit(o0, o1);
+                m += qc_miss(o0, o1);
             }
-            hits += h;
+            hits += (uint32_t)(rem / 2) - m;
         } else {
             for (int k = 0; k < rem; ++k) tw[tile_word<KT>(lane, k)] = ci_step(src, x, slot, p1, p2);
             __syncwarp();
