@@ -4,7 +4,7 @@ sampled groups (groups are independent, so a sampled group is exact)."""
 import numpy as np
 import pytest
 
-from gpu_util import cuda_or_skip, oracle_gen, u32
+from gpu_util import cuda_or_skip, digest_rows_pow, oracle_gen, u32
 
 pytestmark = pytest.mark.gpu
 
@@ -87,3 +87,42 @@ def test_sharded_handles_reproduce_one_range(env):
     whole = u32(ci.States(S, seed=12, comb_size=16).generate(L))
     parts = [u32(ci.States(1024, seed=12, comb_size=16, first_stream=r * 1024).generate(L)) for r in range(4)]
     assert np.array_equal(np.concatenate(parts), whole)
+
+
+def test_batched_10000_requests_full_size_sampled(env):
+    """The 10,000-request uneven workload (seed 4: streams log-uniform in
+    [1, 2^16], lengths log-uniform in [2^6, 2^20], 80 % xor128 / 20 % BBS) at
+    full size, as the benchmark runs it: states seeded in one launch, all
+    requests in ONE persistent batched launch into the digest sink.  The
+    oracle recomputes the first and the last group of a seeded sample of
+    requests over their whole length (the longest xor request, the widest
+    request of each variant, and random others)."""
+    torch, ci = env
+    from paper_1112_5239_gb300.workloads import batched_requests
+
+    reqs = batched_requests(seed=4)
+    specs = [dict(n_streams=r.n_streams, variant=r.variant, seed=r.seed) for r in reqs]
+    A = ci.States.many(specs)
+    d = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+    b = ci.Batch(len(reqs))
+    b.run([(st, r.n_per_stream, "digest", x) for st, r, x in zip(A, reqs, d)])
+    torch.cuda.synchronize()
+    b.close()
+
+    xor = [i for i, r in enumerate(reqs) if r.variant == "xor"]
+    bbs = [i for i, r in enumerate(reqs) if r.variant == "bbs"]
+    rng = np.random.default_rng(44)
+    sample = {max(xor, key=lambda i: reqs[i].n_per_stream), max(xor, key=lambda i: reqs[i].n_streams),
+              max(bbs, key=lambda i: reqs[i].n_streams)}
+    sample |= set(rng.choice(xor, size=4, replace=False).tolist()) | set(rng.choice(bbs, size=3, replace=False).tolist())
+    checked = 0
+    for i in sorted(sample):
+        r = reqs[i]
+        got = d[i].cpu().numpy().view(np.uint64)
+        groups = (r.n_streams + 31) // 32
+        for g in sorted({0, groups - 1}):
+            ref = oracle_gen(r.variant, "xor128", 32, r.seed, 0, r.n_streams, lane0=32 * g, n_lanes=32)
+            want = digest_rows_pow(ref.streams(r.n_per_stream))
+            assert np.array_equal(got[32 * g: 32 * g + want.shape[0]], want), (i, g)
+            checked += want.shape[0]
+    assert checked >= 10 * 32 // 2
