@@ -126,3 +126,45 @@ def test_batched_10000_requests_full_size_sampled(env):
             assert np.array_equal(got[32 * g: 32 * g + want.shape[0]], want), (i, g)
             checked += want.shape[0]
     assert checked >= 10 * 32 // 2
+
+
+def test_serving_mix_20000_requests_full_size_sampled(env):
+    """20,000 requests of the serving mix at full size (seed 5: lognormal
+    sizes with median 2^16 numbers, sigma 2, cap 2^28; 30 % continuations;
+    80/20 xor128/BBS), all arriving at once (saturation) at a server over a
+    64 GiB arena, as the benchmark's serving runs drive it.  The first and the
+    last group of a seeded sample of requests (continuations and the largest
+    request that the oracle can recompute included) equal the oracle's
+    uninterrupted streams at their offsets."""
+    import dataclasses
+
+    torch, ci = env
+    from paper_1112_5239_gb300.workloads import serving_requests
+
+    reqs = [dataclasses.replace(r, arrival=0.0) for r in serving_requests(seed=5, count=20000, rate=1.0)]
+    root, offset, seen = [], [], {}
+    for i, r in enumerate(reqs):
+        root.append(i if r.continues < 0 else root[r.continues])
+        offset.append(seen.get(root[i], 0))
+        seen[root[i]] = offset[-1] + r.n_per_stream
+    reach = [offset[i] + r.n_per_stream for i, r in enumerate(reqs)]  # outputs per stream the oracle runs
+    xs = [i for i, r in enumerate(reqs) if r.variant == "xor" and reach[i] <= 1 << 20]
+    bs = [i for i, r in enumerate(reqs) if r.variant == "bbs" and reach[i] <= 1 << 17]
+    conts = [i for i in xs + bs if reqs[i].continues >= 0]
+    rng = np.random.default_rng(55)
+    sample = {max(xs + bs, key=lambda i: reqs[i].n_streams * reqs[i].n_per_stream)}
+    sample |= set(rng.choice(conts, size=4, replace=False).tolist())
+    sample |= set(rng.choice(xs, size=4, replace=False).tolist()) | set(rng.choice(bs, size=2, replace=False).tolist())
+    srv = ci.Server(64 << 30)
+    results, _ = srv.drive(reqs, hold=[i in sample for i in range(len(reqs))])
+    assert all(results[i].status == 0 for i in range(len(reqs)))
+    assert any(reqs[i].continues >= 0 for i in sample)
+    for i in sorted(sample):
+        r, base = reqs[i], reqs[root[i]]
+        out = srv.output(results[i])
+        groups = (r.n_streams + 31) // 32
+        for g in sorted({0, groups - 1}):
+            ref = oracle_gen(base.variant, "xor128", 32, base.seed, 0, r.n_streams, lane0=32 * g, n_lanes=32)
+            want = ref.streams(reach[i])[:, offset[i]:]
+            assert np.array_equal(u32(out[32 * g: 32 * g + want.shape[0]]), want), (i, g)
+    srv.close()
