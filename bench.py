@@ -685,39 +685,48 @@ def bench_batched_sample(torch, ci):
     """A smaller form of --suite batched inside the default run: 2000 requests
     (seed 4; streams log-uniform [1, 2^16], lengths log-uniform [2^6, 2^16],
     80 % xor128 / 20 % BBS) into the digest sink, as ONE persistent batched
-    launch and as one launch per request; digests compared."""
+    launch, as one plain launch per request (unsplit), and as one public
+    single call per request (ci_generate_digest, which runs narrow states as
+    time segments on its own); digests compared."""
     from paper_1112_5239_gb300.workloads import batched_requests
 
     reqs = batched_requests(seed=4, count=2000, max_len_log2=16)
     specs = [dict(n_streams=r.n_streams, variant=r.variant, seed=r.seed) for r in reqs]
-    A = ci.States.many(specs)
-    B = ci.States.many(specs)
-    dA = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
-    dB = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+    A, B, C = ci.States.many(specs), ci.States.many(specs), ci.States.many(specs)
+    dA, dB, dC = ([torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs] for _ in range(3))
     b = ci.Batch(len(reqs))
     w = ci.States(64, seed=99)
     wd = torch.zeros(64, dtype=torch.int64, device="cuda")
     b.run([(w, 64, "digest", wd)])  # loads the kernel, instantiates the graph
     torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     e[0].record()
     b.run([(st, r.n_per_stream, "digest", d) for st, r, d in zip(A, reqs, dA)])
     e[1].record()
     torch.cuda.synchronize()
     e[2].record()
     for st, r, d in zip(B, reqs, dB):
-        st.generate_digest(r.n_per_stream, digest=d)
+        st.generate_split(r.n_per_stream, sink="digest", out=d, segments=1)
     e[3].record()
     torch.cuda.synchronize()
-    sec_b, sec_p = e[0].elapsed_time(e[1]) / 1e3, e[2].elapsed_time(e[3]) / 1e3
+    e[4].record()
+    for st, r, d in zip(C, reqs, dC):
+        st.generate_digest(r.n_per_stream, digest=d)
+    e[5].record()
+    torch.cuda.synchronize()
+    sec_b, sec_p, sec_a = (e[i].elapsed_time(e[i + 1]) / 1e3 for i in (0, 2, 4))
     n_out = sum(r.n_streams * r.n_per_stream for r in reqs)
-    identical = all(torch.equal(x, y) for x, y in zip(dA, dB))
+    identical = all(torch.equal(x, y) and torch.equal(x, z) for x, y, z in zip(dA, dB, dC))
     b.close()
     return {"workload": "2000 requests, seed 4, streams log-uniform [1, 2^16], lengths log-uniform [2^6, 2^16], "
                         "80%% xor128 / 20%% BBS, digest sink (%d outputs)" % n_out,
             "batched": {"value": n_out / sec_b, "seconds": sec_b, "launches": 1},
-            "per_request": {"value": n_out / sec_p, "seconds": sec_p, "launches": len(reqs)},
-            "batched_over_per_request": sec_p / sec_b, "identical_digests": bool(identical), "unit": "uint32/s"}
+            "per_request": {"value": n_out / sec_p, "seconds": sec_p, "launches": len(reqs),
+                            "form": "one unsplit launch per request"},
+            "per_request_auto_split": {"value": n_out / sec_a, "seconds": sec_a,
+                                       "form": "ci_generate_digest per request (narrow states as time segments)"},
+            "batched_over_per_request": sec_p / sec_b, "batched_over_per_request_auto_split": sec_a / sec_b,
+            "identical_digests": bool(identical), "unit": "uint32/s"}
 
 
 def bench_serving_sample(ci):
@@ -858,9 +867,10 @@ def bench_batched(args):
     6e12 outputs (about 25 TB) cannot be held in HBM, so both forms consume
     them in-kernel through the per-stream digest sink: (a) ONE launch of the
     persistent batched kernel over all requests (ci_batch_run, CUDA graph),
-    (b) one ci_generate_digest launch per request, back to back on one
-    stream.  Every digest of (a) must equal (b); a sample is checked against
-    the oracle."""
+    (b) one plain (unsplit) launch per request, back to back on one stream,
+    (c) one public ci_generate_digest call per request, which runs narrow
+    states as time segments on its own.  Every digest of (a) must equal (b)
+    and (c); a sample is checked against the oracle."""
     import numpy as np
     import torch
 
@@ -880,8 +890,8 @@ def bench_batched(args):
     torch.cuda.synchronize()
     t_init = time.perf_counter() - t_init
     B = [ci.States(r.n_streams, variant=r.variant, seed=r.seed) for r in reqs]  # one seeding launch each
-    dA = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
-    dB = [torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs]
+    C = ci.States.many(specs)
+    dA, dB, dC = ([torch.zeros(r.n_streams, dtype=torch.int64, device="cuda") for r in reqs] for _ in range(3))
     torch.cuda.synchronize()
     # warm-up on a separate tiny batch (loads the kernels, instantiates the graph)
     b = ci.Batch(len(reqs))
@@ -905,14 +915,21 @@ def bench_batched(args):
     e1b = torch.cuda.Event(enable_timing=True)
     e1b.record(stream)
     for st, r, d in zip(B, reqs, dB):
-        st.generate_digest(r.n_per_stream, digest=d)
+        st.generate_split(r.n_per_stream, sink="digest", out=d, segments=1)
     e2.record(stream)
     torch.cuda.synchronize()
     t_host = time.perf_counter() - t_host
     clk_single = clocks.stop()
+    e3, e4 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e3.record(stream)
+    for st, r, d in zip(C, reqs, dC):
+        st.generate_digest(r.n_per_stream, digest=d)
+    e4.record(stream)
+    torch.cuda.synchronize()
     sec_batched = e0.elapsed_time(e1) / 1e3
     sec_single = e1b.elapsed_time(e2) / 1e3
-    identical = all(torch.equal(x, y) for x, y in zip(dA, dB))
+    sec_auto = e3.elapsed_time(e4) / 1e3
+    identical = all(torch.equal(x, y) and torch.equal(x, z) for x, y, z in zip(dA, dB, dC))
     n_out = sum(r.n_streams * r.n_per_stream for r in reqs)
     n_bbs = sum(r.n_streams * r.n_per_stream for r in reqs if r.variant == "bbs")
 
@@ -942,8 +959,11 @@ def bench_batched(args):
                    "outputs": n_out, "bbs_outputs": n_bbs, "work_units": sum(-(-r.n_streams // 32) for r in reqs)},
         "batched": {"value": n_out / sec_batched, "seconds": sec_batched, "launches": 1, "clocks": clk_batched},
         "per_request": {"value": n_out / sec_single, "seconds": sec_single, "launches": len(reqs),
-                        "host_seconds": t_host, "clocks": clk_single},
+                        "form": "one unsplit launch per request", "host_seconds": t_host, "clocks": clk_single},
+        "per_request_auto_split": {"value": n_out / sec_auto, "seconds": sec_auto,
+                                   "form": "ci_generate_digest per request (narrow states as time segments)"},
         "batched_over_per_request": sec_single / sec_batched,
+        "batched_over_per_request_auto_split": sec_auto / sec_batched,
         "identical_digests": bool(identical),
         "oracle_sample": {"requests": sample, "equal": bool(oracle_ok)},
         "init_seconds_batched_seeding": t_init,
@@ -984,7 +1004,7 @@ def _serving_run(ci, reqs, arena_gib, hold=None, **cfg):
                           "arena_peak_gib": stats["arena_peak"] / 2**30, "split_jobs": stats["split_jobs"]}
 
 
-def _plain_per_request(torch, ci, reqs):
+def _plain_per_request(torch, ci, reqs, auto_split=False):
     handles = {}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -994,7 +1014,11 @@ def _plain_per_request(torch, ci, reqs):
             handles[i] = st
         else:
             st = handles[r.continues]
-        st.generate(r.n_per_stream)  # output tensor from torch's caching allocator, dropped after use
+        # output tensor from torch's caching allocator, dropped after use
+        if auto_split:
+            st.generate(r.n_per_stream)  # public single call: narrow states run as time segments
+        else:
+            st.generate_split(r.n_per_stream, segments=1)  # one unsplit launch
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     n_out = sum(r.n_streams * r.n_per_stream for r in reqs)
@@ -1064,6 +1088,7 @@ def bench_serving(args):
     # streams, state in torch memory) and ONE generation launch, asynchronously
     # on one stream; timed from the first issue to the end of the last launch
     plain = _plain_per_request(torch, ci, base)
+    plain_auto = _plain_per_request(torch, ci, base, auto_split=True)
     srv, _, single = _serving_run(ci, at_zero(), 64, max_slots=1, max_inflight=2, slice_xor=1 << 40,
                                   slice_bbs=1 << 40)
     srv.close()
@@ -1096,8 +1121,9 @@ def bench_serving(args):
                                "S = 2^clamp(floor(log2 n) - 10, 0, 16), 30%% continuations, 80%% xor128 / 20%% BBS, "
                                "64 GiB arena" % n},
         "saturation": sat, "sweep": sweep, "sweep_without_split_jobs": no_split, "plain_per_request": plain,
-        "single_slot_server": single,
+        "plain_per_request_auto_split": plain_auto, "single_slot_server": single,
         "served_over_plain": sat["steady_value"] / plain["value"],
+        "served_over_plain_auto_split": sat["steady_value"] / plain_auto["value"],
         "oracle_sample": {"requests": sorted(sample), "continuations": len(set(conts[:12])), "equal": bool(equal)},
         "clocks": clk, "autotuned_batch": tuned["batch"],
     }

@@ -516,6 +516,8 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * digests SET for CI_SINK_DIGEST; out_capacity ignored).  n_segments == 0
  * picks the count from the GPU size; the count is capped at 8192 and
  * segments hold a multiple of 32 iterations, so small calls run unsplit.
+ * n_segments == 1 runs the call unsplit, as ONE launch of the single-call
+ * kernel (without the automatic split of the single-call entry points).
  * Allocates a stream-ordered workspace of about n_segments state copies.
  * CI_VAR_BBS16, whose outputs depend on call boundaries, is split within the
  * one call: every segment uses the arrays the call chose at its start, each of

@@ -146,7 +146,8 @@ class States:
         """The same results as ``generate`` / ``generate_fused_qc`` /
         ``generate_digest`` (sink "written" / "qc" / "digest"), computed as
         up to ``segments`` concurrent time segments (0: chosen from the GPU
-        size) by jump-ahead: for few streams with long lengths."""
+        size) by jump-ahead: for few streams with long lengths.  segments=1
+        runs one unsplit launch of the single-call kernel."""
         n = int(n_per_stream)
         code = SINKS[sink] if isinstance(sink, str) else int(sink)
         if out is None:

@@ -843,12 +843,12 @@ extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, vo
         return fail(CI_E_INVAL, "out_capacity is smaller than n_streams * n");
     if (sink == CI_SINK_QC && (n & 1ull)) return fail(CI_E_INVAL, "quarter-circle sink needs an even length");
     const uint64_t K = split_segments(*h, n, n_segments);
-    if (K <= 1) {  // unsplit: the tuned single-call kernels
-        if (sink == CI_SINK_QC) return ci_generate_fused_qc(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
-        if (sink == CI_SINK_DIGEST) return ci_generate_digest(h, n, static_cast<uint64_t *>(out_dev), cuda_stream);
-        return h->variant != CI_VAR_XOR
-                   ? ci_generate_bbs(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream)
-                   : ci_generate(h, n, static_cast<uint32_t *>(out_dev), out_capacity, cuda_stream);
+    if (K <= 1) {  // unsplit: one launch of the tuned single-call kernel
+        const cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+        const cudaError_t e = sink == CI_SINK_QC       ? launch_fused_qc(*h, n, static_cast<uint64_t *>(out_dev), cs)
+                              : sink == CI_SINK_DIGEST ? launch_digest(*h, n, static_cast<uint64_t *>(out_dev), cs)
+                                                       : launch_generate(*h, n, static_cast<uint32_t *>(out_dev), cs);
+        return e == cudaSuccess ? CI_OK : cuda_fail(e, "unsplit generation kernel launch");
     }
     if (sink == CI_SINK_WRITTEN)
         return split_launch(*h, n, sink, static_cast<uint32_t *>(out_dev), n, 0, nullptr, K,

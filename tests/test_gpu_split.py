@@ -121,3 +121,16 @@ def test_single_calls_split_narrow_states_on_their_own():
     o = orc.streams(n)
     hits = (((o[:, 0::2] >> 8).astype(np.uint64) ** 2 + (o[:, 1::2] >> 8).astype(np.uint64) ** 2) < (1 << 48)).sum(axis=1)
     assert np.array_equal(c, hits.astype(np.uint64))
+
+
+def test_one_segment_is_the_unsplit_call():
+    """segments=1 runs one unsplit launch: on narrow states (which the single
+    calls would split) every sink still equals the oracle, and the state
+    continues exactly."""
+    torch, ci = cuda_or_skip()
+    for variant, n in (("xor", 1 << 13), ("bbs", 1 << 11)):
+        st = _states(ci, variant, "xor128", 32, 93, 32)
+        orc = oracle_gen(variant, "xor128", 32, 93, 100, 32)
+        assert np.array_equal(u32(st.generate_split(n, segments=1)), orc.streams(n))
+        d = st.generate_split(n, sink="digest", segments=1).cpu().numpy().view(np.uint64)
+        assert np.array_equal(d, digest_rows(orc.streams(n)))
