@@ -217,9 +217,10 @@ struct SrcBbs {
 // Algorithm 5 as printed: eight BBS generators per lane with moduli below
 // 2^16, so x^2 fits 32 bits.  x^2 mod M by Barrett reduction with
 // mu = floor(2^32 / M): q = mulhi(x^2, mu) is floor(x^2 / M) or one less, so a
-// single conditional subtraction gives the canonical residue.  The arrays are
-// read from BBS1 and BBS2 when the call starts; at the end of the call
-// generator k (state and modulus) is stored in place k + 1.
+// single conditional subtraction gives the canonical residue, taken as the
+// unsigned minimum of r and r - M (r - M wraps above r when r < M).  The
+// arrays are read from BBS1 and BBS2 when the call starts; at the end of the
+// call generator k (state and modulus) is stored in place k + 1.
 struct SrcBbs16 {
     static constexpr bool kHeavy = true;
     uint32_t y[8], M[8], mu[8];
@@ -248,20 +249,23 @@ struct SrcBbs16 {
     template <int K>
     __device__ __forceinline__ uint32_t bbs() {  // BBS(K+1)
         const uint32_t a = y[K] * y[K];
-        uint32_t r = a - __umulhi(a, mu[K]) * M[K];
-        if (r >= M[K]) r -= M[K];
-        y[K] = r;
-        return r;
+        const uint32_t r = a - __umulhi(a, mu[K]) * M[K];
+        y[K] = min(r, r - M[K]);
+        return y[K];
     }
     __device__ __forceinline__ uint32_t next() {
-        uint32_t t = (bbs<0>() & 15u) << 28;
-        t |= (bbs<1>() & 15u) << 24;
-        t |= (bbs<2>() & 15u) << 20;
-        t |= (bbs<3>() & 15u) << 16;
-        t |= (bbs<4>() & 15u) << 12;
-        t |= (bbs<5>() & 15u) << 8;
-        t |= (bbs<6>() & 15u) << 4;
-        t |= bbs<7>() & 15u;
+        // Four low bits of BBS1 .. BBS8 into bits 31-28 .. 3-0: each funnel
+        // shift moves t down four bits and brings the next generator's low
+        // nibble in at the top, so BBS8 enters first and BBS1 last (the eight
+        // generators are independent, so the order of their steps is free).
+        uint32_t t = bbs<7>() << 28;
+        t = __funnelshift_r(t, bbs<6>(), 4);
+        t = __funnelshift_r(t, bbs<5>(), 4);
+        t = __funnelshift_r(t, bbs<4>(), 4);
+        t = __funnelshift_r(t, bbs<3>(), 4);
+        t = __funnelshift_r(t, bbs<2>(), 4);
+        t = __funnelshift_r(t, bbs<1>(), 4);
+        t = __funnelshift_r(t, bbs<0>(), 4);
         uint32_t shift = bbs<2>() & 3u;
         t <<= shift;
         t |= bbs<0>() & ((1u << shift) - 1u);  // array_shift = {0, 1, 3, 7}
