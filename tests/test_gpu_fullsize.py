@@ -168,3 +168,23 @@ def test_serving_mix_20000_requests_full_size_sampled(env):
             want = ref.streams(reach[i])[:, offset[i]:]
             assert np.array_equal(u32(out[32 * g: 32 * g + want.shape[0]]), want), (i, g)
     srv.close()
+
+
+def test_bbs16_2e16x16384_sampled_groups(env):
+    """Algorithm 5 as printed at the benchmark's size (2^16 streams x 16384,
+    seed 3, written, 4 GiB), then a second call (arrays chosen again,
+    generators rotated): sampled groups, first and last included, equal the
+    oracle call by call."""
+    torch, ci = env
+    S, L = 1 << 16, 1 << 14
+    st = ci.States(S, variant="bbs16", comb_size=32, seed=3)
+    out = st.generate(L)
+    torch.cuda.synchronize()
+    groups = [0, 1, 777, S // 32 - 1]
+    refs = {g: oracle_gen("bbs16", "xor128", 32, 3, 0, S, lane0=32 * g, n_lanes=32) for g in groups}
+    for g in groups:
+        assert np.array_equal(u32(out[32 * g: 32 * g + 32]), refs[g].generate(L)), g
+    del out
+    out2 = u32(st.generate(96))
+    for g in groups:
+        assert np.array_equal(out2[32 * g: 32 * g + 32], refs[g].generate(96)), g
