@@ -56,7 +56,8 @@ def parse_args():
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
-    ap.add_argument("--profile", choices=["written", "fused", "bbs", "bbs16", "batched", "bg", "naive"], default=None,
+    ap.add_argument("--profile", choices=["written", "fused", "bbs", "bbs_split", "bbs16", "batched", "bg", "naive"],
+                    default=None,
                     help="small case for ncu: autotune, 2 warm-up launches, then 1 launch of one kernel inside "
                          "the NVTX range 'profile'; no timing")
     return ap.parse_args()
@@ -64,7 +65,8 @@ def parse_args():
 
 def run_profile_case(kind: str) -> None:
     """Small case for profiler captures: 2^19 streams x 256 written (512 MiB,
-    larger than L2), 2^19 x 4096 fused, 2^16 x 1024 BBS written (256 MiB), or
+    larger than L2), 2^19 x 4096 fused, 2^16 x 1024 BBS written (256 MiB; unsplit),
+    2^16 x 4096 BBS written (1 GiB; run as time segments), or
     one batched launch of 300 uneven requests; two warm-up launches and one
     more of the same kernel inside the NVTX range "profile"."""
     import torch
@@ -88,6 +90,10 @@ def run_profile_case(kind: str) -> None:
         st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
         run = lambda: st.generate(1024, out=out)  # noqa: E731
+    elif kind == "bbs_split":  # 2^16 BBS streams x 4096 written (1 GiB): the call runs as time segments
+        st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
+        out = torch.empty((S_BBS, 4096), dtype=torch.int32, device="cuda")
+        run = lambda: st.generate(4096, out=out)  # noqa: E731
     elif kind == "bbs16":  # Algorithm 5 as printed, 2^16 streams x 1024 written (256 MiB)
         st = ci.States(S_BBS, variant="bbs16", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
