@@ -9,12 +9,15 @@
 // (square roots by the exponent ((p + 1) / 4)^L, joined by Garner's CRT) and
 // regenerates the same keystream.
 //
-// One lane owns one message; a warp owns 32 consecutive messages and moves
-// their chunks (one byte each, message-major) through a warp-private 32 x 32
-// byte tile in shared memory, so global loads and stores are 32-byte rows
-// while each lane walks its own row.  The squarings use the Barrett
-// reduction of the BBS strategy source (modulus odd, below 2^62), which keeps
-// x_i canonical so its low bits are read directly.
+// One lane owns one message; a warp owns 32 consecutive messages.  When the
+// chunk count is a multiple of 32 and both buffers are 16-byte aligned, each
+// lane moves its own 32 chunks per step with two 16-byte loads and stores.
+// Otherwise the warp moves its messages' chunks (one byte each,
+// message-major) through a warp-private 32 x 32 byte tile in shared memory,
+// so global loads and stores are 32-byte rows while each lane walks its own
+// row.  The squarings use the Barrett reduction of the BBS strategy source
+// (modulus odd, below 2^62), which keeps x_i canonical so its low bits are
+// read directly.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,11 +58,18 @@ struct BgLane {
         x = B.sqr(x);
         return (v ^ key) & 0xFFu;
     }
+    // Four chunks, one per byte of w: the keystream bytes are gathered into
+    // one word and XORed in once (key < 2^8: S^0 is a byte, the b_i have at
+    // most 5 bits).
     __device__ __forceinline__ uint32_t word(uint32_t w) {
-        uint32_t o = 0;
+        uint32_t ks = 0;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) o |= chunk((w >> (8 * b)) & 0xFFu) << (8 * b);
-        return o;
+        for (int b = 0; b < 4; ++b) {
+            key ^= (uint32_t)x & mask;
+            x = B.sqr(x);
+            ks |= key << (8 * b);
+        }
+        return w ^ ks;
     }
 };
 
@@ -98,7 +108,7 @@ __device__ __forceinline__ bool bg_setup_decrypt(uint64_t p, uint64_t q, uint64_
     return ok;
 }
 
-template <bool kDecrypt>
+template <bool kDecrypt, bool kVec>
 __global__ void __launch_bounds__(kBgWarps * 32, CI_BG_MIN_BLOCKS)
     k_bg(uint64_t n_msgs, uint64_t L, const uint64_t *__restrict__ key_a, const uint64_t *__restrict__ key_b,
          const uint8_t *__restrict__ S0, const uint64_t *__restrict__ y_in, const uint8_t *in, uint8_t *out,
@@ -124,37 +134,58 @@ __global__ void __launch_bounds__(kBgWarps * 32, CI_BG_MIN_BLOCKS)
             if (!ok && n_rejected) atomicAdd(n_rejected, 1u);
         }
         const uint32_t keep = ok ? 0xFFFFFFFFu : 0u;  // a rejected key's row is written as zeros
-        for (uint64_t k0 = 0; k0 < L; k0 += kBgTile) {
-            const uint32_t width = L - k0 < (uint64_t)kBgTile ? (uint32_t)(L - k0) : (uint32_t)kBgTile;
-            __syncwarp();
-#pragma unroll 8
-            for (uint32_t r = 0; r < rows; ++r)
-                if (lane < width) tile[r * kBgRowPad + lane] = in[(m0 + r) * L + k0 + lane];
-            __syncwarp();
+        if constexpr (kVec) {  // L a multiple of 32, rows 16-byte aligned
             if (live) {
-                uint32_t *w = reinterpret_cast<uint32_t *>(row);
-                if (width == kBgTile) {
-#pragma unroll
-                    for (int j = 0; j < kBgTile / 4; ++j) w[j] = s.word(w[j]) & keep;
-                } else {
-                    for (uint32_t j = 0; j < width; ++j) row[j] = (uint8_t)(s.chunk(row[j]) & keep);
+                const uint4 *src = reinterpret_cast<const uint4 *>(in + msg * L);
+                uint4 *dst = reinterpret_cast<uint4 *>(out + msg * L);
+                const uint64_t steps = L / kBgTile;
+                for (uint64_t t = 0; t < steps; ++t) {  // each step reads its 32 bytes before writing them
+                    uint4 a = src[2 * t], b = src[2 * t + 1];
+                    a.x = s.word(a.x) & keep;
+                    a.y = s.word(a.y) & keep;
+                    a.z = s.word(a.z) & keep;
+                    a.w = s.word(a.w) & keep;
+                    b.x = s.word(b.x) & keep;
+                    b.y = s.word(b.y) & keep;
+                    b.z = s.word(b.z) & keep;
+                    b.w = s.word(b.w) & keep;
+                    dst[2 * t] = a;
+                    dst[2 * t + 1] = b;
                 }
             }
-            __syncwarp();
+        } else {
+            for (uint64_t k0 = 0; k0 < L; k0 += kBgTile) {
+                const uint32_t width = L - k0 < (uint64_t)kBgTile ? (uint32_t)(L - k0) : (uint32_t)kBgTile;
+                __syncwarp();
 #pragma unroll 8
-            for (uint32_t r = 0; r < rows; ++r)
-                if (lane < width) out[(m0 + r) * L + k0 + lane] = tile[r * kBgRowPad + lane];
+                for (uint32_t r = 0; r < rows; ++r)
+                    if (lane < width) tile[r * kBgRowPad + lane] = in[(m0 + r) * L + k0 + lane];
+                __syncwarp();
+                if (live) {
+                    uint32_t *w = reinterpret_cast<uint32_t *>(row);
+                    if (width == kBgTile) {
+#pragma unroll
+                        for (int j = 0; j < kBgTile / 4; ++j) w[j] = s.word(w[j]) & keep;
+                    } else {
+                        for (uint32_t j = 0; j < width; ++j) row[j] = (uint8_t)(s.chunk(row[j]) & keep);
+                    }
+                }
+                __syncwarp();
+#pragma unroll 8
+                for (uint32_t r = 0; r < rows; ++r)
+                    if (lane < width) out[(m0 + r) * L + k0 + lane] = tile[r * kBgRowPad + lane];
+            }
         }
         if (!kDecrypt && live) y_out[msg] = ok ? s.x : 0ull;
     }
 }
 
-template <bool kDecrypt>
+template <bool kDecrypt, bool kVec>
 int bg_grid(uint64_t n_msgs) {
     static int per_sm = 0;
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bg<kDecrypt>, kBgWarps * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bg<kDecrypt, kVec>, kBgWarps * 32, 0);
         if (per_sm <= 0) per_sm = 1;
     });
     const uint64_t blocks = (n_msgs + 32 * kBgWarps - 1) / (32 * kBgWarps);
@@ -167,6 +198,25 @@ ci_status bg_check(uint64_t n_msgs, uint64_t n_chunks, const void *a, const void
     if (n_chunks && (!in || !out)) return fail(CI_E_INVAL, "bg: message and ciphertext must be non-null");
     if (n_chunks > ~0ull / n_msgs) return fail(CI_E_INVAL, "bg: n_msgs * n_chunks overflows");
     return CI_OK;
+}
+
+// The per-lane 16-byte path: whole 32-chunk steps and 16-byte aligned rows.
+bool bg_vec(uint64_t n_chunks, const void *in, const void *out) {
+    return n_chunks % kBgTile == 0 && (reinterpret_cast<uintptr_t>(in) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+}
+
+template <bool kDecrypt>
+cudaError_t bg_launch(uint64_t n_msgs, uint64_t L, const uint64_t *a, const uint64_t *b, const uint8_t *S0,
+                      const uint64_t *y_in, const uint8_t *in, uint8_t *out, uint64_t *y_out, uint32_t *n_rejected,
+                      cudaStream_t stream) {
+    if (bg_vec(L, in, out))
+        k_bg<kDecrypt, true><<<bg_grid<kDecrypt, true>(n_msgs), kBgWarps * 32, 0, stream>>>(
+            n_msgs, L, a, b, S0, y_in, in, out, y_out, n_rejected);
+    else
+        k_bg<kDecrypt, false><<<bg_grid<kDecrypt, false>(n_msgs), kBgWarps * 32, 0, stream>>>(
+            n_msgs, L, a, b, S0, y_in, in, out, y_out, n_rejected);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -182,9 +232,8 @@ ci_status ci_bg_encrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *N_de
     if (n_msgs == 0) return CI_OK;
     const ci_status st = bg_check(n_msgs, n_chunks, N_dev, r_dev, S0_dev, y_dev, msg_dev, cipher_dev);
     if (st != CI_OK) return st;
-    k_bg<false><<<bg_grid<false>(n_msgs), kBgWarps * 32, 0, (cudaStream_t)cuda_stream>>>(
-        n_msgs, n_chunks, N_dev, r_dev, S0_dev, nullptr, msg_dev, cipher_dev, y_dev, n_rejected_dev);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = bg_launch<false>(n_msgs, n_chunks, N_dev, r_dev, S0_dev, nullptr, msg_dev, cipher_dev, y_dev,
+                                           n_rejected_dev, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? CI_OK : cuda_fail(e, "ci_bg_encrypt launch");
 }
 
@@ -196,9 +245,8 @@ ci_status ci_bg_decrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *p_de
     if (n_msgs == 0 || n_chunks == 0) return CI_OK;
     const ci_status st = bg_check(n_msgs, n_chunks, p_dev, q_dev, S0_dev, y_dev, cipher_dev, msg_dev);
     if (st != CI_OK) return st;
-    k_bg<true><<<bg_grid<true>(n_msgs), kBgWarps * 32, 0, (cudaStream_t)cuda_stream>>>(
-        n_msgs, n_chunks, p_dev, q_dev, S0_dev, y_dev, cipher_dev, msg_dev, nullptr, n_rejected_dev);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = bg_launch<true>(n_msgs, n_chunks, p_dev, q_dev, S0_dev, y_dev, cipher_dev, msg_dev, nullptr,
+                                          n_rejected_dev, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? CI_OK : cuda_fail(e, "ci_bg_decrypt launch");
 }
 

@@ -163,3 +163,36 @@ def test_full_size_sampled_and_round_trip():
     md = ci.bg_decrypt(_dev(torch, b["p"], torch.int64), _dev(torch, b["q"], torch.int64),
                        _dev(torch, b["S0"], torch.uint8), y, c)
     assert torch.equal(md, msg)
+
+
+@pytest.mark.parametrize("L", [96, 160])
+def test_aligned_and_unaligned_rows(L):
+    """Lengths that are a multiple of 32 chunks take the per-lane 16-byte path
+    when both buffers are 16-byte aligned and the staged path when they are
+    not (views at a one-byte offset): separate, in-place and unaligned
+    encryption, and decryption of each, equal the oracle."""
+    torch, ci = cuda_or_skip()
+    n = 70
+    b, m = _batch(51 + L, n, L, n_keys=8)
+    oc, oy = _oracle_rows(b, m, range(n))
+    N, S0, r = _dev(torch, b["N"], torch.int64), _dev(torch, b["S0"], torch.uint8), _dev(torch, b["r"], torch.int64)
+    m_al = _dev(torch, m, torch.uint8)
+    c_al, y_al = ci.bg_encrypt(N, S0, r, m_al)
+    m_ip = _dev(torch, m, torch.uint8)
+    c_ip, y_ip = ci.bg_encrypt(N, S0, r, m_ip, out=m_ip)
+    buf_in = torch.zeros(n * L + 1, dtype=torch.uint8, device="cuda")
+    buf_out = torch.zeros(n * L + 1, dtype=torch.uint8, device="cuda")
+    m_un, c_un = buf_in[1:].view(n, L), buf_out[1:].view(n, L)
+    m_un.copy_(m_al)
+    _, y_un = ci.bg_encrypt(N, S0, r, m_un, out=c_un)
+    torch.cuda.synchronize()
+    for c, y in ((c_al, y_al), (c_ip, y_ip), (c_un, y_un)):
+        assert np.array_equal(c.cpu().numpy(), oc)
+        assert np.array_equal(y.cpu().numpy().view(np.uint64), oy)
+    md, rej = _decrypt(torch, ci, b, oy, oc)
+    assert rej == 0 and np.array_equal(md, m)
+    buf_dec = torch.zeros(n * L + 1, dtype=torch.uint8, device="cuda")
+    d_un = ci.bg_decrypt(_dev(torch, b["p"], torch.int64), _dev(torch, b["q"], torch.int64), S0, y_un, c_un,
+                         out=buf_dec[1:].view(n, L))
+    torch.cuda.synchronize()
+    assert np.array_equal(d_un.cpu().numpy(), m)
