@@ -550,7 +550,9 @@ ci_status ci_generate_split(ci_states states, uint64_t n_per_stream, int32_t sin
  * decryptable (not checkable without the factors).  n_rejected_dev (uint32,
  * may be NULL) is INCREMENTED by the number of rejected messages.
  * Asynchronous on cuda_stream.  n_msgs == 0 is a no-op; n_chunks == 0 still
- * writes y = r^2 mod N.
+ * writes y = r^2 mod N.  Fastest when n_chunks is a multiple of 32 and both
+ * chunk buffers are 16-byte aligned (each thread then moves its message's
+ * chunks 32 at a time); any other size or alignment gives the same result.
  * Errors: CI_E_INVAL (a null array, n_msgs * n_chunks overflowing), CI_E_CUDA. */
 ci_status ci_bg_encrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *N_dev, const uint8_t *S0_dev,
                         const uint64_t *r_dev, const uint8_t *msg_dev, uint8_t *cipher_dev, uint64_t *y_dev,
