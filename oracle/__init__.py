@@ -30,6 +30,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ci_oracle.c")
 _LIB = os.path.join(_HERE, "libci_oracle.so")
+# The planted-mistake tests point this at a prebuilt copy of the oracle with
+# one slip planted in it (tests/test_oracle_planted.py); nothing else sets it.
+_LIB_OVERRIDE = os.environ.get("CI_ORACLE_LIB")
 
 VAR_XOR, VAR_BBS, VAR_BBS16 = 0, 1, 2
 XL_XOR128, XL_XORSHIFT32, XL_XOR64 = 0, 1, 2
@@ -60,6 +63,8 @@ NAIVE_DTYPE = np.dtype([("xs", "<u8", (5,)), ("xo", "<u8", (4,)), ("xw", "<u8", 
 
 def build(force: bool = False) -> str:
     """Compile ci_oracle.c into libci_oracle.so with the host C compiler."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
         cc = os.environ.get("CC", "gcc")
@@ -75,7 +80,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
+        L = ctypes.CDLL(_LIB_OVERRIDE or _LIB)
         u32, u64, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
         vp = ctypes.c_void_p
         sig = {

@@ -100,6 +100,15 @@ def test_partner_indexing_impulse_bbs(orc):
     exp = [(1 << ((j + s1) % 4)) ^ (1 << ((j + s2) % 4)) for j, s1, s2 in
            zip(range(4), [0, 1, 2, 3], [1, 2, 3, 0])]
     assert out[:, 0].tolist() == exp
+    # arrays 0-7 map offset j to (j + 1) % 4, arrays 8-15 to (j + 2) % 4: with
+    # sel1 = sel2 = 0 the second partner comes from array 8, not array 0
+    # (array 0 twice would cancel): lane j gets bits (j + 1) % 4 and (j + 2) % 4
+    comb = np.array([np.roll(np.arange(4), -1 if a < 8 else -2) for a in range(16)], dtype=np.uint8)
+    lanes = _zero_xorlike_lanes(orc, 4, BBS)
+    lanes["sel1"] = 0
+    lanes["sel2"] = 0
+    out, _ = orc.run(BBS, 0, 4, comb.reshape(-1), lanes, 1)
+    assert out[:, 0].tolist() == [6, 12, 9, 3]
 
 
 def _plain_xorlike_stream(orc, xl, w0, L):

@@ -1,0 +1,112 @@
+"""Planted mistakes: each plausible slip in the oracle's arithmetic (a dropped
+term, a wrong shift amount or direction, a transposed operand or index, a
+wrong operator, a missing step) is planted in a copy of oracle/ci_oracle.c,
+compiled on the CPU, and the pins named beside it must fail against that copy
+(the unmodified oracle passes the same pins in the rest of the suite).  This
+shows that the pins tell the oracle from a near miss of it, not only that the
+oracle agrees with itself."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ci_oracle.c")
+
+# (id, text in ci_oracle.c, planted text, pins: test node ids under tests/)
+MUTANTS = [
+    # Eq. (Oplus)
+    ("ci_step_or_for_xor", "return x ^ strategy;", "return x | strategy;",
+     ["test_oracle_ci.py::test_table1_worked_example"]),
+    # Algorithm 2 (XORshift)
+    ("xorshift32_shift_amount", "z = z ^ (z << 13);", "z = z ^ (z << 12);",
+     ["test_oracle_xorlike.py::test_xorshift32_full_period_gf2"]),
+    ("xorshift32_shift_direction", "z = z ^ (z >> 17);", "z = z ^ (z << 17);",
+     ["test_oracle_xorlike.py::test_xorshift32_full_period_gf2"]),
+    # xor128 (Sec. 6.2) and xor64 (Sec. 7)
+    ("xor128_shift_amount", "uint32_t tmp = a ^ (a << 11);", "uint32_t tmp = a ^ (a << 12);",
+     ["test_oracle_xorlike.py::test_xor128_full_period_gf2"]),
+    ("xor128_dropped_term", "s[3] = s[3] ^ (s[3] >> 19) ^ (tmp ^ (tmp >> 8));", "s[3] = s[3] ^ (tmp ^ (tmp >> 8));",
+     ["test_oracle_xorlike.py::test_xor128_full_period_gf2"]),
+    ("xor64_shift_amount", "x = x ^ (x >> 7);", "x = x ^ (x >> 8);",
+     ["test_oracle_xorlike.py::test_xor64_full_period_gf2"]),
+    # Algorithm 4: the mixing
+    ("mix_dropped_partner", "tnew[l] = xl[l] ^ tprev[part1[l]] ^ tprev[part2[l]];",
+     "tnew[l] = xl[l] ^ tprev[part1[l]];",
+     ["test_oracle_mixing.py::test_hand_worked_c2_synchronous", "test_oracle_mixing.py::test_hand_worked_c4"]),
+    ("mix_asynchronous_reading", "tnew[l] = xl[l] ^ tprev[part1[l]] ^ tprev[part2[l]];",
+     "tnew[l] = tprev[l] = xl[l] ^ tprev[part1[l]] ^ tprev[part2[l]];",
+     ["test_oracle_mixing.py::test_hand_worked_c2_synchronous", "test_oracle_mixing.py::test_hand_worked_c4"]),
+    ("mix_second_array_read_from_first", "p2[l] = base + c2[offset];", "p2[l] = base + c1[offset];",
+     ["test_oracle_mixing.py::test_partner_indexing_impulse_xor"]),
+    ("mix_group_base_dropped", "p1[l] = base + c1[offset];", "p1[l] = c1[offset];",
+     ["test_oracle_mixing.py::test_partner_indexing_impulse_xor"]),
+    # BBS and Algorithm 5
+    ("bbs_square_wrong_modulus", "return (uint64_t)(sq % (unsigned __int128)M);",
+     "return (uint64_t)(sq % (unsigned __int128)(M - 1));",
+     ["test_oracle_bbs.py::test_bbs_step_large_moduli"]),
+    ("bbs_chunk_one_bit_short", "t |= (uint32_t)(orc_bbs_next(s) & mask);",
+     "t |= (uint32_t)(orc_bbs_next(s) & (mask >> 1));",
+     ["test_oracle_bbs.py::test_assembly_w4_matches_algorithm5_text", "test_oracle_bbs.py::test_assembly_w5"]),
+    ("bbs_array_shift_entry", "static const uint32_t array_shift[4] = {0u, 1u, 3u, 7u};",
+     "static const uint32_t array_shift[4] = {0u, 1u, 3u, 3u};",
+     ["test_oracle_bbs.py::test_assembly_w4_matches_algorithm5_text", "test_oracle_bbs.py::test_assembly_w5"]),
+    ("bbs_second_array_precedence", "c2 = comb + (size_t)(8 + lanes[l].sel2) * C;",
+     "c2 = comb + (size_t)((8 + lanes[l].sel2) & 7u) * C;",
+     ["test_oracle_mixing.py::test_partner_indexing_impulse_bbs"]),
+    ("trial_division_misses_squares", "for (uint64_t d = 3; d * d <= n; d += 2)",
+     "for (uint64_t d = 3; d * d < n; d += 2)",
+     ["test_oracle_bbs.py::test_trial_division_matches_library"]),
+    # Algorithm 5 as printed
+    ("bbs16_second_array_precedence", "c2 = comb + (size_t)(8 + (lanes[l].y16[1] & 7u)) * C;",
+     "c2 = comb + (size_t)((8 + lanes[l].y16[1]) & 7u) * C;",
+     ["test_oracle_bbs16.py::test_recurrence_with_arrays_chosen_per_call"]),
+    ("bbs16_rotation_missing", "orc_bbs16_rotate(&lanes[l]);", ";",
+     ["test_oracle_bbs16.py::test_squaring_counts_and_rotation_after_a_call"]),
+    ("bbs16_nibble_three_bits", "t |= orc_bbs16_next(L, k) & 15u;", "t |= orc_bbs16_next(L, k) & 7u;",
+     ["test_oracle_bbs16.py::test_hand_worked_word_fixes_generator_order"]),
+    # the quarter-circle consumer and the seeding counter layout
+    ("qc_fixed_point_shift", "uint64_t a = held[l] >> 8, b = xs[l] >> 8;",
+     "uint64_t a = held[l] >> 7, b = xs[l] >> 8;",
+     ["test_oracle_seeding_stats.py::test_qc_counts_equal_real_number_test"]),
+    ("lane_counter_overlap", "return orc_draw(seed, (lane << 32) + k);", "return orc_draw(seed, (lane << 31) + k);",
+     ["test_oracle_seeding_stats.py::test_lane_counter_ranges"]),
+    # chaotic Blum-Goldwasser (Sec. 9.2)
+    ("bg_keystream_without_s0", "uint32_t k = S0;", "uint32_t k = 0;",
+     ["test_oracle_bg.py::test_keystream_is_prefix_xor_of_bbs_bits"]),
+    ("bg_crt_inverse_transposed", "orc_invmod(q % p, p)", "orc_invmod(p % q, q)",
+     ["test_oracle_bg.py::test_crt_recovers_x0"]),
+    ("bg_root_exponent_power_off_by_one", "orc_powmod((p + 1) / 4, L, p - 1)", "orc_powmod((p + 1) / 4, L + 1, p - 1)",
+     ["test_oracle_bg.py::test_crt_recovers_x0"]),
+    # Listing 1 / Algorithm 3
+    ("listing1_dropped_xor", "    x ^= (uint32_t)(t3 >> 32);\n", "",
+     ["test_oracle_naive.py::test_listing1_combination_hand_worked"]),
+    ("naive_xorshift_shift_amount", "T t = s[0] ^ (s[0] >> 7);", "T t = s[0] ^ (s[0] >> 6);",
+     ["test_oracle_naive.py::test_xorshift160_full_period"]),
+    ("naive_xorwow_shift_amount", "s[4] = (s[4] ^ (s[4] << 4)) ^ (t ^ (t << 1));",
+     "s[4] = (s[4] ^ (s[4] << 5)) ^ (t ^ (t << 1));",
+     ["test_oracle_naive.py::test_xorwow_linear_part_full_period"]),
+]
+
+
+def _cc():
+    return os.environ.get("CC") or shutil.which("gcc") or shutil.which("cc")
+
+
+@pytest.mark.skipif(_cc() is None, reason="no host C compiler")
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_its_pins(name, old, new, pins, tmp_path):
+    with open(SRC) as f:
+        src = f.read()
+    assert src.count(old) >= 1, "the text to mutate is not in the oracle: %r" % old
+    c_file, so_file = tmp_path / "planted.c", tmp_path / "libplanted.so"
+    c_file.write_text(src.replace(old, new, 1))
+    subprocess.check_call([_cc(), "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so_file), str(c_file)])
+    env = dict(os.environ, CI_ORACLE_LIB=str(so_file))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x"] + [os.path.join(ROOT, "tests", p) for p in pins],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    summary = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else r.stderr[-500:]
+    assert r.returncode == 1 and "failed" in summary, (
+        "planted mistake %s was not caught by %s: %s" % (name, pins, summary))
