@@ -56,6 +56,15 @@ MUTANTS = [
     ("bbs_second_array_precedence", "c2 = comb + (size_t)(8 + lanes[l].sel2) * C;",
      "c2 = comb + (size_t)((8 + lanes[l].sel2) & 7u) * C;",
      ["test_oracle_mixing.py::test_partner_indexing_impulse_bbs"]),
+    ("bbs_bits_per_step_rounded_up", "while ((lg >> w) > 1)", "while ((lg >> w) > 0)",
+     ["test_oracle_bbs.py::test_secure_bit_count"]),
+    ("bbs_prime_not_3_mod_4", "p = (uint32_t)((1ULL << 30) + (d >> 34)) | 3u;",
+     "p = (uint32_t)((1ULL << 30) + (d >> 34)) | 1u;",
+     ["test_oracle_bbs.py::test_seeded_lanes_have_blum_primes"]),
+    ("bbs_second_selector_bits", "L->sel2 = (uint32_t)((v >> 3) & 7);", "L->sel2 = (uint32_t)((v >> 4) & 7);",
+     ["test_oracle_bbs.py::test_seeded_lanes_have_blum_primes"]),
+    ("bbs16_prime_range", "p = (uint32_t)(128 + d % 128) | 3u;", "p = (uint32_t)(128 + d % 256) | 3u;",
+     ["test_oracle_bbs16.py::test_seeded_generators"]),
     ("trial_division_misses_squares", "for (uint64_t d = 3; d * d <= n; d += 2)",
      "for (uint64_t d = 3; d * d < n; d += 2)",
      ["test_oracle_bbs.py::test_trial_division_matches_library"]),
@@ -71,11 +80,16 @@ MUTANTS = [
     ("qc_fixed_point_shift", "uint64_t a = held[l] >> 8, b = xs[l] >> 8;",
      "uint64_t a = held[l] >> 7, b = xs[l] >> 8;",
      ["test_oracle_seeding_stats.py::test_qc_counts_equal_real_number_test"]),
+    ("qc_threshold", "if (a * a + b * b < (1ULL << 48))", "if (a * a + b * b < (1ULL << 47))",
+     ["test_oracle_seeding_stats.py::test_qc_counts_equal_real_number_test"]),
     ("lane_counter_overlap", "return orc_draw(seed, (lane << 32) + k);", "return orc_draw(seed, (lane << 31) + k);",
      ["test_oracle_seeding_stats.py::test_lane_counter_ranges"]),
     # chaotic Blum-Goldwasser (Sec. 9.2)
     ("bg_keystream_without_s0", "uint32_t k = S0;", "uint32_t k = 0;",
      ["test_oracle_bg.py::test_keystream_is_prefix_xor_of_bbs_bits"]),
+    ("bg_decryption_keystream_without_s0", "uint64_t x = orc_bg_recover_x0(p, q, y, L);\n    uint32_t k = S0;",
+     "uint64_t x = orc_bg_recover_x0(p, q, y, L);\n    uint32_t k = 0;",
+     ["test_oracle_bg.py::test_round_trip_and_paper_sized_key"]),
     ("bg_crt_inverse_transposed", "orc_invmod(q % p, p)", "orc_invmod(p % q, q)",
      ["test_oracle_bg.py::test_crt_recovers_x0"]),
     ("bg_root_exponent_power_off_by_one", "orc_powmod((p + 1) / 4, L, p - 1)", "orc_powmod((p + 1) / 4, L + 1, p - 1)",
