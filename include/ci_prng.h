@@ -121,7 +121,13 @@ ci_status ci_state_bytes(const ci_params *params, uint64_t n_streams, uint64_t *
  * padding lanes are computed but never returned.
  * The library allocates the device memory (cudaMalloc); ci_free_states frees it.
  * Errors: CI_E_INVAL (bad params, n_streams out of range), CI_E_NOMEM,
- * CI_E_CUDA. */
+ * CI_E_CUDA.
+ * Fault injection (tests of the error paths; host only): with the environment
+ * variable CI_FAULT holding "alloc_fail@N", the N-th state allocation of
+ * ci_init_states / ci_init_states_many since CI_FAULT took its current value
+ * fails with CI_E_NOMEM before any device call.  The serving loop reads
+ * "queue_full@N", "reject_admit@N" and "launch_fail@N" from the same variable
+ * (comma-separated) when a server is created (ci_server_create). */
 ci_status ci_init_states(const ci_params *params, uint64_t n_streams, void *cuda_stream,
                          ci_states *out);
 
@@ -346,7 +352,12 @@ typedef struct {
 /* Creates a server over caller-owned device memory `arena_dev` of arena_bytes
  * bytes (outputs and stream states are sub-allocated from it; it must outlive
  * the server), on the current device.  cfg may be NULL (defaults).  Starts the
- * worker thread.  Errors: CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA. */
+ * worker thread.  Fault injection (host only, read here from the environment
+ * variable CI_FAULT, comma-separated): "queue_full@N" makes the N-th
+ * submission return CI_E_BUSY, "reject_admit@N" fails the N-th admission with
+ * CI_E_NOMEM, "launch_fail@N" treats the N-th wave as not launched (its
+ * requests end with CI_E_CUDA once the earlier waves have completed).
+ * Errors: CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA. */
 ci_status ci_server_create(void *arena_dev, uint64_t arena_bytes, const ci_server_config *cfg, ci_server *out);
 
 /* Queues a request (thread-safe) and returns its ticket (> 0).  Errors:

@@ -3,7 +3,9 @@
 // ci_status and records a message for ci_last_error() on failure.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -176,12 +178,35 @@ ci_status ci_state_bytes(const ci_params *params, uint64_t n_streams, uint64_t *
     return CI_OK;
 }
 
+// Host-side fault injection for the error paths (CI_FAULT="alloc_fail@N"):
+// the N-th state allocation since CI_FAULT took its current value fails with
+// CI_E_NOMEM before anything touches the device.  The server's own hooks
+// (queue_full, reject_admit, launch_fail) share the variable and are read
+// when a server is created.
+static bool injected_alloc_failure() {
+    static std::mutex m;
+    static std::string spec;
+    static uint64_t count = 0;
+    const char *env = std::getenv("CI_FAULT");
+    std::lock_guard<std::mutex> g(m);
+    const std::string now = env ? env : "";
+    if (now != spec) {
+        spec = now;
+        count = 0;
+    }
+    const size_t at = spec.find("alloc_fail@");
+    if (at == std::string::npos) return false;
+    const uint64_t n = std::strtoull(spec.c_str() + at + 11, nullptr, 10);
+    return ++count == n;
+}
+
 ci_status ci_init_states(const ci_params *params, uint64_t n_streams, void *cuda_stream, ci_states *out) {
     if (!out) return fail(CI_E_INVAL, "out is NULL");
     *out = nullptr;
     ci_status st = check_params(params, n_streams);
     if (st != CI_OK) return st;
     const uint64_t bytes = state_bytes_for(params->variant, lanes_for(n_streams));
+    if (injected_alloc_failure()) return fail(CI_E_NOMEM, "injected allocation failure (CI_FAULT alloc_fail)");
     void *dev = nullptr;
     cudaError_t e = cudaMalloc(&dev, bytes);
     if (e != cudaSuccess) {
@@ -222,6 +247,10 @@ ci_status ci_init_states_many(const ci_params *params, const uint64_t *n_streams
     ci_status rc = CI_OK;
     for (uint32_t i = 0; i < n && rc == CI_OK; ++i) {
         const uint64_t bytes = state_bytes_for(params[i].variant, lanes_for(n_streams[i]));
+        if (injected_alloc_failure()) {
+            rc = fail(CI_E_NOMEM, "item " + std::to_string(i) + ": injected allocation failure (CI_FAULT alloc_fail)");
+            break;
+        }
         void *dev = nullptr;
         cudaError_t e = cudaMalloc(&dev, bytes);
         if (e != cudaSuccess) {

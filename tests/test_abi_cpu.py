@@ -120,3 +120,26 @@ def test_workload_generators_are_deterministic():
         if r.continues >= 0:
             base = s[r.continues]
             assert base.continues < 0 and base.n_streams == r.n_streams and base.seed == r.seed
+
+
+def test_injected_allocation_failure_without_gpu(L, monkeypatch):
+    """CI_FAULT="alloc_fail@N" fails the N-th state allocation with
+    CI_E_NOMEM before any device call (so it runs here, without a GPU); the
+    count restarts whenever CI_FAULT changes, and ci_init_states_many reports
+    the failing item."""
+    lib = L.lib()
+    p = L.ci_params()
+    p.variant, p.xl, p.comb_size, p.seed = 0, 0, 32, 1
+    h = ctypes.c_void_p()
+    monkeypatch.setenv("CI_FAULT", "alloc_fail@1")
+    assert lib.ci_init_states(ctypes.byref(p), 64, None, ctypes.byref(h)) == L.CI_E_NOMEM
+    assert b"injected allocation failure" in lib.ci_last_error()
+    assert not h.value
+    monkeypatch.setenv("CI_FAULT", "queue_full@3,alloc_fail@1")  # a new value: the count restarts
+    params = (L.ci_params * 2)(p, p)
+    counts = np.array([64, 40], dtype=np.uint64)
+    hs = (ctypes.c_void_p * 2)()
+    assert lib.ci_init_states_many(ctypes.cast(params, ctypes.c_void_p), counts.ctypes.data, 2, None,
+                                   ctypes.cast(hs, ctypes.c_void_p)) == L.CI_E_NOMEM
+    assert b"item 0: injected allocation failure" in lib.ci_last_error()
+    assert not hs[0] and not hs[1]

@@ -199,3 +199,19 @@ def test_init_states_many_equals_single_inits(env):
     sp = specs[5]
     ref = oracle_gen(sp["variant"], sp["xl"], sp["comb_size"], sp["seed"], sp["comb_seed"], sp["n_streams"] + 32 * (5 % 5))
     assert np.array_equal(out, ref.streams(40)[:sp["n_streams"]])
+
+
+def test_injected_allocation_failure(env, monkeypatch):
+    """CI_FAULT="alloc_fail@2": the second state allocation fails with
+    CI_E_NOMEM and leaves nothing behind; the states around it are intact and
+    equal the oracle."""
+    torch, ci = env
+    monkeypatch.setenv("CI_FAULT", "alloc_fail@2")
+    a = ci.States(64, seed=31)
+    with pytest.raises(ci.CIError) as e:
+        ci.States(64, seed=32)
+    assert e.value.status == -2
+    c = ci.States(64, seed=33)
+    monkeypatch.delenv("CI_FAULT")
+    assert np.array_equal(u32(a.generate(40)), oracle_gen("xor", "xor128", 32, 31, 0, 64).streams(40))
+    assert np.array_equal(u32(c.generate(40)), oracle_gen("xor", "xor128", 32, 33, 0, 64).streams(40))
