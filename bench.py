@@ -322,7 +322,8 @@ def host_cpu() -> str:
 
 def run_reference(args, world, rank):
     """--impl reference: the oracle on the host cores, each step a bounded
-    sample of the main workload (2^15 streams x 4096)."""
+    sample of the main workload (2^17 streams x 4096).  Under torchrun only
+    rank 0 runs and prints; the other ranks return without work."""
     if rank != 0:
         return
     n_streams = 1 << 17
