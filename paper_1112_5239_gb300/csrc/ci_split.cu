@@ -37,6 +37,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "ci_split.h"
@@ -580,9 +581,15 @@ constexpr uint64_t kMinAutoSegment = 1024;  // ... xor-likes, and when a single 
 // segment state with that index.
 // Instantiated per source and sink, with at most 64 registers (4 blocks of 8
 // warps per SM): the all-source batched kernel needs 128, which held the
-// BBS segments to 16 resident warps per SM.
+// BBS segments to 16 resident warps per SM.  BBS segments (one serial
+// squaring chain per lane) ask for 5 blocks, i.e. 48 registers.
+template <class Src>
+constexpr int split_min_blocks() {
+    return std::is_same<Src, SrcBbs>::value ? 5 : 4;
+}
+
 template <class Src, int SINK>
-__global__ void __launch_bounds__(256, 4) k_split_run(SegSpace seg, DevState caller, int zero, uint32_t k_begin,
+__global__ void __launch_bounds__(256, split_min_blocks<Src>()) k_split_run(SegSpace seg, DevState caller, int zero, uint32_t k_begin,
                                                    uint32_t k_end, uint32_t K, uint64_t len, uint64_t len_last,
                                                    uint64_t groups, uint32_t *out, uint64_t ld, uint64_t col0,
                                                    uint64_t *aux) {
