@@ -143,3 +143,36 @@ def test_injected_allocation_failure_without_gpu(L, monkeypatch):
                                    ctypes.cast(hs, ctypes.c_void_p)) == L.CI_E_NOMEM
     assert b"item 0: injected allocation failure" in lib.ci_last_error()
     assert not hs[0] and not hs[1]
+
+
+def test_workload_distributions_follow_the_recipe():
+    """The seeded request lists have the stated shapes: log-uniform stream
+    counts in [1, 2^16] and lengths in [2^6, 2^20] (mean log2 about 8 and 13),
+    80 % xor128; serving sizes lognormal with median about 2^16 numbers,
+    power-of-two stream counts S = 2^clamp(floor(log2 n) - 10, 0, 16) for new
+    stream sets, and about 30 % continuations."""
+    import math
+
+    from paper_1112_5239_gb300 import workloads as W
+
+    a = W.batched_requests(count=4000)
+    ls = np.array([math.log2(r.n_streams) for r in a])
+    ll = np.array([math.log2(r.n_per_stream) for r in a])
+    assert abs(ls.mean() - 8.0) < 0.4 and ls.min() >= 0 and ls.max() <= 16
+    assert abs(ll.mean() - 13.0) < 0.4 and ll.min() >= 6 and ll.max() <= 20
+    s = W.serving_requests(count=4000)
+    cont = [r for r in s if r.continues >= 0]
+    assert abs(len(cont) / len(s) - 0.3) < 0.03
+    new = [r for r in s if r.continues < 0]
+    for r in new:
+        S, L = r.n_streams, r.n_per_stream
+        assert S & (S - 1) == 0 and 1 <= S <= 2**16
+        # n in [2^(10+k), 2^(11+k)) with S = 2^k gives L = ceil(n / S) in [2^10, 2^11]
+        if S == 1:
+            assert L <= 2**11
+        elif S < 2**16:
+            assert 2**10 <= L <= 2**11
+        else:
+            assert 2**10 <= L <= 2**12  # n capped at 2^28
+    med = float(np.median([r.n_streams * r.n_per_stream for r in new]))
+    assert 2**15.6 < med < 2**16.5
