@@ -17,14 +17,15 @@
 //      powers for the xor-likes, x <- x^(2^(11 k len) mod lambda(M)) for BBS,
 //      each of the eight 16-bit generators by its own squaring count for
 //      Algorithm 5 as printed) and (s, x) = (0, 0) for k >= 1;
-//   2. pass 1 (k_split_run): written BBS outputs: every segment from there
+//   2. pass 1 (k_split_run): written outputs of the BBS sources (62-bit and
+//      Algorithm 5 as printed): every segment from there
 //      into its output columns; otherwise segments 0 .. K-2 into a digest
 //      sink (only their end states are needed);
 //   3. k_split_carry: one block per warp group scans the segments: the true
 //      start of segment k is its predecessor's particular end plus
 //      (Q s_a, x_a ^ S s_a) with Q = P^len, S = P + ... + P^len (a chunked
 //      parallel scan over up to 16 warps);
-//   4. written BBS outputs: k_split_fixup XORs each segment's homogeneous
+//   4. written BBS-source outputs: k_split_fixup XORs each segment's homogeneous
 //      part into its outputs (the mixing step with zero own words: two
 //      shuffles per output); otherwise pass 2 (k_split_run) runs every
 //      segment from its true start, with the own words k_split_setup jumped
