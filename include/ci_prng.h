@@ -31,6 +31,8 @@
  *   - Results depend only on (parameters, stream index, position in the
  *     stream): not on launch shape, batching, or how a stream's length is split
  *     over calls (a call continues exactly where the previous one stopped).
+ *     The one exception is CI_VAR_BBS16, Algorithm 5 as printed, whose array
+ *     choice and rotation happen per call (see ci_params.variant).
  */
 #ifndef CI_PRNG_H
 #define CI_PRNG_H
@@ -150,6 +152,10 @@ ci_status ci_init_states_many(const ci_params *params, const uint64_t *n_streams
  * The caller must ensure no enqueued call still uses it.  NULL is a no-op. */
 ci_status ci_free_states(ci_states states);
 
+/* Fills *out with what the handle holds: parameters, stream and lane counts,
+ * the state's size and device address, and the combination arrays in use.
+ * Host only; no device call.  Errors: CI_E_STATE (dead handle), CI_E_INVAL
+ * (out NULL). */
 ci_status ci_states_query(ci_states states, ci_states_desc *out);
 
 /* ---------------------------------------------------------- generation */
@@ -175,8 +181,7 @@ ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev
  * with BBS7 and BBS2 (12 squarings per output); the arrays are comb[BBS1 & 7]
  * and comb[8 + (BBS2 & 7)] taken when the call starts, and at its end
  * generator k (state and modulus) moves to place k + 1.
- * For CI_VAR_BBS:  Each strategy
- * word takes ceil(32/w) BBS outputs' low w bits (w = floor(log2 log2 M) = 5
+ * For CI_VAR_BBS, each strategy word takes ceil(32/w) BBS outputs' low w bits (w = floor(log2 log2 M) = 5
  * for these 62-bit moduli), then twice: shift = BBS & 3; t <<= shift;
  * t |= BBS & {0,1,3,7}[shift] -- 11 modular squarings per output, done with
  * 64x64->128-bit multiplies and Barrett reduction.  The stream's two
@@ -285,8 +290,9 @@ ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, voi
 
 /* ------------------------------------------------------------ serving */
 
-/* A serving loop with continuous batching.  A worker thread owns one CUDA
- * stream.  Requests queue on submission; at every wave the worker:
+/* A serving loop with continuous batching.  A worker thread owns the
+ * server's CUDA streams.  Requests queue on submission; at every wave the
+ * worker:
  *  - admits pending requests in arrival order while a slot and arena memory
  *    for the request's output (and, for new streams, its state) are free;
  *  - takes the next time slice of every admitted request (slice_xor or
@@ -298,10 +304,11 @@ ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, voi
  * result whether the request runs alone or in any mix.  (CI_VAR_BBS16, whose
  * outputs depend on call boundaries, runs each request as one slice: one
  * call.)  Long requests over few streams run instead as one time-parallel
- * split job on the same stream (see ci_generate_split), with the same
- * results.  Stream state stays
- * resident in the arena between requests; a request may continue the streams
- * of an earlier request. */
+ * split job (see ci_generate_split), up to four at a time, each on its own
+ * side stream beside the waves, with the same results.  New stream sets are
+ * seeded in one launch per admission pass on another side stream.  Stream
+ * state stays resident in the arena between requests; a request may continue
+ * the streams of an earlier request. */
 typedef struct ci_server_s *ci_server;
 
 typedef struct {
@@ -392,6 +399,8 @@ ci_status ci_release(ci_server server, uint64_t ticket);
  * not be in use by a queued or running request (CI_E_BUSY). */
 ci_status ci_release_states(ci_server server, uint64_t ticket);
 
+/* Copies the server's counters (a consistent snapshot taken under its lock)
+ * into *out.  Errors: CI_E_STATE (dead server), CI_E_INVAL (out NULL). */
 ci_status ci_server_get_stats(ci_server server, ci_server_stats *out);
 
 /* Load generator for measurement: submits reqs[i] when arrival_s[i] seconds
