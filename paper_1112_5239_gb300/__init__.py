@@ -30,6 +30,30 @@ def stream_ptr(stream=None) -> int:
     return int(s.cuda_stream)
 
 
+def _dev_buf(name, t, dtype, min_numel=0) -> int:
+    """Device address of a caller-supplied buffer, after the checks the C ABI
+    cannot make: a contiguous CUDA tensor of the right dtype, and (for the
+    per-stream counts and digests, which carry no capacity) at least
+    ``min_numel`` elements.  Output capacities are checked by the library."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, not %s" % (name, dtype, t.dtype))
+    if t.numel() < min_numel:
+        raise ValueError("%s needs at least %d elements, has %d" % (name, min_numel, t.numel()))
+    return t.data_ptr()
+
+
+def _item_buffers(st, sink, t):
+    """(out_dev, out_capacity_u32, aux_dev) of one batch item."""
+    if t is None:
+        return None, 0, None
+    if sink == _lib.CI_SINK_WRITTEN:
+        return _dev_buf("written output", t, torch.int32), t.numel(), None
+    n = st.n_streams if isinstance(st, States) else 0
+    return None, 0, _dev_buf("counts / digests", t, torch.int64, n)
+
+
 def make_params(variant="xor", xl="xor128", comb_size=32, seed=0, comb_seed=0, comb=None, first_stream=0):
     """A ci_params struct (and the buffer keeping explicit arrays alive)."""
     p = ci_params()
@@ -122,7 +146,7 @@ class States:
         if out is None:
             out = torch.empty((self.n_streams, n), dtype=torch.int32, device="cuda")
         name = "ci_generate" if self.variant == _lib.CI_VAR_XOR else "ci_generate_bbs"
-        _lib.call(name, self.handle, n, out.data_ptr(), out.numel(), stream_ptr(stream))
+        _lib.call(name, self.handle, n, _dev_buf("out", out, torch.int32), out.numel(), stream_ptr(stream))
         return out
 
     def generate_fused_qc(self, n_per_stream, counts=None, stream=None) -> torch.Tensor:
@@ -130,8 +154,8 @@ class States:
         ``counts`` (int64 [n_streams], zero-initialised if not given)."""
         if counts is None:
             counts = torch.zeros(self.n_streams, dtype=torch.int64, device="cuda")
-        _lib.call("ci_generate_fused_qc", self.handle, int(n_per_stream), counts.data_ptr(),
-                  stream_ptr(stream))
+        _lib.call("ci_generate_fused_qc", self.handle, int(n_per_stream),
+                  _dev_buf("counts", counts, torch.int64, self.n_streams), stream_ptr(stream))
         return counts
 
     def generate_digest(self, n_per_stream, digest=None, stream=None) -> torch.Tensor:
@@ -139,7 +163,8 @@ class States:
         without storing them."""
         if digest is None:
             digest = torch.zeros(self.n_streams, dtype=torch.int64, device="cuda")
-        _lib.call("ci_generate_digest", self.handle, int(n_per_stream), digest.data_ptr(), stream_ptr(stream))
+        _lib.call("ci_generate_digest", self.handle, int(n_per_stream),
+                  _dev_buf("digest", digest, torch.int64, self.n_streams), stream_ptr(stream))
         return digest
 
     def generate_split(self, n_per_stream, sink="written", out=None, segments=0, stream=None) -> torch.Tensor:
@@ -155,8 +180,11 @@ class States:
                 out = torch.empty((self.n_streams, n), dtype=torch.int32, device="cuda")
             else:
                 out = torch.zeros(self.n_streams, dtype=torch.int64, device="cuda")
-        _lib.call("ci_generate_split", self.handle, n, code, out.data_ptr(), out.numel(), int(segments),
-                  stream_ptr(stream))
+        if code == _lib.CI_SINK_WRITTEN:
+            ptr = _dev_buf("out", out, torch.int32)
+        else:
+            ptr = _dev_buf("out", out, torch.int64, self.n_streams)
+        _lib.call("ci_generate_split", self.handle, n, code, ptr, out.numel(), int(segments), stream_ptr(stream))
         return out
 
     # ------------------------------------------------- checkpoint/resume
@@ -205,14 +233,7 @@ class Batch:
             it.n_per_stream = int(n)
             it.sink = SINKS[sink] if isinstance(sink, str) else int(sink)
             it.reserved = 0
-            if it.sink == _lib.CI_SINK_WRITTEN:
-                it.out_dev = t.data_ptr() if t is not None else None
-                it.out_capacity_u32 = t.numel() if t is not None else 0
-                it.aux_dev = None
-            else:
-                it.out_dev = None
-                it.out_capacity_u32 = 0
-                it.aux_dev = t.data_ptr() if t is not None else None
+            it.out_dev, it.out_capacity_u32, it.aux_dev = _item_buffers(st, it.sink, t)
         _lib.call("ci_batch_run", self.handle, ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
 
     def close(self) -> None:
@@ -382,10 +403,7 @@ def batch_run_noalloc(items, stream=None) -> None:
         it.n_per_stream = int(n)
         it.sink = SINKS[sink] if isinstance(sink, str) else int(sink)
         it.reserved = 0
-        written = it.sink == _lib.CI_SINK_WRITTEN
-        it.out_dev = t.data_ptr() if (written and t is not None) else None
-        it.out_capacity_u32 = t.numel() if (written and t is not None) else 0
-        it.aux_dev = t.data_ptr() if (not written and t is not None) else None
+        it.out_dev, it.out_capacity_u32, it.aux_dev = _item_buffers(st, it.sink, t)
     _lib.call("ci_batch_run_noalloc", ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
 
 
@@ -405,8 +423,8 @@ class NaiveStates:
         n = int(n_per_stream)
         if out is None:
             out = torch.empty((self.n_streams, n), dtype=torch.int32, device="cuda")
-        _lib.call("ci_naive_generate", self.buf.data_ptr(), self.n_streams, n, out.data_ptr(), out.numel(),
-                  stream_ptr(stream))
+        _lib.call("ci_naive_generate", self.buf.data_ptr(), self.n_streams, n, _dev_buf("out", out, torch.int32),
+                  out.numel(), stream_ptr(stream))
         return out
 
 

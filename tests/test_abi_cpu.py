@@ -176,3 +176,22 @@ def test_workload_distributions_follow_the_recipe():
             assert 2**10 <= L <= 2**12  # n capped at 2^28
     med = float(np.median([r.n_streams * r.n_per_stream for r in new]))
     assert 2**15.6 < med < 2**16.5
+
+
+def test_binding_rejects_host_tensors_without_gpu():
+    """Host tensors never reach the C ABI as device pointers (checked before
+    any library call, so this runs without a GPU)."""
+    import torch
+
+    import paper_1112_5239_gb300 as ci
+
+    st = ci.States.__new__(ci.States)
+    st.n_streams, st.variant, st.handle = 4, 0, ctypes.c_void_p()
+    with pytest.raises(TypeError):
+        st.generate(8, out=torch.empty(32, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        st.generate_fused_qc(8, counts=torch.zeros(4, dtype=torch.int64))
+    with pytest.raises(TypeError):
+        st.generate_digest(8, digest=torch.zeros(4, dtype=torch.int64))
+    with pytest.raises(TypeError):
+        st.generate_split(8, sink="digest", out=torch.zeros(4, dtype=torch.int64))

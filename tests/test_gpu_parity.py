@@ -215,3 +215,27 @@ def test_injected_allocation_failure(env, monkeypatch):
     monkeypatch.delenv("CI_FAULT")
     assert np.array_equal(u32(a.generate(40)), oracle_gen("xor", "xor128", 32, 31, 0, 64).streams(40))
     assert np.array_equal(u32(c.generate(40)), oracle_gen("xor", "xor128", 32, 33, 0, 64).streams(40))
+
+
+def test_binding_buffer_checks(env):
+    """The binding rejects buffers the C ABI cannot check before any call:
+    wrong dtype, non-contiguous views, and per-stream counts or digests
+    shorter than the stream count (the ABI takes no capacity for them)."""
+    torch, ci = env
+    st = _states(ci, "xor", "xor128", 32, 1, 0, 10)
+    with pytest.raises(TypeError):
+        st.generate(8, out=torch.empty(80, dtype=torch.float32, device="cuda"))
+    with pytest.raises(TypeError):
+        st.generate(8, out=torch.empty((8, 10), dtype=torch.int32, device="cuda").t())
+    with pytest.raises(ValueError):
+        st.generate_fused_qc(8, counts=torch.zeros(9, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        st.generate_digest(8, digest=torch.zeros(9, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        st.generate_split(64, sink="qc", out=torch.zeros(9, dtype=torch.int64, device="cuda"))
+    b = ci.Batch(1)
+    with pytest.raises(ValueError):
+        b.run([(st, 8, "digest", torch.zeros(9, dtype=torch.int64, device="cuda"))])
+    b.close()
+    # the state did not move: the next outputs are the first ones
+    assert np.array_equal(u32(st.generate(8)), oracle_gen("xor", "xor128", 32, 1, 0, 10).streams(8))
