@@ -39,6 +39,8 @@ MUTANTS = [
     ("mix_asynchronous_reading", "tnew[l] = xl[l] ^ tprev[part1[l]] ^ tprev[part2[l]];",
      "tnew[l] = tprev[l] = xl[l] ^ tprev[part1[l]] ^ tprev[part2[l]];",
      ["test_oracle_mixing.py::test_hand_worked_c2_synchronous", "test_oracle_mixing.py::test_hand_worked_c4"]),
+    ("ci_update_with_own_word", "x[l] = orc_ci_step(x[l], tnew[l]);", "x[l] = orc_ci_step(x[l], xl[l]);",
+     ["test_oracle_mixing.py::test_hand_worked_c2_synchronous"]),
     ("mix_second_array_read_from_first", "p2[l] = base + c2[offset];", "p2[l] = base + c1[offset];",
      ["test_oracle_mixing.py::test_partner_indexing_impulse_xor"]),
     ("mix_group_base_dropped", "p1[l] = base + c1[offset];", "p1[l] = c1[offset];",
@@ -49,6 +51,9 @@ MUTANTS = [
      ["test_oracle_bbs.py::test_bbs_step_large_moduli"]),
     ("bbs_chunk_one_bit_short", "t |= (uint32_t)(orc_bbs_next(s) & mask);",
      "t |= (uint32_t)(orc_bbs_next(s) & (mask >> 1));",
+     ["test_oracle_bbs.py::test_assembly_w4_matches_algorithm5_text", "test_oracle_bbs.py::test_assembly_w5"]),
+    ("bbs_shift_draw_one_bit", "uint32_t shift = (uint32_t)(orc_bbs_next(s) & 3u);",
+     "uint32_t shift = (uint32_t)(orc_bbs_next(s) & 1u);",
      ["test_oracle_bbs.py::test_assembly_w4_matches_algorithm5_text", "test_oracle_bbs.py::test_assembly_w5"]),
     ("bbs_array_shift_entry", "static const uint32_t array_shift[4] = {0u, 1u, 3u, 7u};",
      "static const uint32_t array_shift[4] = {0u, 1u, 3u, 3u};",
@@ -74,6 +79,8 @@ MUTANTS = [
      ["test_oracle_bbs16.py::test_recurrence_with_arrays_chosen_per_call"]),
     ("bbs16_rotation_missing", "orc_bbs16_rotate(&lanes[l]);", ";",
      ["test_oracle_bbs16.py::test_squaring_counts_and_rotation_after_a_call"]),
+    ("bbs16_shift_from_wrong_generator", "shift = orc_bbs16_next(L, 2) & 3u;", "shift = orc_bbs16_next(L, 3) & 3u;",
+     ["test_oracle_bbs16.py::test_hand_worked_word_fixes_generator_order"]),
     ("bbs16_nibble_three_bits", "t |= orc_bbs16_next(L, k) & 15u;", "t |= orc_bbs16_next(L, k) & 7u;",
      ["test_oracle_bbs16.py::test_hand_worked_word_fixes_generator_order"]),
     # the quarter-circle consumer and the seeding counter layout
@@ -82,10 +89,14 @@ MUTANTS = [
      ["test_oracle_seeding_stats.py::test_qc_counts_equal_real_number_test"]),
     ("qc_threshold", "if (a * a + b * b < (1ULL << 48))", "if (a * a + b * b < (1ULL << 47))",
      ["test_oracle_seeding_stats.py::test_qc_counts_equal_real_number_test"]),
+    ("qc_pairs_shifted_by_one", "if ((i & 1) == 0) {", "if ((i & 1) == 1) {",
+     ["test_oracle_seeding_stats.py::test_qc_counts_equal_real_number_test"]),
     ("lane_counter_overlap", "return orc_draw(seed, (lane << 32) + k);", "return orc_draw(seed, (lane << 31) + k);",
      ["test_oracle_seeding_stats.py::test_lane_counter_ranges"]),
     # chaotic Blum-Goldwasser (Sec. 9.2)
     ("bg_keystream_without_s0", "uint32_t k = S0;", "uint32_t k = 0;",
+     ["test_oracle_bg.py::test_keystream_is_prefix_xor_of_bbs_bits"]),
+    ("bg_chunk_one_bit_short", "k ^= (uint32_t)(x & mask);", "k ^= (uint32_t)(x & (mask >> 1));",
      ["test_oracle_bg.py::test_keystream_is_prefix_xor_of_bbs_bits"]),
     ("bg_decryption_keystream_without_s0", "uint64_t x = orc_bg_recover_x0(p, q, y, L);\n    uint32_t k = S0;",
      "uint64_t x = orc_bg_recover_x0(p, q, y, L);\n    uint32_t k = 0;",
@@ -97,6 +108,8 @@ MUTANTS = [
     # Listing 1 / Algorithm 3
     ("listing1_dropped_xor", "    x ^= (uint32_t)(t3 >> 32);\n", "",
      ["test_oracle_naive.py::test_listing1_combination_hand_worked"]),
+    ("naive_xor128_shift_amount", "T t = s[0] ^ (s[0] << 11);", "T t = s[0] ^ (s[0] << 10);",
+     ["test_oracle_naive.py::test_xor128_instances_share_the_pinned_recurrence"]),
     ("naive_xorshift_shift_amount", "T t = s[0] ^ (s[0] >> 7);", "T t = s[0] ^ (s[0] >> 6);",
      ["test_oracle_naive.py::test_xorshift160_full_period"]),
     ("naive_xorwow_shift_amount", "s[4] = (s[4] ^ (s[4] << 4)) ^ (t ^ (t << 1));",
