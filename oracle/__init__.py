@@ -111,7 +111,7 @@ def lib() -> ctypes.CDLL:
             "orc_xorwow_step64": (u64, [vp, vp]),
             "orc_listing1_combine": (u32, [u32, u64, u64, u64]),
             "orc_naive_lane_size": (u32, []),
-            "orc_listing1_run": (None, [u64, vp]),
+            "orc_listing1_run": (None, [u32, u64, vp]),
             "orc_naive_init_lanes": (None, [u64, u64, u64, vp]),
             "orc_naive_run": (None, [vp, u64, u64, vp]),
         }
@@ -242,9 +242,11 @@ def listing1_combine(x: int, t1: int, t2: int, t3: int) -> int:
     return int(lib().orc_listing1_combine(x, t1, t2, t3))
 
 
-def listing1_run(n: int) -> np.ndarray:
+def listing1_run(n: int, x0: int) -> np.ndarray:
+    """Listing 1 run sequentially from CI state x0 (the listing starts it at
+    123123123)."""
     out = np.zeros(n, dtype=np.uint32)
-    lib().orc_listing1_run(n, _ptr(out))
+    lib().orc_listing1_run(x0, n, _ptr(out))
     return out
 
 

@@ -62,9 +62,12 @@
  *   full period of xor128 as a GF(2)-linear map; mixing special cases and a
  *   hand-worked small case; GF(2) linearity; BBS squaring on tiny Blum moduli;
  *   Algorithm 5's 4-bit packing on hand-fed BBS values; quarter-circle counts
- *   against the real-number test.  The splitmix64 seeding and the exact xor128
- *   shift triple are readings taken from outside the paper: their values are
- *   "parity unpinned" beyond the structural checks above.
+ *   against the real-number test; the first outputs of the published
+ *   splitmix64, xor128 and xor64 programs from their printed start states; the
+ *   output functions of Listing 1's five-word xorshift and xorwow by the
+ *   linearity of the word sequences they must give back.  Parity unpinned
+ *   (readings, not values fixed by the paper): the counter layout of the
+ *   seeding draws, and Listing 1's use of its xor-likes on 64-bit words.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -729,16 +732,13 @@ void orc_bg_decrypt(uint64_t p, uint64_t q, uint32_t S0, uint64_t y, uint64_t L,
 ORC_DEFINE_NAIVE_XORLIKES(uint32_t, 32)
 ORC_DEFINE_NAIVE_XORLIKES(uint64_t, 64)
 
-/* Listing 1's six XORs: the low and high halves of t1, t2 and t3. */
+/* Listing 1 (Sec. 5) XORs into x the low and the high 32-bit half of each of
+ * t1, t2 and t3.  XOR is associative and commutative, so that is x XOR the two
+ * halves of T = t1 XOR t2 XOR t3. */
 uint32_t orc_listing1_combine(uint32_t x, uint64_t t1, uint64_t t2, uint64_t t3)
 {
-    x ^= (uint32_t)t1;
-    x ^= (uint32_t)(t2 >> 32);
-    x ^= (uint32_t)(t3 >> 32);
-    x ^= (uint32_t)t2;
-    x ^= (uint32_t)(t1 >> 32);
-    x ^= (uint32_t)t3;
-    return x;
+    const uint64_t T = t1 ^ t2 ^ t3;
+    return x ^ (uint32_t)T ^ (uint32_t)(T >> 32);
 }
 
 typedef struct {
@@ -761,10 +761,10 @@ static uint32_t orc_naive_next(orc_naive_lane *L)
     return L->x;
 }
 
-/* Listing 1 as a sequential program: x starts at 123123123 and the three
- * xor-likes at the static seeds of Marsaglia's listings (x, y, z, w, v =
- * 123456789, 362436069, 521288629, 88675123, 5783321; d = 6615241). */
-void orc_listing1_run(uint64_t n, uint32_t *out)
+/* Listing 1 as a sequential program: the CI state starts at x0 and the three
+ * xor-likes at the start words of Marsaglia's published generators (x, y, z, w,
+ * v = 123456789, 362436069, 521288629, 88675123, 5783321; d = 6615241). */
+void orc_listing1_run(uint32_t x0, uint64_t n, uint32_t *out)
 {
     orc_naive_lane L;
     const uint64_t seeds[5] = {123456789u, 362436069u, 521288629u, 88675123u, 5783321u};
@@ -774,7 +774,7 @@ void orc_listing1_run(uint64_t n, uint32_t *out)
     }
     for (int i = 0; i < 4; ++i) L.xo[i] = seeds[i];
     L.d = 6615241u;
-    L.x = 123123123u;
+    L.x = x0;
     for (uint64_t i = 0; i < n; ++i) out[i] = orc_naive_next(&L);
 }
 

@@ -79,9 +79,10 @@ struct NaiveLane {
         xw[4] = (xw[4] ^ (xw[4] << 4)) ^ (t ^ (t << 1));
         d += 362437ull;
         const uint64_t t3 = d + xw[4];
-        // Listing 1: the six 32-bit halves
-        x ^= (uint32_t)t1 ^ (uint32_t)(t2 >> 32) ^ (uint32_t)(t3 >> 32) ^ (uint32_t)t2 ^ (uint32_t)(t1 >> 32) ^
-             (uint32_t)t3;
+        // Listing 1 XORs both 32-bit halves of t1, t2 and t3 into x, which is x
+        // XOR both halves of T = t1 ^ t2 ^ t3
+        const uint64_t T = t1 ^ t2 ^ t3;
+        x ^= (uint32_t)T ^ (uint32_t)(T >> 32);
         return x;
     }
 };

@@ -6,7 +6,8 @@ macro instantiated for 32- and 64-bit words; the 32-bit instances must have
 the full periods their shift triples were chosen for (2^160 - 1, and
 xor128's 2^128 - 1, which also equals the separately pinned 32-bit xor128),
 so a wrong shift amount or direction fails here.  The output functions
-((y + y + 1) v, d + v) and the static seeds are parity-unpinned readings."""
+((y + y + 1) v, d + v) are pinned in tests/test_oracle_published.py; the
+64-bit use and the static start words are readings."""
 import numpy as np
 import pytest
 
@@ -114,5 +115,5 @@ def test_algorithm3_lanes_run_listing1_independently():
 
 
 def test_listing1_sequential_is_the_static_seeded_lane():
-    out = oracle.listing1_run(64)
+    out = oracle.listing1_run(64, 123123123)  # Listing 1's start value of x (Sec. 5)
     assert out.dtype == np.uint32 and len(set(out.tolist())) == 64

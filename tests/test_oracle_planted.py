@@ -106,7 +106,9 @@ MUTANTS = [
     ("bg_root_exponent_power_off_by_one", "orc_powmod((p + 1) / 4, L, p - 1)", "orc_powmod((p + 1) / 4, L + 1, p - 1)",
      ["test_oracle_bg.py::test_crt_recovers_x0"]),
     # Listing 1 / Algorithm 3
-    ("listing1_dropped_xor", "    x ^= (uint32_t)(t3 >> 32);\n", "",
+    ("listing1_dropped_high_halves", "return x ^ (uint32_t)T ^ (uint32_t)(T >> 32);", "return x ^ (uint32_t)T;",
+     ["test_oracle_naive.py::test_listing1_combination_hand_worked"]),
+    ("listing1_dropped_generator", "const uint64_t T = t1 ^ t2 ^ t3;", "const uint64_t T = t1 ^ t2;",
      ["test_oracle_naive.py::test_listing1_combination_hand_worked"]),
     ("naive_xor128_shift_amount", "T t = s[0] ^ (s[0] << 11);", "T t = s[0] ^ (s[0] << 10);",
      ["test_oracle_naive.py::test_xor128_instances_share_the_pinned_recurrence"]),
@@ -115,6 +117,44 @@ MUTANTS = [
     ("naive_xorwow_shift_amount", "s[4] = (s[4] ^ (s[4] << 4)) ^ (t ^ (t << 1));",
      "s[4] = (s[4] ^ (s[4] << 5)) ^ (t ^ (t << 1));",
      ["test_oracle_naive.py::test_xorwow_linear_part_full_period"]),
+    # published first outputs (splitmix64, xor128, xor64) and the output
+    # functions of Listing 1's five-word xorshift and xorwow
+    ("splitmix64_multiplier", "0xBF58476D1CE4E5B9ULL", "0xBF58476D1CE4E5B5ULL",
+     ["test_oracle_published.py::test_splitmix64_published_outputs"]),
+    ("splitmix64_shift", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;",
+     ["test_oracle_published.py::test_splitmix64_published_outputs"]),
+    ("splitmix64_gamma", "#define ORC_GAMMA 0x9E3779B97F4A7C15ULL", "#define ORC_GAMMA 0x9E3779B97F4A7C17ULL",
+     ["test_oracle_published.py::test_splitmix64_published_outputs"]),
+    ("splitmix64_counter_from_zero", "return orc_mix64(seed + (index + 1) * ORC_GAMMA);",
+     "return orc_mix64(seed + index * ORC_GAMMA);",
+     ["test_oracle_published.py::test_splitmix64_published_outputs"]),
+    ("xor128_triple_reversed",
+     "uint32_t tmp = a ^ (a << 11);\n    s[0] = s[1];\n    s[1] = s[2];\n    s[2] = s[3];\n"
+     "    s[3] = s[3] ^ (s[3] >> 19) ^ (tmp ^ (tmp >> 8));",
+     "uint32_t tmp = a ^ (a << 19);\n    s[0] = s[1];\n    s[1] = s[2];\n    s[2] = s[3];\n"
+     "    s[3] = s[3] ^ (s[3] >> 11) ^ (tmp ^ (tmp >> 8));",
+     ["test_oracle_published.py::test_xor128_published_outputs"]),
+    ("xor128_right_shifts_swapped", "s[3] = s[3] ^ (s[3] >> 19) ^ (tmp ^ (tmp >> 8));",
+     "s[3] = s[3] ^ (s[3] >> 8) ^ (tmp ^ (tmp >> 19));",
+     ["test_oracle_published.py::test_xor128_published_outputs"]),
+    ("xor64_triple_reversed", "x = x ^ (x << 13);\n    x = x ^ (x >> 7);\n    x = x ^ (x << 17);",
+     "x = x ^ (x << 17);\n    x = x ^ (x >> 7);\n    x = x ^ (x << 13);",
+     ["test_oracle_published.py::test_xor64_published_outputs"]),
+    ("naive_xs160_output_multiplier_word", "return (T)((T)(s[1] + s[1] + 1u) * s[4]);",
+     "return (T)((T)(s[2] + s[2] + 1u) * s[4]);",
+     ["test_oracle_published.py::test_xorshift160_32_output_is_odd_multiple_of_newest_word"]),
+    ("naive_xs160_output_even_multiplier", "return (T)((T)(s[1] + s[1] + 1u) * s[4]);",
+     "return (T)((T)(s[1] + s[1]) * s[4]);",
+     ["test_oracle_published.py::test_xorshift160_32_output_is_odd_multiple_of_newest_word"]),
+    ("naive_xs160_output_old_word", "return (T)((T)(s[1] + s[1] + 1u) * s[4]);",
+     "return (T)((T)(s[1] + s[1] + 1u) * s[3]);",
+     ["test_oracle_published.py::test_xorshift160_32_output_is_odd_multiple_of_newest_word"]),
+    ("naive_xorwow_output_xor", "return (T)(*d + s[4]);", "return (T)(*d ^ s[4]);",
+     ["test_oracle_published.py::test_xorwow32_output_is_weyl_plus_newest_word"]),
+    ("naive_xorwow_output_old_word", "return (T)(*d + s[4]);", "return (T)(*d + s[3]);",
+     ["test_oracle_published.py::test_xorwow32_output_is_weyl_plus_newest_word"]),
+    ("naive_xorwow_output_before_weyl_step", "return (T)(*d + s[4]);", "return (T)(*d - 362437u + s[4]);",
+     ["test_oracle_published.py::test_xorwow32_output_is_weyl_plus_newest_word"]),
 ]
 
 
