@@ -282,9 +282,12 @@ ci_status ci_batch_destroy(ci_batch batch);
  * call waits until work already queued on cuda_stream has started the copy;
  * host-side calls are serialised by a lock.  The first call on a device, made
  * with that device current, looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Errors: CI_E_INVAL (n_items > CI_NOALLOC_MAX_ITEMS, or the item checks of
- * ci_batch_run), CI_E_STATE, CI_E_CUDA. */
+ * (cudaGetSymbolAddress) and the launch size for that device's SM count.
+ * Because each call stages its queue in one host array that the next call
+ * overwrites, the call refuses to run on a stream that is being captured into
+ * a CUDA graph (a replay would read whatever the latest call staged).
+ * Errors: CI_E_INVAL (n_items > CI_NOALLOC_MAX_ITEMS, the stream is being
+ * captured, or the item checks of ci_batch_run), CI_E_STATE, CI_E_CUDA. */
 #define CI_NOALLOC_MAX_ITEMS 1024
 ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, void *cuda_stream);
 

@@ -213,6 +213,20 @@ class States:
             pass
 
 
+def batch_items(items):
+    """The ``ci_batch_item`` array (ctypes) of items ``(states, n_per_stream,
+    sink, tensor)``, as ``Batch.run`` and ``batch_run_noalloc`` pass it."""
+    arr = (_lib.ci_batch_item * max(1, len(items)))()
+    for i, (st, n, sink, t) in enumerate(items):
+        it = arr[i]
+        it.states = st.handle.value if isinstance(st, States) else st
+        it.n_per_stream = int(n)
+        it.sink = SINKS[sink] if isinstance(sink, str) else int(sink)
+        it.reserved = 0
+        it.out_dev, it.out_capacity_u32, it.aux_dev = _item_buffers(st, it.sink, t)
+    return arr
+
+
 class Batch:
     """A ``ci_batch``: runs many requests in one persistent-kernel launch.
 
@@ -226,14 +240,7 @@ class Batch:
         _lib.call("ci_batch_create", self.max_items, ctypes.byref(self.handle))
 
     def run(self, items, stream=None) -> None:
-        arr = (_lib.ci_batch_item * max(1, len(items)))()
-        for i, (st, n, sink, t) in enumerate(items):
-            it = arr[i]
-            it.states = st.handle.value if isinstance(st, States) else st
-            it.n_per_stream = int(n)
-            it.sink = SINKS[sink] if isinstance(sink, str) else int(sink)
-            it.reserved = 0
-            it.out_dev, it.out_capacity_u32, it.aux_dev = _item_buffers(st, it.sink, t)
+        arr = batch_items(items)
         _lib.call("ci_batch_run", self.handle, ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
 
     def close(self) -> None:
@@ -395,15 +402,9 @@ def batch_run_noalloc(items, stream=None) -> None:
     """Runs items (as ``Batch.run`` takes them) through the allocation-free
     entry point ``ci_batch_run_noalloc``: no device memory is allocated, the
     work queue is a fixed array inside the library (at most
-    CI_NOALLOC_MAX_ITEMS items; calls that overlap on the GPU race)."""
-    arr = (_lib.ci_batch_item * max(1, len(items)))()
-    for i, (st, n, sink, t) in enumerate(items):
-        it = arr[i]
-        it.states = st.handle.value if isinstance(st, States) else st
-        it.n_per_stream = int(n)
-        it.sink = SINKS[sink] if isinstance(sink, str) else int(sink)
-        it.reserved = 0
-        it.out_dev, it.out_capacity_u32, it.aux_dev = _item_buffers(st, it.sink, t)
+    CI_NOALLOC_MAX_ITEMS items; calls that overlap on the GPU race; refused
+    on a stream that is being captured)."""
+    arr = batch_items(items)
     _lib.call("ci_batch_run_noalloc", ctypes.cast(arr, ctypes.c_void_p), len(items), stream_ptr(stream))
 
 

@@ -338,8 +338,16 @@ extern "C" ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n
     if (n_items > kNoAllocMaxItems)
         return fail(CI_E_INVAL, "ci_batch_run_noalloc takes at most CI_NOALLOC_MAX_ITEMS (1024) items");
     if (n_items > 0 && !items) return fail(CI_E_INVAL, "items is NULL");
+    cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    // The queue upload reads the library's host staging array, which the next
+    // call overwrites: a captured upload would replay whatever was staged last.
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(cs, &capture);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (capture != cudaStreamCaptureStatusNone)
+        return fail(CI_E_INVAL, "ci_batch_run_noalloc cannot run while its stream is being captured");
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CI_E_INVAL, "device ordinal above 63");
 
@@ -398,7 +406,6 @@ extern "C" ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n
     std::memcpy(g_noalloc_host + sizeof hdr, g_noalloc_tasks, sizeof(BatchTask) * n_tasks);
     const size_t bytes = sizeof hdr + sizeof(BatchTask) * n_tasks;
 
-    cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
     // From pageable memory: returns once the bytes are staged, so the host
     // arrays may be reused by the next call.
     e = cudaMemcpyAsync(d.queue, g_noalloc_host, bytes, cudaMemcpyHostToDevice, cs);

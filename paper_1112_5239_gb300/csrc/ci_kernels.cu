@@ -7,6 +7,7 @@
 // which apply the autotuned launch shape.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -194,15 +195,21 @@ cudaError_t launch_init_batched(const InitTask *dev_tasks, uint32_t n_tasks, uin
 }
 
 // ------------------------------------------------------------ launchers
+// SM count of the current device, looked up once per device: one process may
+// drive GPUs of different models.
 int sm_count() {
-    static int count = 0;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
-        if (count <= 0) count = 1;
-    });
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> counts[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    const bool cached = dev >= 0 && dev < kMaxDevices;
+    if (cached) {
+        const int c = counts[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int count = 0;
+    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count <= 0) count = 1;
+    if (cached) counts[dev].store(count, std::memory_order_relaxed);
     return count;
 }
 
