@@ -299,6 +299,227 @@ def oracle_sample(n_streams: int, reps_chunks: int = L_MAIN // CHUNK, threads: i
     return n / dt, n, dt
 
 
+def oracle_timed(contexts, work, seconds: float) -> tuple[float, int, float]:
+    """Runs work(ctx) again and again on each context, one Python thread per
+    context (the oracle's C calls release the interpreter lock), until
+    `seconds` have passed; all threads start together.  work returns the units
+    it did (outputs, chunks).  Returns (units per second, units, wall s)."""
+    import concurrent.futures as cf
+
+    n = len(contexts)
+    start = threading.Barrier(n + 1)
+    units = [0] * n
+    stop_at = [0.0]
+
+    def run(i):
+        start.wait()
+        u = 0
+        while time.perf_counter() < stop_at[0]:
+            u += work(contexts[i])
+        units[i] = u
+        return time.perf_counter()
+
+    old_interval = sys.getswitchinterval()
+    sys.setswitchinterval(5e-4)  # threads returning from C calls get the interpreter lock back quickly
+    try:
+        with cf.ThreadPoolExecutor(n) as ex:
+            futs = [ex.submit(run, i) for i in range(n)]
+            t0 = time.perf_counter()
+            stop_at[0] = t0 + seconds
+            start.wait()
+            ends = [f.result() for f in futs]
+    finally:
+        sys.setswitchinterval(old_interval)
+    wall = max(ends) - t0
+    return sum(units) / wall, sum(units), wall
+
+
+def oracle_runs(tasks, threads: int) -> tuple[float, int, float]:
+    """Runs a fixed list of oracle tasks (callables returning the units each
+    did) on `threads` Python threads, longest first; returns (units per
+    second, units, wall s)."""
+    import concurrent.futures as cf
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max(1, threads)) as ex:
+        done = sum(ex.map(lambda f: f(), tasks))
+    wall = time.perf_counter() - t0
+    return done / wall, done, wall
+
+
+def cpu_baseline_leg(make_ctx, work, unit: str, sample: str, seconds: float = 2.0) -> dict:
+    """The oracle as it stands on all host cores (one context per core, each a
+    disjoint slice of the leg's workload) and on one core, time-bounded."""
+    threads = os.cpu_count() or 1
+    r, n, dt = oracle_timed([make_ctx(i, threads) for i in range(threads)], work, seconds)
+    r1, n1, dt1 = oracle_timed([make_ctx(0, threads)], work, seconds / 2)
+    return {"value": r, "unit": unit, "cores": threads, "kind": "oracle", "cpu": host_cpu(),
+            "sample": "%s; %d units in %.1f s" % (sample, n, dt),
+            "single_thread": {"value": r1, "cores": 1, "sample": "the first thread's slice, %.1f s" % dt1}}
+
+
+def cpu_fused(xl_name: str) -> dict:
+    """Oracle on the fused leg: xor-like xl, C = 32, seed 2, per core a slice
+    of 2048 of the 2^20 streams advanced 256 outputs at a time into the
+    quarter-circle counts."""
+    import oracle
+
+    oracle.build()
+    xl = {"xor128": oracle.XL_XOR128, "xor64": oracle.XL_XOR64}[xl_name]
+
+    def make(i, _n):
+        return oracle.Generator(oracle.VAR_XOR, xl, 32, SEED_MAIN, 0, S_MAIN, lane0=i * 2048, n_lanes=2048)
+
+    def work(g):
+        g.fused_qc(512)
+        return 2048 * 512
+
+    return cpu_baseline_leg(make, work, "uint32/s",
+                            "2^20 x 4096 %s workload: 2048 streams per core, quarter-circle counts" % xl_name)
+
+
+def cpu_written(variant_name: str) -> dict:
+    """Oracle on a written leg: per core a slice of whole lane groups of the
+    leg's streams, outputs stored to an array 32 (BBS variants) or 256 (naive)
+    at a time."""
+    import oracle
+
+    oracle.build()
+    if variant_name == "naive":
+        def make(i, _n):
+            return oracle.naive_init_lanes(SEED_MAIN, i * 2048, 2048)
+
+        def work(lanes):
+            oracle.naive_run(lanes, 256)
+            return 2048 * 256
+
+        sample = "2^20 x 4096 naive workload (Listing 1 per stream): 2048 streams per core, written"
+    else:
+        var = {"bbs": oracle.VAR_BBS, "bbs16": oracle.VAR_BBS16}[variant_name]
+
+        def make(i, _n):
+            return oracle.Generator(var, oracle.XL_XOR128, 32, SEED_BBS, 0, S_BBS, lane0=i * 64, n_lanes=64)
+
+        chunk = 512 if variant_name == "bbs" else 2048
+
+        def work(g):
+            g.generate(chunk)
+            return 64 * chunk
+
+        sample = "2^16 x 16384 %s workload: 64 streams per core (seeding not timed), written" % variant_name
+    return cpu_baseline_leg(make, work, "uint32/s", sample)
+
+
+_PROC_BARRIER = None
+
+
+def _proc_init(barrier):
+    global _PROC_BARRIER
+    _PROC_BARRIER = barrier
+
+
+def _bg_proc(job):
+    """One process of the Blum-Goldwasser CPU baseline: messages k0 .. k0+7 of
+    the leg's key pool, encrypted or decrypted again and again for `seconds`
+    after all processes are ready."""
+    mode, k0, total, seconds = job
+    import numpy as np
+
+    import oracle
+    from paper_1112_5239_gb300 import workloads as W
+
+    b = W.bg_batch(SEED_BG, total)
+    msgs = np.random.default_rng(SEED_BG).integers(0, 32, size=(total, 1024), dtype=np.uint8)
+    ks = list(range(k0, k0 + 8))
+    enc = {k: oracle.bg_encrypt(int(b["N"][k]), int(b["S0"][k]), int(b["r"][k]), msgs[k]) for k in ks}
+    _PROC_BARRIER.wait()
+    t0 = time.perf_counter()
+    units = 0
+    while time.perf_counter() - t0 < seconds:
+        for k in ks:
+            if mode == "encrypt":
+                oracle.bg_encrypt(int(b["N"][k]), int(b["S0"][k]), int(b["r"][k]), msgs[k])
+            else:
+                oracle.bg_decrypt(int(b["p"][k]), int(b["q"][k]), int(b["S0"][k]), enc[k][1], enc[k][0])
+        units += 8 * 1024
+    return units, time.perf_counter() - t0
+
+
+def cpu_bg() -> dict:
+    """Oracle on the Blum-Goldwasser leg: per core 8 messages of 1024 five-bit
+    chunks with keys of the leg's key pool, encrypted (and separately
+    decrypted) again and again.  One oracle call is one short message, so the
+    cores run as spawned processes, not threads."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    out = {}
+    for mode in ("encrypt", "decrypt"):
+        res = {}
+        for n in (threads, 1):
+            ctx = mp.get_context("spawn")
+            barrier = ctx.Barrier(n)
+            with cf.ProcessPoolExecutor(n, mp_context=ctx, initializer=_proc_init, initargs=(barrier,)) as ex:
+                got = list(ex.map(_bg_proc, [(mode, 8 * i, 8 * threads, 1.5) for i in range(n)]))
+            res[n] = (sum(u for u, _ in got) / max(t for _, t in got), sum(u for u, _ in got), max(t for _, t in got))
+        r, u, dt = res[threads]
+        out[mode] = {"value": r, "unit": "chunks/s", "cores": threads, "kind": "oracle", "cpu": host_cpu(),
+                     "sample": "8 messages x 1024 chunks per core (one spawned process per core), 62-bit keys of "
+                               "the leg's pool; %d chunks in %.1f s" % (u, dt),
+                     "single_thread": {"value": res[1][0], "cores": 1, "sample": "one process, %.1f s" % res[1][2]}}
+    return out
+
+
+def cpu_requests(reqs, label: str, budget_core_s: float = 24.0) -> dict:
+    """Oracle on a seeded sample of a request mix: each sampled request's first
+    warp group (up to 32 streams) over its whole length, on all host cores;
+    requests are taken in a seeded random order until their estimated oracle
+    time reaches the budget.  Seeding is not timed."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    cost = {"xor": 1.2e-8, "bbs": 5e-7}  # rough oracle seconds per output, for sizing the sample only
+    order = np.random.default_rng(11).permutation(len(reqs))
+    picked, est = [], 0.0
+    for i in order:
+        r = reqs[int(i)]
+        L = r.n_per_stream
+        c = 32 * L * cost[r.variant]
+        if est + c > budget_core_s:
+            continue
+        picked.append(int(i))
+        est += c
+    tasks = []
+    for i in picked:
+        r = reqs[i]
+        var = oracle.VAR_BBS if r.variant == "bbs" else oracle.VAR_XOR
+        g = oracle.Generator(var, oracle.XL_XOR128, 32, r.seed, r.comb_seed, r.n_streams, n_lanes=32)
+        real = min(r.n_streams, 32)
+
+        def task(g=g, L=r.n_per_stream, real=real):
+            left = L
+            while left:
+                k = min(left, 8192)
+                oracle.run(g.variant, g.xl, g.C, g.comb, g.lanes, k, want_out=False)
+                left -= k
+            return real * L
+
+        tasks.append((32 * r.n_per_stream * cost[r.variant], task))
+    tasks.sort(key=lambda t: -t[0])
+    threads = os.cpu_count() or 1
+    rate, n, dt = oracle_runs([t for _, t in tasks], threads)
+    n_bbs = sum(1 for i in picked if reqs[i].variant == "bbs")
+    return {"value": rate, "unit": "uint32/s", "cores": threads, "kind": "oracle", "cpu": host_cpu(),
+            "sample": "%s: %d requests (%d BBS), the first warp group of each over its whole length; %d outputs "
+                      "in %.1f s" % (label, len(picked), n_bbs, n, dt)}
+
+
 def host_cpu() -> str:
     """CPU model of the host (lscpu's model name, else /proc/cpuinfo)."""
     try:
@@ -477,6 +698,19 @@ def main():
             result["batched_sample"] = bench_batched_sample(torch, ci)
             result["serving_sample"] = bench_serving_sample(ci)
         if rank == 0 and world == 1:
+            # the oracle beside every leg, after all GPU timing
+            result["fused"]["cpu_baseline"] = cpu_fused("xor128")
+            result["fused_xor64"]["cpu_baseline"] = cpu_fused("xor64")
+            result["bbs"]["cpu_baseline"] = cpu_written("bbs")
+            result["bbs16"]["cpu_baseline"] = cpu_written("bbs16")
+            result["naive"]["cpu_baseline"] = cpu_written("naive")
+            result["bg"]["cpu_baseline"] = cpu_bg()
+            from paper_1112_5239_gb300.workloads import batched_requests, serving_requests
+
+            result["batched_sample"]["cpu_baseline"] = cpu_requests(
+                batched_requests(seed=4, count=2000, max_len_log2=16), "the batched sample's 2000 requests")
+            result["serving_sample"]["cpu_baseline"] = cpu_requests(
+                serving_requests(seed=5, count=5000, rate=1.0), "the serving sample's 5000 requests")
             threads = os.cpu_count() or 1
             r, n, dt = oracle_sample(args.cpu_sample_streams, threads=threads)
             r1, n1, dt1 = oracle_sample(args.cpu_sample_streams // 16)

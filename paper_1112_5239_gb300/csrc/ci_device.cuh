@@ -158,9 +158,19 @@ __host__ __device__ __forceinline__ uint64_t barrett_mu(uint64_t M) {
     return n <= 61 ? q << (61 - n) : q;
 }
 
+// 32 x 32 -> 64-bit product, one mul.wide (a single wide multiply-add on the
+// FMA-heavy pipe).
+__device__ __forceinline__ uint64_t mul_wide32(uint32_t a, uint32_t b) {
+    uint64_t r;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(r) : "r"(a), "r"(b));
+    return r;
+}
+
 struct Barrett62 {
     uint64_t M, mu;      // mu: barrett_mu(M)
     uint32_t s1, s2, t;  // n - 2; 66 - n (at most 63: below n = 4, X < 2^64 and the high half is 0); n == 62
+    uint32_t sl;         // n - 34 (limb form, n >= 34)
+    uint64_t nM;         // 2^64 - M
     __host__ __device__ __forceinline__ void set(uint64_t mod, uint64_t mu_stored) {
         M = mod;
         mu = mu_stored;
@@ -168,6 +178,8 @@ struct Barrett62 {
         s1 = n - 2;
         s2 = 66 - n < 63 ? 66 - n : 63;
         t = n == 62 ? 1u : 0u;
+        sl = n >= 34 ? n - 34 : 0u;
+        nM = 0ull - mod;
     }
     __host__ __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) const {
         const uint64_t lo = a * b, hi = mul_hi64(a, b);
@@ -176,6 +188,52 @@ struct Barrett62 {
         return r >= M ? r - M : r;
     }
     __host__ __device__ __forceinline__ uint64_t sqr(uint64_t x) const { return mul(x, x); }
+
+    // The same Barrett square on 32-bit limbs, for 34 <= n <= 62 (so the
+    // quotient input floor(X / 2^(n-2)) starts in limb 1 or above).
+    // Schoolbook products (Knuth, TAOCP 2, Alg. 4.3.1M), each one mul.wide;
+    // every carry is an explicit add-with-carry, so the products are the only
+    // work on the FMA-heavy pipe, the kernel's limiting pipe.
+    //   X = x^2 = x0^2 + 2 x0 x1 2^32 + x1^2 2^64 (x1 < 2^30, so 2 x1 fits);
+    //   q1 = X >> (n - 2): two funnel shifts by n - 34 of limbs 1..3;
+    //   q = floor(q1 mu / 2^64) >> t: all four partial products, exactly;
+    //   r = X - q M mod 2^64 (r < 2M < 2^63), then one conditional
+    //   subtraction, decided by the sign of r - M.
+    // Equal to mul(x, x) for every canonical x (checked on the host against
+    // 128-bit remainders for every n from 34 to 62, and on the GPU).
+    __device__ __forceinline__ uint64_t sqr_limb(uint64_t x) const {
+        const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+        const uint64_t p00 = mul_wide32(x0, x0), d = mul_wide32(x0, x1 + x1), p11 = mul_wide32(x1, x1);
+        uint32_t X1, X2, X3;
+        asm("add.cc.u32 %0, %3, %4;\n\t"
+            "addc.cc.u32 %1, %5, %6;\n\t"
+            "addc.u32 %2, %7, 0;"
+            : "=r"(X1), "=r"(X2), "=r"(X3)
+            : "r"((uint32_t)(p00 >> 32)), "r"((uint32_t)d), "r"((uint32_t)p11), "r"((uint32_t)(d >> 32)),
+              "r"((uint32_t)(p11 >> 32)));
+        const uint32_t q0 = __funnelshift_r(X1, X2, sl), q1 = __funnelshift_r(X2, X3, sl);
+        const uint32_t m0 = (uint32_t)mu, m1 = (uint32_t)(mu >> 32);
+        const uint32_t c00 = __umulhi(q0, m0);
+        const uint64_t c01 = mul_wide32(q0, m1), c10 = mul_wide32(q1, m0), c11 = mul_wide32(q1, m1);
+        uint32_t w2, w3;  // bits 64..127 of q1 mu
+        asm("{\n\t.reg .u32 a, b, c, a2;\n\t"
+            "add.cc.u32 a, %2, %3;\n\t"
+            "addc.cc.u32 b, %4, %5;\n\t"
+            "addc.u32 c, %6, 0;\n\t"
+            "add.cc.u32 a2, a, %7;\n\t"
+            "addc.cc.u32 %0, b, %8;\n\t"
+            "addc.u32 %1, c, 0;\n\t}"
+            : "=r"(w2), "=r"(w3)
+            : "r"(c00), "r"((uint32_t)c01), "r"((uint32_t)(c01 >> 32)), "r"((uint32_t)c11),
+              "r"((uint32_t)(c11 >> 32)), "r"((uint32_t)c10), "r"((uint32_t)(c10 >> 32)));
+        const uint32_t qa = __funnelshift_r(w2, w3, t), qb = w3 >> t;
+        const uint32_t n0 = (uint32_t)nM, n1 = (uint32_t)(nM >> 32);
+        uint64_t r = mul_wide32(qa, n0) + (((uint64_t)X1 << 32) | (uint32_t)p00);
+        const uint32_t rh = (uint32_t)(r >> 32) + qa * n1 + qb * n0;
+        r = ((uint64_t)rh << 32) | (uint32_t)r;
+        const uint64_t dm = r - M;
+        return (int32_t)(dm >> 32) < 0 ? r : dm;
+    }
 };
 
 // Blum Blum Shub strategy source (Algorithm 5 generalised to w = 5 bits per
@@ -185,10 +243,12 @@ struct SrcBbs {
     Barrett62 B;
     uint64_t y;  // BBS state, canonical in [0, M)
     uint32_t sel;
+    bool limb;  // every modulus of the warp has 34..62 bits: the limb-form square
     __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
         y = s.u64[G_Y * s.P + l];
         B.set(s.u64[G_M * s.P + l], s.u64[G_MU * s.P + l]);
         sel = s.u32[F_SEL * s.P + l];
+        limb = __all_sync(kFull, bit_length64(B.M) >= 34u);
     }
     __device__ __forceinline__ void store(const DevState &s, uint64_t l) const { s.u64[G_Y * s.P + l] = y; }
     __device__ __forceinline__ void arrays(const DevState &, uint64_t, int &a1, int &a2) const {
@@ -196,22 +256,26 @@ struct SrcBbs {
         a2 = 8 + (int)((sel >> 8) & 7u);
     }
     // One BBS output: x <- x^2 mod M (its low bits are the secure ones).
+    template <bool kLimb>
     __device__ __forceinline__ uint32_t bbs() {
-        y = B.sqr(y);
+        y = kLimb ? B.sqr_limb(y) : B.sqr(y);
         return (uint32_t)y;
     }
-    __device__ __forceinline__ uint32_t next() {
+    template <bool kLimb>
+    __device__ __forceinline__ uint32_t assemble() {
         uint32_t t = 0;
 #pragma unroll
-        for (int c = 0; c < 7; ++c) t = (t << 5) | (bbs() & 31u);
+        for (int c = 0; c < 7; ++c) t = (t << 5) | (bbs<kLimb>() & 31u);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            const uint32_t shift = bbs() & 3u;
+            const uint32_t shift = bbs<kLimb>() & 3u;
             t <<= shift;
-            t |= bbs() & ((1u << shift) - 1u);  // array_shift = {0, 1, 3, 7}
+            t |= bbs<kLimb>() & ((1u << shift) - 1u);  // array_shift = {0, 1, 3, 7}
         }
         return t;
     }
+    // `limb` is the same in every lane of the warp, so the branch never diverges.
+    __device__ __forceinline__ uint32_t next() { return limb ? assemble<true>() : assemble<false>(); }
 };
 
 // Algorithm 5 as printed: eight BBS generators per lane with moduli below
