@@ -17,7 +17,8 @@
 // so global loads and stores are 32-byte rows while each lane walks its own
 // row.  The squarings use the Barrett reduction of the BBS strategy source
 // (modulus odd, below 2^62), which keeps x_i canonical so its low bits are
-// read directly.
+// read directly; a warp whose moduli all have at least 34 bits takes its
+// limb form.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,24 +50,31 @@ __device__ __forceinline__ uint32_t bg_w(uint64_t N) {
 }
 
 // One chunk: b = x_i & mask (x_i canonical), key ^= b, x_{i+1} = x_i^2.
+// kLimb: the limb-form square (every modulus of the warp has 34..62 bits).
 struct BgLane {
     Barrett62 B;
     uint64_t x;
     uint32_t mask, key;
+    template <bool kLimb>
+    __device__ __forceinline__ uint64_t sqr(uint64_t v) const {
+        return kLimb ? B.sqr_limb(v) : B.sqr(v);
+    }
+    template <bool kLimb>
     __device__ __forceinline__ uint32_t chunk(uint32_t v) {
         key ^= (uint32_t)x & mask;
-        x = B.sqr(x);
+        x = sqr<kLimb>(x);
         return (v ^ key) & 0xFFu;
     }
     // Four chunks, one per byte of w: the keystream bytes are gathered into
     // one word and XORed in once (key < 2^8: S^0 is a byte, the b_i have at
     // most 5 bits).
+    template <bool kLimb>
     __device__ __forceinline__ uint32_t word(uint32_t w) {
         uint32_t ks = 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             key ^= (uint32_t)x & mask;
-            x = B.sqr(x);
+            x = sqr<kLimb>(x);
             ks |= key << (8 * b);
         }
         return w ^ ks;
@@ -108,6 +116,55 @@ __device__ __forceinline__ bool bg_setup_decrypt(uint64_t p, uint64_t q, uint64_
     return ok;
 }
 
+// The chunks of one warp's 32 messages (lane = message), after key setup.
+template <bool kVec, bool kLimb>
+__device__ __forceinline__ void bg_rows(BgLane &s, uint32_t keep, bool live, uint64_t msg, uint64_t m0,
+                                        uint32_t rows, uint64_t L, const uint8_t *in, uint8_t *out, uint8_t *tile,
+                                        uint8_t *row, uint32_t lane) {
+    if constexpr (kVec) {  // L a multiple of 32, rows 16-byte aligned
+        if (live) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(in + msg * L);
+            uint4 *dst = reinterpret_cast<uint4 *>(out + msg * L);
+            const uint64_t steps = L / kBgTile;
+            for (uint64_t t = 0; t < steps; ++t) {  // each step reads its 32 bytes before writing them
+                uint4 a = src[2 * t], b = src[2 * t + 1];
+                a.x = s.word<kLimb>(a.x) & keep;
+                a.y = s.word<kLimb>(a.y) & keep;
+                a.z = s.word<kLimb>(a.z) & keep;
+                a.w = s.word<kLimb>(a.w) & keep;
+                b.x = s.word<kLimb>(b.x) & keep;
+                b.y = s.word<kLimb>(b.y) & keep;
+                b.z = s.word<kLimb>(b.z) & keep;
+                b.w = s.word<kLimb>(b.w) & keep;
+                dst[2 * t] = a;
+                dst[2 * t + 1] = b;
+            }
+        }
+    } else {
+        for (uint64_t k0 = 0; k0 < L; k0 += kBgTile) {
+            const uint32_t width = L - k0 < (uint64_t)kBgTile ? (uint32_t)(L - k0) : (uint32_t)kBgTile;
+            __syncwarp();
+#pragma unroll 8
+            for (uint32_t r = 0; r < rows; ++r)
+                if (lane < width) tile[r * kBgRowPad + lane] = in[(m0 + r) * L + k0 + lane];
+            __syncwarp();
+            if (live) {
+                uint32_t *w = reinterpret_cast<uint32_t *>(row);
+                if (width == kBgTile) {
+#pragma unroll
+                    for (int j = 0; j < kBgTile / 4; ++j) w[j] = s.word<kLimb>(w[j]) & keep;
+                } else {
+                    for (uint32_t j = 0; j < width; ++j) row[j] = (uint8_t)(s.chunk<kLimb>(row[j]) & keep);
+                }
+            }
+            __syncwarp();
+#pragma unroll 8
+            for (uint32_t r = 0; r < rows; ++r)
+                if (lane < width) out[(m0 + r) * L + k0 + lane] = tile[r * kBgRowPad + lane];
+        }
+    }
+}
+
 template <bool kDecrypt, bool kVec>
 __global__ void __launch_bounds__(kBgWarps * 32, CI_BG_MIN_BLOCKS)
     k_bg(uint64_t n_msgs, uint64_t L, const uint64_t *__restrict__ key_a, const uint64_t *__restrict__ key_b,
@@ -134,48 +191,11 @@ __global__ void __launch_bounds__(kBgWarps * 32, CI_BG_MIN_BLOCKS)
             if (!ok && n_rejected) atomicAdd(n_rejected, 1u);
         }
         const uint32_t keep = ok ? 0xFFFFFFFFu : 0u;  // a rejected key's row is written as zeros
-        if constexpr (kVec) {  // L a multiple of 32, rows 16-byte aligned
-            if (live) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(in + msg * L);
-                uint4 *dst = reinterpret_cast<uint4 *>(out + msg * L);
-                const uint64_t steps = L / kBgTile;
-                for (uint64_t t = 0; t < steps; ++t) {  // each step reads its 32 bytes before writing them
-                    uint4 a = src[2 * t], b = src[2 * t + 1];
-                    a.x = s.word(a.x) & keep;
-                    a.y = s.word(a.y) & keep;
-                    a.z = s.word(a.z) & keep;
-                    a.w = s.word(a.w) & keep;
-                    b.x = s.word(b.x) & keep;
-                    b.y = s.word(b.y) & keep;
-                    b.z = s.word(b.z) & keep;
-                    b.w = s.word(b.w) & keep;
-                    dst[2 * t] = a;
-                    dst[2 * t + 1] = b;
-                }
-            }
-        } else {
-            for (uint64_t k0 = 0; k0 < L; k0 += kBgTile) {
-                const uint32_t width = L - k0 < (uint64_t)kBgTile ? (uint32_t)(L - k0) : (uint32_t)kBgTile;
-                __syncwarp();
-#pragma unroll 8
-                for (uint32_t r = 0; r < rows; ++r)
-                    if (lane < width) tile[r * kBgRowPad + lane] = in[(m0 + r) * L + k0 + lane];
-                __syncwarp();
-                if (live) {
-                    uint32_t *w = reinterpret_cast<uint32_t *>(row);
-                    if (width == kBgTile) {
-#pragma unroll
-                        for (int j = 0; j < kBgTile / 4; ++j) w[j] = s.word(w[j]) & keep;
-                    } else {
-                        for (uint32_t j = 0; j < width; ++j) row[j] = (uint8_t)(s.chunk(row[j]) & keep);
-                    }
-                }
-                __syncwarp();
-#pragma unroll 8
-                for (uint32_t r = 0; r < rows; ++r)
-                    if (lane < width) out[(m0 + r) * L + k0 + lane] = tile[r * kBgRowPad + lane];
-            }
-        }
+        // the same in every lane: the branch never diverges
+        if (__all_sync(0xFFFFFFFFu, !live || s.B.M >= (1ull << 33)))
+            bg_rows<kVec, true>(s, keep, live, msg, m0, rows, L, in, out, tile, row, lane);
+        else
+            bg_rows<kVec, false>(s, keep, live, msg, m0, rows, L, in, out, tile, row, lane);
         if (!kDecrypt && live) y_out[msg] = ok ? s.x : 0ull;
     }
 }
