@@ -596,6 +596,29 @@ ci_status ci_bg_decrypt(uint64_t n_msgs, uint64_t n_chunks, const uint64_t *p_de
 
 /* --------------------------------------------------------------- misc */
 
+/* Bounds-checked debugging build.  The paper has no counterpart: this stands
+ * in for a memory checker.  Built with -DCI_CHECKED (build.py --checked,
+ * libci_prng_checked.so), the generation, batched and split kernels check, at
+ * the start of each warp's work, that the warp group lies within the state's
+ * lanes, that the columns it writes lie within a row of the output, that
+ * 16-byte and TMA stores start on aligned columns, that a batched unit lies
+ * within its task, and that a split segment index lies within the call's
+ * segments.  A failed check records (check id << 56) | index in a status word
+ * of the device (allocated on first use; the first failure wins) and the warp
+ * skips the guarded work: nothing traps and no out-of-range access is made.
+ * Every synchronous entry point that launches those kernels (ci_generate*,
+ * ci_generate_split, ci_batch_run, ci_batch_run_noalloc) then waits for its
+ * stream, reads and clears the word, and returns CI_E_INVAL naming the check.
+ *
+ * ci_check_status: waits for cuda_stream, stores the status word in *word
+ * (0: no check failed) and clears it.  ci_check_probe: launches one warp whose
+ * check fails on purpose (no memory is touched) and returns what the
+ * epilogue reports, CI_E_INVAL, so the reporting path can be tested.
+ * Errors: CI_E_STATE in the ordinary build (the checks are compiled out
+ * there), CI_E_INVAL (word NULL), CI_E_CUDA. */
+ci_status ci_check_status(uint64_t *word, void *cuda_stream);
+ci_status ci_check_probe(void *cuda_stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char *ci_last_error(void);
 

@@ -9,7 +9,10 @@ import ctypes
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libci_prng.so")
+# CI_PRNG_CHECKED=1 selects the bounds-checked debugging build (build.py
+# build(checked=True)); it must exist then, like the ordinary one.
+CHECKED = os.environ.get("CI_PRNG_CHECKED") == "1"
+LIB_PATH = os.path.join(PKG, "libci_prng_checked.so" if CHECKED else "libci_prng.so")
 
 CI_OK, CI_PENDING = 0, 1
 CI_E_INVAL, CI_E_NOMEM, CI_E_CUDA, CI_E_BUSY, CI_E_TIMEOUT, CI_E_STATE, CI_E_CANCELED = -1, -2, -3, -4, -5, -6, -7
@@ -164,6 +167,8 @@ _SIGNATURES = {
     "ci_tune_set": [_VP],
     "ci_export_state": [_VP, _VP, _U64, _VP],
     "ci_import_state": [_VP, _VP, _U64, _VP],
+    "ci_check_status": [_VP, _VP],
+    "ci_check_probe": [_VP],
 }
 
 
@@ -172,9 +177,9 @@ def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libci_prng.so is not built (run `python -c 'import __graft_entry__ as g; "
-                              "g.build()'` or `python paper_1112_5239_gb300/build.py`); there is no CPU "
-                              "fallback")
+            raise ImportError("%s is not built (run `python -c 'import __graft_entry__ as g; g.build()'` or "
+                              "`python paper_1112_5239_gb300/build.py%s`); there is no CPU fallback"
+                              % (os.path.basename(LIB_PATH), " --checked" if CHECKED else ""))
         L = ctypes.CDLL(LIB_PATH)
         for name, args in _SIGNATURES.items():
             fn = getattr(L, name)

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "ci_device.cuh"
 #include "ci_split.h"
 #include "ci_internal.h"
 #include "ci_trace.h"
@@ -163,8 +164,83 @@ ci::DevState ci_states_s::view() const {
                                   : nullptr;
     s.P = P;
     s.S = S;
+    s.check = ci::check_word();
     return s;
 }
+
+// ------------------------------------------------- bounds-checked build
+namespace ci {
+
+#ifdef CI_CHECKED
+namespace {
+
+std::mutex g_check_mu;
+unsigned long long *g_check_words[64];  // per device, allocated on first use
+
+// The one deliberate failure: a check whose condition is false, so the status
+// path can be tested without any out-of-range access.
+__global__ void k_check_probe(DevState st) { CI_WARP_CHECK(st, false, CHK_PROBE, 0); }
+
+const char *check_name(unsigned id) {
+    switch (id) {
+        case CHK_GROUP: return "warp group beyond the state's lanes";
+        case CHK_COLS: return "written columns beyond the row length";
+        case CHK_TMA_ALIGN: return "TMA store column not a multiple of 4 words";
+        case CHK_V4_ALIGN: return "16-byte stores with unaligned columns or row length";
+        case CHK_UNIT: return "batch unit beyond its task's warp groups";
+        case CHK_SEGMENT: return "split segment index beyond the segment count";
+        case CHK_SEG_COLS: return "split segment's columns beyond the row length";
+        case CHK_PROBE: return "probe";
+        default: return "unknown check";
+    }
+}
+
+// Waits for `stream`, then reads and clears the current device's status word.
+ci_status read_clear(cudaStream_t stream, unsigned long long *value) {
+    *value = 0;
+    unsigned long long *w = check_word();
+    if (!w) return fail(CI_E_CUDA, "no bounds-check status word on this device");
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = cudaMemcpy(value, w, sizeof *value, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && *value) e = cudaMemsetAsync(w, 0, sizeof *value, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e == cudaSuccess ? CI_OK : cuda_fail(e, "bounds-check status read");
+}
+
+}  // namespace
+
+unsigned long long *check_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_check_mu);
+    if (!g_check_words[dev]) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(unsigned long long)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        g_check_words[dev] = static_cast<unsigned long long *>(p);
+    }
+    return g_check_words[dev];
+}
+
+ci_status check_epilogue(cudaStream_t stream, ci_status rc) {
+    if (rc != CI_OK) return rc;
+    unsigned long long v = 0;
+    const ci_status st = read_clear(stream, &v);
+    if (st != CI_OK) return st;
+    if (v)
+        return fail(CI_E_INVAL, std::string("bounds check failed: ") + check_name((unsigned)(v >> 56)) + " (index " +
+                                    std::to_string(v & ((1ull << 56) - 1)) + ")");
+    return CI_OK;
+}
+#else
+unsigned long long *check_word() { return nullptr; }
+ci_status check_epilogue(cudaStream_t, ci_status rc) { return rc; }
+#endif
+
+}  // namespace ci
 
 using namespace ci;
 
@@ -317,6 +393,7 @@ static ci_status check_out(ci_states s, uint64_t n, const void *out, uint64_t ca
 }
 
 ci_status ci_generate(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void *stream) {
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     TraceRange trace("ci_generate");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (s->variant != CI_VAR_XOR) return fail(CI_E_STATE, "ci_generate needs an xor-variant state (use ci_generate_bbs)");
@@ -325,12 +402,13 @@ ci_status ci_generate(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void
     if (st != CI_OK) return st;
     // A narrow state is a few serial chains: run it as time segments (identical results).
     const uint64_t K = split_auto(*s, n);
-    if (K > 1) return split_launch(*s, n, CI_SINK_WRITTEN, out, n, 0, nullptr, K, static_cast<cudaStream_t>(stream));
-    cudaError_t e = launch_generate(*s, n, out, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? CI_OK : cuda_fail(e, "generation kernel launch");
+    if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_WRITTEN, out, n, 0, nullptr, K, cs));
+    cudaError_t e = launch_generate(*s, n, out, cs);
+    return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "generation kernel launch"));
 }
 
 ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void *stream) {
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     TraceRange trace("ci_generate_bbs");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (s->variant == CI_VAR_XOR) return fail(CI_E_STATE, "ci_generate_bbs needs a BBS-variant state (use ci_generate)");
@@ -340,32 +418,34 @@ ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, 
     // Few streams leave most SMs idle on their serial squaring chains: run the
     // call as time segments instead (identical results).
     const uint64_t K = split_auto(*s, n);
-    if (K > 1) return split_launch(*s, n, CI_SINK_WRITTEN, out, n, 0, nullptr, K, static_cast<cudaStream_t>(stream));
-    cudaError_t e = launch_generate(*s, n, out, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? CI_OK : cuda_fail(e, "BBS generation kernel launch");
+    if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_WRITTEN, out, n, 0, nullptr, K, cs));
+    cudaError_t e = launch_generate(*s, n, out, cs);
+    return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "BBS generation kernel launch"));
 }
 
 ci_status ci_generate_fused_qc(ci_states s, uint64_t n, uint64_t *counts, void *stream) {
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     TraceRange trace("ci_generate_fused_qc");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (n & 1ull) return fail(CI_E_INVAL, "n_per_stream must be even (outputs are consumed in pairs)");
     if (n == 0) return CI_OK;
     if (!counts) return fail(CI_E_INVAL, "counts_dev is NULL");
     const uint64_t K = split_auto(*s, n);
-    if (K > 1) return split_launch(*s, n, CI_SINK_QC, nullptr, n, 0, counts, K, static_cast<cudaStream_t>(stream));
-    cudaError_t e = launch_fused_qc(*s, n, counts, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? CI_OK : cuda_fail(e, "fused generation kernel launch");
+    if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_QC, nullptr, n, 0, counts, K, cs));
+    cudaError_t e = launch_fused_qc(*s, n, counts, cs);
+    return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "fused generation kernel launch"));
 }
 
 ci_status ci_generate_digest(ci_states s, uint64_t n, uint64_t *digest, void *stream) {
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     TraceRange trace("ci_generate_digest");
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (n == 0) return CI_OK;
     if (!digest) return fail(CI_E_INVAL, "digest_dev is NULL");
     const uint64_t K = split_auto(*s, n);
-    if (K > 1) return split_launch(*s, n, CI_SINK_DIGEST, nullptr, n, 0, digest, K, static_cast<cudaStream_t>(stream));
-    cudaError_t e = launch_digest(*s, n, digest, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? CI_OK : cuda_fail(e, "digest kernel launch");
+    if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_DIGEST, nullptr, n, 0, digest, K, cs));
+    cudaError_t e = launch_digest(*s, n, digest, cs);
+    return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "digest kernel launch"));
 }
 
 ci_status ci_export_state(ci_states s, void *host_buf, uint64_t bytes, void *stream) {
@@ -386,6 +466,36 @@ ci_status ci_import_state(ci_states s, const void *host_buf, uint64_t bytes, voi
     if (e != cudaSuccess) return cuda_fail(e, "state import");
     std::memcpy(s->table, host_buf, kTableBytes);
     return CI_OK;
+}
+
+ci_status ci_check_status(uint64_t *word, void *stream) {
+    if (!word) return fail(CI_E_INVAL, "word is NULL");
+    *word = 0;
+#ifdef CI_CHECKED
+    unsigned long long v = 0;
+    const ci_status st = read_clear(static_cast<cudaStream_t>(stream), &v);
+    *word = v;
+    return st;
+#else
+    (void)stream;
+    return fail(CI_E_STATE, "bounds checks are compiled only into the CI_CHECKED build");
+#endif
+}
+
+ci_status ci_check_probe(void *stream) {
+#ifdef CI_CHECKED
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    DevState st{};
+    st.check = check_word();
+    if (!st.check) return fail(CI_E_CUDA, "no bounds-check status word on this device");
+    k_check_probe<<<1, 32, 0, cs>>>(st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "probe kernel launch");
+    return check_epilogue(cs, CI_OK);
+#else
+    (void)stream;
+    return fail(CI_E_STATE, "bounds checks are compiled only into the CI_CHECKED build");
+#endif
 }
 
 const char *ci_last_error(void) { return g_err.c_str(); }

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batched(BatchHeader *hdr, const 
                 hi = mid;
         }
         const BatchTask T = tasks[lo];
+        CI_WARP_CHECK(T.st, u - T.prefix < T.ngroups, CHK_UNIT, u);
         const uint64_t g = T.g0 + (u - T.prefix);
         if (T.kind == K_BBS)
             run_sink<SrcBbs>(T, g, tile);
@@ -292,7 +293,8 @@ ci_status ci_batch_run(ci_batch b, const ci_batch_item *items, uint32_t n_items,
         if (n == 0) continue;
         b->tasks.push_back(make_task(h, n, it.sink, it.out_dev, it.aux_dev, n, 0));
     }
-    return batch_launch_tasks(b, b->tasks.data(), (uint32_t)b->tasks.size(), static_cast<cudaStream_t>(cuda_stream));
+    const cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    return check_epilogue(cs, batch_launch_tasks(b, b->tasks.data(), (uint32_t)b->tasks.size(), cs));
 }
 
 ci_status ci_batch_destroy(ci_batch b) {
@@ -414,5 +416,5 @@ extern "C" ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n
     const BatchTask *dtasks = reinterpret_cast<const BatchTask *>(static_cast<unsigned char *>(d.queue) + sizeof hdr);
     k_batched<8><<<d.geo.grid, d.geo.block, 0, cs>>>(dhdr, dtasks);
     e = cudaGetLastError();
-    return e == cudaSuccess ? CI_OK : cuda_fail(e, "no-alloc batched kernel launch");
+    return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "no-alloc batched kernel launch"));
 }

@@ -24,6 +24,25 @@ namespace dev {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
+// A bounds check of the CI_CHECKED build, written where every lane of the warp
+// is converged: if `cond` fails in any lane, lane 0 records (id, index) in the
+// state's status word (the first failure wins) and the whole warp returns from
+// the enclosing function, so no lane leaves a warp-collective step early and
+// the guarded access is never made.  Compiled out otherwise.
+#ifdef CI_CHECKED
+#define CI_WARP_CHECK(st, cond, id, index)                                                             \
+    do {                                                                                              \
+        if (__any_sync(0xffffffffu, !(cond))) {                                                       \
+            if ((threadIdx.x & 31) == 0 && (st).check)                                                \
+                atomicCAS((st).check, 0ull,                                                           \
+                          ((unsigned long long)(id) << 56) | ((unsigned long long)(index) & ((1ull << 56) - 1))); \
+            return;                                                                                   \
+        }                                                                                             \
+    } while (0)
+#else
+#define CI_WARP_CHECK(st, cond, id, index) ((void)0)
+#endif
+
 // ------------------------------------------------------------------ seeding
 // splitmix64 (Steele, Lea & Flood 2014) used counter-based: draw k of lane l
 // is the (l * 2^32 + k + 1)-th output of the generator started at `seed`.
@@ -423,6 +442,9 @@ __device__ __forceinline__ void warp_task(const DevState &st, uint64_t g, uint64
                                           uint4 *tile) {
     constexpr int KT = (SINK == SINK_V4 || SINK == SINK_SCALAR) ? TC::KT : 32;
     constexpr int CH = KT / 4;
+    CI_WARP_CHECK(st, g < st.P / 32, CHK_GROUP, g);
+    if (SINK == SINK_V4 || SINK == SINK_SCALAR) CI_WARP_CHECK(st, col0 + n <= ld, CHK_COLS, col0 + n);
+    if (SINK == SINK_V4) CI_WARP_CHECK(st, (col0 | ld) % 4 == 0, CHK_V4_ALIGN, col0);
     const int lane = threadIdx.x & 31;
     const uint64_t l = g * 32 + lane;
     Src src;
@@ -556,6 +578,9 @@ __device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.prox
 template <class Src>
 __device__ __forceinline__ void warp_task_tma(const DevState &st, uint64_t g, uint64_t n, const CUtensorMap *map,
                                               uint32_t *out, uint64_t ld, uint64_t col0, uint4 *tiles) {
+    CI_WARP_CHECK(st, g < st.P / 32, CHK_GROUP, g);
+    CI_WARP_CHECK(st, col0 + n <= ld, CHK_COLS, col0 + n);
+    CI_WARP_CHECK(st, col0 % 4 == 0, CHK_TMA_ALIGN, col0);
     const int lane = threadIdx.x & 31;
     const uint64_t l = g * 32 + lane;
     Src src;

@@ -27,7 +27,30 @@ struct DevState {
     uint64_t *u64;         // field g at u64 + g * P (BBS)
     uint64_t P;            // lanes (multiple of 32)
     uint64_t S;            // streams returned
+    unsigned long long *check;  // bounds-check status word (CI_CHECKED builds), else null
 };
+
+// Bounds checks of the CI_CHECKED build.  A failed check stores
+// (id << 56) | (index & (2^56 - 1)) in the status word of the device (the
+// first failure wins) and the warp skips the work the check guards.
+enum CheckId : uint32_t {
+    CHK_GROUP = 1,      // warp group beyond the state's lanes
+    CHK_COLS = 2,       // written columns beyond the row length
+    CHK_TMA_ALIGN = 3,  // TMA store column not a multiple of 4 words
+    CHK_V4_ALIGN = 4,   // 16-byte stores with unaligned columns or row length
+    CHK_UNIT = 5,       // batch unit beyond its task's warp groups
+    CHK_SEGMENT = 6,    // split segment index beyond the segment count
+    CHK_SEG_COLS = 7,   // split segment's columns beyond the row length
+    CHK_PROBE = 8,      // the deliberate failure of ci_check_probe
+};
+
+// Status word of the current device (CI_CHECKED builds: allocated on first use;
+// otherwise null).
+unsigned long long *check_word();
+// Run by every synchronous entry point before it returns rc: in CI_CHECKED
+// builds it waits for `stream`, reads and clears the status word and turns a
+// recorded failure into CI_E_INVAL; otherwise it returns rc unchanged.
+ci_status check_epilogue(cudaStream_t stream, ci_status rc);
 
 uint64_t state_bytes_for(int variant, uint64_t P);
 

@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(512) k_split_carry(SegSpace seg, uint32_t K, u
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, NW = blockDim.x >> 5;
     const DevState s0 = seg.at(0);
     const uint64_t P = s0.P, l = g * 32 + lane;
+    CI_WARP_CHECK(s0, g < P / 32, CHK_GROUP, g);  // g = blockIdx.x: every warp of the block returns together
     Src src;
     src.load(s0, l);
     int a1, a2;
@@ -457,6 +458,9 @@ __global__ void __launch_bounds__(256) k_split_fixup(SegSpace seg, const uint2 *
     const uint64_t units = (uint64_t)(K - 1) * groups;
     for (uint64_t u = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < units; u += (uint64_t)gridDim.x * 8) {
         const uint64_t k = 1 + u / groups, g = u % groups, l = g * 32 + lane, row0 = g * 32;
+        CI_WARP_CHECK(s0, k < K && g < P / 32, CHK_SEGMENT, k);
+        CI_WARP_CHECK(s0, col0 + k * len + (k + 1 == K ? len_last : len) <= ld, CHK_SEG_COLS, k);
+        if (V4) CI_WARP_CHECK(s0, ((col0 + k * len) | ld) % 4 == 0, CHK_V4_ALIGN, k);
         Src src;
         src.load(s0, l);
         int a1, a2;
@@ -599,6 +603,7 @@ __global__ void __launch_bounds__(256, split_min_blocks<Src>()) k_split_run(SegS
     const uint64_t units = (uint64_t)(k_end - k_begin) * groups;
     for (uint64_t u = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < units; u += (uint64_t)gridDim.x * 8) {
         const uint64_t k = k_begin + u / groups, g = u % groups;
+        CI_WARP_CHECK(caller, k < K, CHK_SEGMENT, k);
         const DevState st = k != 0 ? seg.at(k) : zero < 0 ? caller : seg.at((uint64_t)zero);
         const uint64_t n = k + 1 == K ? len_last : len;
         if (SINK == SINK_V4 || SINK == SINK_SCALAR)
@@ -851,15 +856,14 @@ extern "C" ci_status ci_generate_split(ci_states h, uint64_t n, int32_t sink, vo
         return fail(CI_E_INVAL, "out_capacity is smaller than n_streams * n");
     if (sink == CI_SINK_QC && (n & 1ull)) return fail(CI_E_INVAL, "quarter-circle sink needs an even length");
     const uint64_t K = split_segments(*h, n, n_segments);
+    const cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
     if (K <= 1) {  // unsplit: one launch of the tuned single-call kernel
-        const cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
         const cudaError_t e = sink == CI_SINK_QC       ? launch_fused_qc(*h, n, static_cast<uint64_t *>(out_dev), cs)
                               : sink == CI_SINK_DIGEST ? launch_digest(*h, n, static_cast<uint64_t *>(out_dev), cs)
                                                        : launch_generate(*h, n, static_cast<uint32_t *>(out_dev), cs);
-        return e == cudaSuccess ? CI_OK : cuda_fail(e, "unsplit generation kernel launch");
+        return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "unsplit generation kernel launch"));
     }
     if (sink == CI_SINK_WRITTEN)
-        return split_launch(*h, n, sink, static_cast<uint32_t *>(out_dev), n, 0, nullptr, K,
-                            (cudaStream_t)cuda_stream);
-    return split_launch(*h, n, sink, nullptr, n, 0, static_cast<uint64_t *>(out_dev), K, (cudaStream_t)cuda_stream);
+        return check_epilogue(cs, split_launch(*h, n, sink, static_cast<uint32_t *>(out_dev), n, 0, nullptr, K, cs));
+    return check_epilogue(cs, split_launch(*h, n, sink, nullptr, n, 0, static_cast<uint64_t *>(out_dev), K, cs));
 }

@@ -195,3 +195,13 @@ def test_binding_rejects_host_tensors_without_gpu():
         st.generate_digest(8, digest=torch.zeros(4, dtype=torch.int64))
     with pytest.raises(TypeError):
         st.generate_split(8, sink="digest", out=torch.zeros(4, dtype=torch.int64))
+
+
+def test_ordinary_build_reports_checks_compiled_out_without_gpu(L):
+    # the bounds checks exist only in the CI_CHECKED build; the ordinary
+    # library answers before touching CUDA
+    w = ctypes.c_uint64(9)
+    assert L.lib().ci_check_status(ctypes.byref(w), None) == L.CI_E_STATE and w.value == 0
+    assert b"CI_CHECKED" in L.lib().ci_last_error()
+    assert L.lib().ci_check_status(None, None) == L.CI_E_INVAL
+    assert L.lib().ci_check_probe(None) == L.CI_E_STATE
