@@ -40,7 +40,7 @@ S_BBS, L_BBS, SEED_BBS = 1 << 16, 1 << 14, 3
 SEED_BG = 6
 STATE_BYTES_PER_LANE_XOR128 = 24      # a, b, c, d, x, slot: read once and written once per launch
 FALLBACK_HBM_GBS = 6800.0
-GPU_SM_COUNT_NOMINAL = 152
+PIPES_JSON = os.path.join(ROOT, "profiles", "ncu_pipes.json")
 
 
 def parse_args():
@@ -56,7 +56,8 @@ def parse_args():
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
-    ap.add_argument("--profile", choices=["written", "fused", "bbs", "bbs_split", "bbs16", "batched", "bg", "naive"],
+    ap.add_argument("--profile", choices=["written", "fused", "fused_xor64", "bbs", "bbs_split", "bbs16", "batched",
+                                          "bg", "bg_dec", "naive"],
                     default=None,
                     help="small case for ncu: autotune, 2 warm-up launches, then 1 launch of one kernel inside "
                          "the NVTX range 'profile'; no timing")
@@ -65,10 +66,12 @@ def parse_args():
 
 def run_profile_case(kind: str) -> None:
     """Small case for profiler captures: 2^19 streams x 256 written (512 MiB,
-    larger than L2), 2^19 x 4096 fused, 2^16 x 1024 BBS written (256 MiB; unsplit),
-    2^16 x 4096 BBS written (1 GiB; run as time segments), or
-    one batched launch of 300 uneven requests; two warm-up launches and one
-    more of the same kernel inside the NVTX range "profile"."""
+    larger than L2), 2^19 x 4096 fused (xor128 or xor64), 2^16 x 1024 BBS
+    written (256 MiB; unsplit), 2^16 x 4096 BBS written (1 GiB; run as time
+    segments), Algorithm 5 as printed or the naive generator, Blum-Goldwasser
+    encryption or decryption of 2^18 messages, or one batched launch of 300
+    uneven requests; two warm-up calls and one more inside the NVTX range
+    "profile"."""
     import torch
 
     from paper_1112_5239_gb300 import build as libbuild
@@ -82,8 +85,8 @@ def run_profile_case(kind: str) -> None:
         st = ci.States(1 << 19, seed=SEED_MAIN)
         out = torch.empty((1 << 19, CHUNK), dtype=torch.int32, device="cuda")
         run = lambda: st.generate(CHUNK, out=out)  # noqa: E731
-    elif kind == "fused":
-        st = ci.States(1 << 19, seed=SEED_MAIN)
+    elif kind in ("fused", "fused_xor64"):
+        st = ci.States(1 << 19, seed=SEED_MAIN, xl="xor64" if kind == "fused_xor64" else "xor128")
         counts = torch.zeros(1 << 19, dtype=torch.int64, device="cuda")
         run = lambda: st.generate_fused_qc(L_MAIN, counts=counts)  # noqa: E731
     elif kind == "bbs":
@@ -98,15 +101,19 @@ def run_profile_case(kind: str) -> None:
         st = ci.States(S_BBS, variant="bbs16", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
         run = lambda: st.generate(1024, out=out)  # noqa: E731
-    elif kind == "bg":  # chaotic Blum-Goldwasser encryption, 2^18 messages x 1024 chunks (256 MiB each way)
+    elif kind in ("bg", "bg_dec"):  # chaotic Blum-Goldwasser, 2^18 messages x 1024 chunks (256 MiB each way)
         from paper_1112_5239_gb300 import workloads as W
 
         b = W.bg_batch(SEED_BG, 1 << 18)
-        N, r = torch.from_numpy(b["N"]).cuda(), torch.from_numpy(b["r"]).cuda()
-        S0 = torch.from_numpy(b["S0"]).cuda()
+        dev = {k: torch.from_numpy(v).cuda() for k, v in b.items()}
         msg = torch.randint(0, 32, (1 << 18, 1024), dtype=torch.uint8, device="cuda")
         c, y = torch.empty_like(msg), torch.empty(1 << 18, dtype=torch.int64, device="cuda")
-        run = lambda: ci.bg_encrypt(N, S0, r, msg, out=c, y=y)  # noqa: E731
+        back = torch.empty_like(msg)
+        ci.bg_encrypt(dev["N"], dev["S0"], dev["r"], msg, out=c, y=y)
+        if kind == "bg":
+            run = lambda: ci.bg_encrypt(dev["N"], dev["S0"], dev["r"], msg, out=c, y=y)  # noqa: E731
+        else:
+            run = lambda: ci.bg_decrypt(dev["p"], dev["q"], dev["S0"], y, c, out=back)  # noqa: E731
     elif kind == "naive":  # Listing 1 per stream (Algorithm 3), 2^19 streams x 256 written (512 MiB)
         st = ci.NaiveStates(1 << 19, seed=SEED_MAIN)
         out = torch.empty((1 << 19, CHUNK), dtype=torch.int32, device="cuda")
@@ -234,6 +241,52 @@ def kernel_source_hash() -> str:
         with open(os.path.join(ROOT, "paper_1112_5239_gb300", "csrc", name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
+
+
+def library_source_hash() -> str:
+    """Hash of every library source file: a pipe profile taken on other
+    sources no longer describes the kernels."""
+    import glob
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1112_5239_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                       glob.glob(os.path.join(csrc, "*.h")) + [os.path.join(ROOT, "include", "ci_prng.h")]):
+        with open(path, "rb") as f:
+            h.update(os.path.basename(path).encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def pipe_roofline(leg: str, value: float, unit: str, clocks: dict, sms: int) -> dict:
+    """Roofline of a compute-bound leg from its committed ncu profile
+    (profiles/ncu_pipes.json).  For each resource X (instruction issue, the
+    ALU, FMA-heavy, FMA-lite and LSU pipes) the profile holds b_X, the SM
+    cycles X is busy per output over all kernels of the call (busy fraction x
+    duration x SM clock / outputs).  At the live rate the busy fraction of X is
+    value x b_X x (profiled SMs / live SMs) / live SM clock; the bound is the
+    busiest resource, and its peak the rate at which it would be busy all the
+    time.  The fractions are null once the library sources differ from the
+    profiled ones."""
+    try:
+        with open(PIPES_JSON) as f:
+            d = json.load(f)[leg]
+    except (OSError, KeyError, ValueError):
+        return {"bound": "alu", "achieved": value, "peak": None, "unit": unit, "frac": None, "traffic": None,
+                "note": "no pipe profile for this leg"}
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    fresh = d.get("source_hash") == library_source_hash()
+    if not mhz or not fresh:
+        return {"bound": "alu", "achieved": value, "peak": None, "unit": unit, "frac": None, "traffic": None,
+                "note": "profile taken on other library sources" if not fresh else "no SM clock sample",
+                "profile": d.get("summary")}
+    scale = d["sms"] / (mhz * 1e6 * sms)
+    fr = {x: value * b * scale for x, b in d["busy_cycles_per_output"].items()}
+    pipe = max(fr, key=fr.get)
+    return {"bound": "alu", "pipe": pipe, "achieved": value, "peak": value / fr[pipe], "unit": unit,
+            "frac": fr[pipe], "traffic": None, "busy": fr, "issue_frac": fr.get("issue"),
+            "inst_per_output": d.get("inst_per_output"), "sm_mhz": mhz, "sms": sms,
+            "peak_source": "ncu busy cycles per output (%s) at the sampled SM clock and this GPU's SM count"
+                           % d.get("summary")}
 
 
 def ncu_traffic(kernel_key: str):
@@ -694,6 +747,14 @@ def main():
         result["bg"] = bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["split"] = bench_split(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank)
         result["naive"] = bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_ranks, world)
+        # counter-derived rooflines of the compute-bound legs (per GPU)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        for leg in ("fused", "fused_xor64", "bbs", "bbs16", "naive"):
+            r = result[leg]
+            r["roofline"] = pipe_roofline(leg, r["value"] / world, "uint32/s", r.get("clocks"), sms)
+        for leg, key in (("bg", "encrypt"), ("bg_dec", "decrypt")):
+            r = result["bg"][key]
+            r["roofline"] = pipe_roofline(leg, r["value"] / world, "chunks/s", result["bg"].get("clocks"), sms)
         if rank == 0 and world == 1:
             result["batched_sample"] = bench_batched_sample(torch, ci)
             result["serving_sample"] = bench_serving_sample(ci)
@@ -735,6 +796,8 @@ def bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
         st.generate_fused_qc(L_MAIN, counts=counts)
     barrier_sync()
     evs = []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.fill_(1)  # evict the 24 MB state from L2 between steps
@@ -745,20 +808,14 @@ def bench_fused(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
         evs.append((a, b))
     torch.cuda.nvtx.range_pop()
     barrier_sync()
+    clk = clocks.stop()
     kms = [a.elapsed_time(b) for a, b in evs]
     ms = max_over_ranks(statistics.mean(kms))
     value = world * S_MAIN * L_MAIN / (ms / 1e3)
-    # integer lane-ops per output (xor128 7, mixing 2 shuffles + 2 xor, CI 1,
-    # quarter-circle 8 per pair); peak: 152 SMs x 128 lanes x max SM clock.
-    ops = 7 + 4 + 1 + 4
-    peak = GPU_SM_COUNT_NOMINAL * 128 * 2.07e9
     st.free()
     return {"value": value, "unit": "uint32/s", "ms_per_step": ms,
             "workload": "same 2^20 x 4096 streams, outputs consumed in-kernel by the quarter-circle counter",
-            "roofline": {"bound": "alu", "achieved": ops * value / world / 1e9, "peak": peak / 1e9,
-                         "unit": "Gop/s", "frac": ops * value / world / peak, "ops_per_output": ops,
-                         "peak_source": "152 SMs x 128 int lanes/clk x 2.07 GHz"},
-            "l2": "256 MiB flush between steps"}
+            "l2": "256 MiB flush between steps", "clocks": clk}
 
 
 def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, rank):
@@ -769,6 +826,8 @@ def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world,
         st.generate(L_BBS, out=out)
     barrier_sync()
     evs = []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     torch.cuda.nvtx.range_push("timed")
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -778,11 +837,12 @@ def bench_bbs(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world,
         evs.append((a, b))
     torch.cuda.nvtx.range_pop()
     barrier_sync()
+    clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
     value = world * S_BBS * L_BBS / (ms / 1e3)
     del out
     st.free()
-    return {"value": value, "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
+    return {"clocks": clk, "value": value, "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
             "workload": "BBS-driven CI PRNG (Alg. 5, 62-bit Blum moduli, 11 Barrett squarings per output,"
                         " C=32, seed 3): 2^16 streams x 16384, written (4 GiB per launch)",
             "modsq_per_s": 11 * value}
@@ -797,6 +857,8 @@ def bench_fused_xor64(torch, ci, args, dev, stream, first, barrier_sync, max_ove
         st.generate_fused_qc(L_MAIN, counts=counts)
     barrier_sync()
     evs = []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -806,9 +868,10 @@ def bench_fused_xor64(torch, ci, args, dev, stream, first, barrier_sync, max_ove
         evs.append((a, b))
     torch.cuda.nvtx.range_pop()
     barrier_sync()
+    clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
     st.free()
-    return {"value": world * S_MAIN * L_MAIN / (ms / 1e3), "unit": "uint32/s", "ms_per_step": ms,
+    return {"clocks": clk, "value": world * S_MAIN * L_MAIN / (ms / 1e3), "unit": "uint32/s", "ms_per_step": ms,
             "workload": "2^20 x 4096, xor64 as the Algorithm 4 xor-like, outputs consumed by the quarter-circle counter"}
 
 
@@ -822,6 +885,8 @@ def bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, worl
         st.generate(L_BBS, out=out)
     barrier_sync()
     evs = []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     torch.cuda.nvtx.range_push("timed")
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -831,11 +896,12 @@ def bench_bbs16(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, worl
         evs.append((a, b))
     torch.cuda.nvtx.range_pop()
     barrier_sync()
+    clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
     value = world * S_BBS * L_BBS / (ms / 1e3)
     del out
     st.free()
-    return {"value": value, "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
+    return {"clocks": clk, "value": value, "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
             "workload": "Algorithm 5 as printed (8 BBS per stream, Blum primes in [128, 256), 4 bits per squaring, "
                         "12 squarings per output, C=32, seed 3): 2^16 streams x 16384, written",
             "modsq_per_s": 12 * value}
@@ -868,6 +934,8 @@ def bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, 
         dec()
     barrier_sync()
     ev_e, ev_d = [], []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     torch.cuda.nvtx.range_push("timed")
     for _ in range(steps):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -880,12 +948,13 @@ def bench_bg(torch, ci, args, dev, stream, barrier_sync, max_over_ranks, world, 
         ev_d.append((evs[1], evs[2]))
     torch.cuda.nvtx.range_pop()
     barrier_sync()
+    clk = clocks.stop()
     ms_e = max_over_ranks(statistics.mean(a.elapsed_time(b_) for a, b_ in ev_e))
     ms_d = max_over_ranks(statistics.mean(a.elapsed_time(b_) for a, b_ in ev_d))
     ok = bool(torch.equal(back, msg))
     del msg, cipher, back
     chunks = world * n * L
-    return {"unit": "chunks/s", "bits_per_chunk": 5,
+    return {"clocks": clk, "unit": "chunks/s", "bits_per_chunk": 5,
             "encrypt": {"value": chunks / (ms_e / 1e3), "ms_per_step": ms_e},
             "decrypt": {"value": chunks / (ms_d / 1e3), "ms_per_step": ms_d},
             "steps": steps, "round_trip_ok": ok,
@@ -905,6 +974,8 @@ def bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
     barrier_sync()
     steps = max(1, min(args.steps, 5))
     evs = []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     torch.cuda.nvtx.range_push("timed")
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -915,9 +986,10 @@ def bench_naive(torch, ci, args, dev, stream, first, barrier_sync, max_over_rank
         evs.append((a, b))
     torch.cuda.nvtx.range_pop()
     barrier_sync()
+    clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
     del out
-    return {"value": world * S_MAIN * L_MAIN / (ms / 1e3), "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
+    return {"clocks": clk, "value": world * S_MAIN * L_MAIN / (ms / 1e3), "unit": "uint32/s", "ms_per_step": ms, "steps": steps,
             "workload": "Listing 1 run by each of 2^20 streams (Algorithm 3: three 64-bit xor-likes, no mixing), "
                         "4096 outputs each in 16 written launches of 256"}
 
