@@ -1058,7 +1058,8 @@ def bench_serving_sample(ci):
     rate = 0.5 * sat["steady_req_per_s"]
     srv, _, half = _serving_run(ci, [dataclasses.replace(r, arrival=r.arrival / rate) for r in base], 64)
     srv.close()
-    keys = ("value", "req_per_s", "steady_value", "steady_req_per_s", "p50_ms", "p99_ms", "split_jobs", "ok")
+    keys = ("value", "req_per_s", "steady_value", "steady_req_per_s", "p50_ms", "p99_ms", "split_jobs", "ok",
+            "slowest_1pct")
     return {"workload": "5000 requests of the serving mix (seed 5: lognormal sizes, median 2^16, sigma 2, cap 2^28; "
                         "30% continuations; 80% xor128 / 20% BBS), 64 GiB arena",
             "saturation": {k: sat[k] for k in keys},
@@ -1308,7 +1309,22 @@ def _serving_run(ci, reqs, arena_gib, hold=None, **cfg):
     t10, t90 = done[order[k10]], done[order[k90]]
     mid_out = sum(reqs[i].n_streams * reqs[i].n_per_stream for i in order[k10 + 1:k90 + 1])
     steady_s = max((t90 - t10) / 1e9, 1e-9)
+    # what the slowest 1 % of requests are: time before admission against time
+    # from admission to completion, and their kind and size
+    admit = np.array([r.admit_ns for r in results], dtype=np.float64)
+    slow = np.argsort(lat_ms)[-max(1, len(reqs) // 100):]
+    tail = {"requests": int(len(slow)),
+            "median_wait_ms": float(np.median((admit[slow] - submit[slow]) / 1e6)),
+            "median_service_ms": float(np.median((done[slow] - admit[slow]) / 1e6)),
+            "bbs_frac": float(np.mean([reqs[i].variant == "bbs" for i in slow])),
+            "continuation_frac": float(np.mean([reqs[i].continues >= 0 for i in slow])),
+            "median_outputs": float(np.median([reqs[i].n_streams * reqs[i].n_per_stream for i in slow])),
+            "median_len": float(np.median([reqs[i].n_per_stream for i in slow])),
+            "median_streams": float(np.median([reqs[i].n_streams for i in slow])),
+            "all_median_wait_ms": float(np.median((admit - submit) / 1e6)),
+            "all_median_service_ms": float(np.median((done - admit) / 1e6))}
     return srv, results, {"ok": ok, "requests": len(reqs), "outputs": n_out, "seconds": span, "wall_s": wall,
+                          "slowest_1pct": tail,
                           "value": n_out / span, "req_per_s": len(reqs) / span,
                           "steady_value": mid_out / steady_s, "steady_req_per_s": (k90 - k10) / steady_s,
                           "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),

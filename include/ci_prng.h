@@ -438,8 +438,13 @@ ci_status ci_server_destroy(ci_server server);
  *     residue, BBS state), 1 M (odd, bit length n <= 62), 2 the Barrett
  *     reciprocal floor(2^(2n+1) / M), shifted left by 61 - n when n <= 61.
  * Importing replaces the state of a handle with the same parameters and
- * n_streams; an imported BBS state must hold y < M and the reciprocal of M.
- * Errors: CI_E_INVAL (size mismatch), CI_E_CUDA. */
+ * n_streams.  Every lane of an imported CI_VAR_BBS state must hold M = p q of
+ * 33 to 62 bits (the lengths for which Algorithm 5 takes w = 5 bits per
+ * squaring, as the kernels do), y < M and the reciprocal of M; every
+ * generator of a CI_VAR_BBS16 state a modulus in [3, 2^16) and a state below
+ * it.  The host checks this before copying anything.
+ * Errors: CI_E_INVAL (size mismatch, or a lane that breaks those rules; the
+ * handle's state is then unchanged), CI_E_CUDA. */
 ci_status ci_export_state(ci_states states, void *host_buf, uint64_t bytes, void *cuda_stream);
 ci_status ci_import_state(ci_states states, const void *host_buf, uint64_t bytes,
                           void *cuda_stream);

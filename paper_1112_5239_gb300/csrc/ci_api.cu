@@ -457,9 +457,38 @@ ci_status ci_export_state(ci_states s, void *host_buf, uint64_t bytes, void *str
     return e == cudaSuccess ? CI_OK : cuda_fail(e, "state export");
 }
 
+// The per-lane rules an imported state must follow (see ci_import_state).
+static ci_status check_import(const ci_states_s &h, const uint8_t *buf) {
+    const uint64_t P = h.P;
+    const uint32_t *u32 = reinterpret_cast<const uint32_t *>(buf + kTableBytes);
+    if (h.variant == CI_VAR_BBS) {
+        const uint64_t *u64 = reinterpret_cast<const uint64_t *>(buf + kTableBytes + 4ull * kU32Fields * P);
+        for (uint64_t l = 0; l < P; ++l) {
+            const uint64_t y = u64[G_Y * P + l], M = u64[G_M * P + l], mu = u64[G_MU * P + l];
+            const uint64_t p = u32[F_P * P + l], q = u32[F_Q * P + l];
+            const uint32_t n = M ? dev::bit_length64(M) : 0;
+            if (n < 33 || n > 62 || !(M & 1ull) || p * q != M)
+                return fail(CI_E_INVAL, "imported BBS lane " + std::to_string(l) + ": M must be p q of 33 to 62 bits");
+            if (y >= M || mu != dev::barrett_mu(M))
+                return fail(CI_E_INVAL, "imported BBS lane " + std::to_string(l) + ": y >= M or a wrong reciprocal");
+        }
+    } else if (h.variant == CI_VAR_BBS16) {
+        for (uint64_t l = 0; l < P; ++l)
+            for (int g = 0; g < 8; ++g) {
+                const uint32_t y = u32[(F_Y16 + g) * P + l], M = u32[(F_M16 + g) * P + l];
+                if (M < 3 || M >= (1u << 16) || y >= M)
+                    return fail(CI_E_INVAL, "imported Algorithm 5 lane " + std::to_string(l) +
+                                                ": a modulus outside [3, 2^16) or a state above it");
+            }
+    }
+    return CI_OK;
+}
+
 ci_status ci_import_state(ci_states s, const void *host_buf, uint64_t bytes, void *stream) {
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (!host_buf || bytes != s->bytes) return fail(CI_E_INVAL, "host_buf NULL or bytes != state_bytes");
+    const ci_status chk = check_import(*s, static_cast<const uint8_t *>(host_buf));
+    if (chk != CI_OK) return chk;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(s->dev, host_buf, bytes, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);

@@ -262,7 +262,8 @@ struct SrcBbs {
     Barrett62 B;
     uint64_t y;  // BBS state, canonical in [0, M)
     uint32_t sel;
-    bool limb;  // every modulus of the warp has 34..62 bits: the limb-form square
+    bool limb;  // every modulus of the warp has 34..62 bits (all seeded ones): the limb-form square;
+                // otherwise (33-bit imported moduli) the generic one
     __device__ __forceinline__ void load(const DevState &s, uint64_t l) {
         y = s.u64[G_Y * s.P + l];
         B.set(s.u64[G_M * s.P + l], s.u64[G_MU * s.P + l]);
