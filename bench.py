@@ -243,17 +243,19 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def library_source_hash() -> str:
-    """Hash of every library source file: a pipe profile taken on other
-    sources no longer describes the kernels."""
-    import glob
+# Sources that define the compute-bound legs' kernels and their launch shapes.
+PIPE_SOURCES = ("ci_device.cuh", "ci_gen.cuh", "ci_gen_bbs.cu", "ci_gen_bbs16.cu", "ci_gen_xor128.cu",
+                "ci_gen_xor64.cu", "ci_gen_xs32.cu", "ci_split.cu", "ci_split.h", "ci_bg.cu", "ci_modarith.cuh",
+                "ci_naive.cu", "ci_internal.h", "ci_kernels.cu", "ci_tune.cu", "ci_tune.h")
 
+
+def library_source_hash() -> str:
+    """Hash of the sources of the compute legs' kernels: a pipe profile taken
+    on other sources no longer describes them."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1112_5239_gb300", "csrc")
-    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
-                       glob.glob(os.path.join(csrc, "*.h")) + [os.path.join(ROOT, "include", "ci_prng.h")]):
-        with open(path, "rb") as f:
-            h.update(os.path.basename(path).encode() + f.read())
+    for name in PIPE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1112_5239_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -265,7 +267,7 @@ def pipe_roofline(leg: str, value: float, unit: str, clocks: dict, sms: int) -> 
     duration x SM clock / outputs).  At the live rate the busy fraction of X is
     value x b_X x (profiled SMs / live SMs) / live SM clock; the bound is the
     busiest resource, and its peak the rate at which it would be busy all the
-    time.  The fractions are null once the library sources differ from the
+    time.  The fractions are null once those kernels' sources differ from the
     profiled ones."""
     try:
         with open(PIPES_JSON) as f:
@@ -1323,6 +1325,22 @@ def _serving_run(ci, reqs, arena_gib, hold=None, **cfg):
             "median_streams": float(np.median([reqs[i].n_streams for i in slow])),
             "all_median_wait_ms": float(np.median((admit - submit) / 1e6)),
             "all_median_service_ms": float(np.median((done - admit) / 1e6))}
+    # the request just ahead of each slow continuation in its stream set
+    # (requests of one stream set run in submission order)
+    root, ahead, last = [], [], {}
+    for i, r in enumerate(reqs):
+        root.append(i if r.continues < 0 else root[r.continues])
+        ahead.append(last.get(root[i], -1))
+        last[root[i]] = i
+    prev = [ahead[i] for i in slow if ahead[i] >= 0]
+    if prev:
+        tail.update({
+            "ahead_median_outputs": float(np.median([reqs[j].n_streams * reqs[j].n_per_stream for j in prev])),
+            "ahead_median_len": float(np.median([reqs[j].n_per_stream for j in prev])),
+            "ahead_median_service_ms": float(np.median([(done[j] - admit[j]) / 1e6 for j in prev])),
+            "ahead_bbs_frac": float(np.mean([reqs[j].variant == "bbs" for j in prev])),
+            "ahead_done_to_admit_ms": float(np.median([(admit[i] - done[ahead[i]]) / 1e6 for i in slow
+                                                       if ahead[i] >= 0]))})
     return srv, results, {"ok": ok, "requests": len(reqs), "outputs": n_out, "seconds": span, "wall_s": wall,
                           "slowest_1pct": tail,
                           "value": n_out / span, "req_per_s": len(reqs) / span,
