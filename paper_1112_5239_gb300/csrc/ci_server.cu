@@ -58,6 +58,8 @@ struct Req {
     uint32_t waves;     // waves in flight holding a slice of it
     bool split;         // runs as one split job
     bool cancel;        // ci_cancel was called while it was admitted
+    uint64_t handed_to; // the next request of its stream set, admitted before this one finished
+    uint64_t early_of;  // while its predecessor runs: the request that handed it the stream set
 };
 
 // Requests of at most this many warp groups may run as split jobs, at most
@@ -186,12 +188,16 @@ bool valid_server(const ci_server s) { return s && s->magic == kServerMagic; }
 void finish_request(ci_server_s *s, uint64_t t, ci_status status) {  // under lock
     Req &q = s->reqs[t];
     const bool held_states = q.state == RQ_ACTIVE;  // only an admitted request holds its streams
+    const uint64_t next = held_states ? q.handed_to : 0;  // already admitted: the stream set passes to it
+    // admitted early and finishing (cancelled) while its predecessor still
+    // runs: the predecessor keeps the stream set's turn
+    const uint64_t pred = held_states && q.early_of && s->reqs[q.early_of].state == RQ_ACTIVE ? q.early_of : 0;
     q.state = status == CI_OK ? RQ_DONE : RQ_FAILED;
     q.status = status;
     q.t_done = now_ns();
     auto sit = s->states.find(q.root);
     if (held_states && sit != s->states.end()) {
-        sit->second.busy = false;
+        if (!next && !pred) sit->second.busy = false;
         if (status != CI_OK) sit->second.poisoned = true;  // advanced part-way: continuations fail
     }
     if (status != CI_OK && q.out) {
@@ -204,6 +210,24 @@ void finish_request(ci_server_s *s, uint64_t t, ci_status status) {  // under lo
         last->active_idx = q.active_idx;
         s->active.pop_back();
     }
+    if (s->feed_completed) s->completed.push_back(t);
+    if (status == CI_OK) s->st.completed++;
+    s->admit_dirty = true;
+    if (next) {
+        // Handed over: the next request holds the stream set's turn already
+        // (behind q's own predecessor, if that one still runs).  q can only
+        // fail here through its last wave's launch, and then the next request
+        // has no slice queued yet: it fails as well.
+        Req &n = s->reqs[next];
+        n.early_of = pred;
+        if (pred) s->reqs[pred].handed_to = next;
+        if (status != CI_OK && n.state == RQ_ACTIVE && n.waves == 0) finish_request(s, next, CI_E_STATE);
+        return;
+    }
+    if (pred) {
+        s->reqs[pred].handed_to = 0;  // it passes the turn on itself when it finishes
+        return;
+    }
     Chain &ch = s->chains[q.root];
     if (!ch.waiting.empty()) {
         s->ready.push_back(ch.waiting.front());
@@ -211,9 +235,6 @@ void finish_request(ci_server_s *s, uint64_t t, ci_status status) {  // under lo
     } else {
         ch.busy = false;
     }
-    s->admit_dirty = true;
-    if (status == CI_OK) s->st.completed++;
-    if (s->feed_completed) s->completed.push_back(t);
 }
 
 void retire_front(ci_server_s *s) {
@@ -347,6 +368,39 @@ void admit(ci_server_s *s) {  // under lock
     s->init_slot ^= 1;
 }
 
+// Whether an admitted request would run as one split job (see build_wave).
+bool split_candidate(const ci_server_s *s, const Req &q) {
+    const uint64_t slice = q.variant == CI_VAR_BBS16 ? q.L
+                           : q.variant == CI_VAR_BBS ? s->cfg.slice_bbs
+                                                     : s->cfg.slice_xor;
+    const uint64_t measure = q.variant == CI_VAR_BBS16 ? s->cfg.slice_bbs : slice;
+    return (q.S + 31) / 32 <= kSplitMaxGroups && q.L / measure >= s->cfg.split_min_slices;
+}
+
+// Early admission of the next request of q's stream set (under lock): only
+// for a request that runs in waves (a split job runs on its own stream, which
+// would not wait for q's last wave), with a slot and arena room free now.
+// Not when its admission could fail the request (a released or poisoned
+// stream set, the injected admission fault): that would pass the stream
+// set's turn on while q still runs.
+void handover(ci_server_s *s, Req &q) {
+    if (q.split || q.cancel || q.handed_to || s->faults.reject_admit) return;
+    Chain &ch = s->chains[q.root];
+    if (ch.waiting.empty() || s->active.size() >= s->cfg.max_slots) return;
+    auto sit = s->states.find(q.root);
+    if (sit == s->states.end() || sit->second.released || sit->second.poisoned) return;
+    const uint64_t nt = ch.waiting.front();
+    Req &n = s->reqs[nt];
+    if (n.state != RQ_PENDING || split_candidate(s, n)) return;
+    ch.waiting.pop_front();
+    if (!admit_one(s, nt)) {  // no room now: it is admitted after q finishes, as before
+        ch.waiting.push_front(nt);
+        return;
+    }
+    q.handed_to = nt;
+    n.early_of = q.ticket;
+}
+
 void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vector<SplitJob> &splits) {
     // under lock
     for (Req *qp : s->active) {
@@ -382,6 +436,13 @@ void build_wave(ci_server_s *s, std::vector<BatchTask> &tasks, Wave &w, std::vec
         w.members.push_back(q.ticket);
         if (q.enq == q.L) w.finishing.push_back(q.ticket);
     }
+    // A request whose last slice is in this wave hands its stream set to the
+    // next request of the set at once (after the loop: admission appends to
+    // `active`).  Waves run in order on one stream, so the next request's
+    // first slice, in the next wave, starts from the state this one leaves;
+    // otherwise it would wait for this wave to finish and then for a wave
+    // already queued behind it.
+    for (uint64_t t : w.finishing) handover(s, s->reqs[t]);
 }
 
 // Split jobs run on their own streams, up to kSplitSlots at a time, so that

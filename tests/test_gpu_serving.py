@@ -82,6 +82,28 @@ def test_continuation_chain_equals_uninterrupted(env):
     srv.close()
 
 
+def test_continuation_taken_into_the_wave_after_its_predecessor(env):
+    """A continuation queued behind the request it continues is admitted as
+    soon as that request's last slice is queued, before it completes: its
+    first slice runs in the next wave on the same stream, which starts from
+    the state the predecessor leaves.  Over a chain of one-slice requests the
+    outputs equal the uninterrupted streams, and admissions come before the
+    predecessor's completion."""
+    torch, ci = env
+    for variant, slice_kw in (("xor", {"slice_xor": 64}), ("bbs", {"slice_bbs": 64})):
+        srv = ci.Server(64 << 20, **slice_kw)
+        t = [srv.submit(64, 96, variant=variant, seed=11)]  # 96 streams x 64
+        for _ in range(8):
+            t.append(srv.submit(64, continue_ticket=t[0]))
+        res = [srv.wait(x) for x in t]
+        assert all(r.status == 0 for r in res)
+        outs = np.concatenate([u32(srv.output(r)) for r in res], axis=1)
+        assert np.array_equal(outs, _oracle_rows(variant, 11, 96, 64 * 9)), variant
+        early = sum(res[i + 1].admit_ns < res[i].done_ns for i in range(8))
+        assert early >= 4, early
+        srv.close()
+
+
 def test_admission_bounded_by_arena(env):
     """A 3 MiB arena and 1 MiB outputs: requests wait for memory released by
     earlier ones; every request completes and the peak stays in the arena."""
