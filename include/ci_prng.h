@@ -302,7 +302,11 @@ ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, voi
  *    slice_bbs outputs per stream) into one launch of the batched persistent
  *    kernel (a CUDA graph replay);
  *  - keeps up to two waves in flight, so requests that arrive while others
- *    are on the GPU join the next wave.
+ *    are on the GPU join the next wave;
+ *  - admits the next request of a stream set as soon as the request before
+ *    it has its last slice queued, so that its first slice runs in the next
+ *    wave (waves run in order, so it starts from the state the earlier
+ *    request leaves).
  * Slicing a stream over waves is exact: each result equals the one-call
  * result whether the request runs alone or in any mix.  (CI_VAR_BBS16, whose
  * outputs depend on call boundaries, runs each request as one slice: one
