@@ -311,7 +311,7 @@ ci_status ci_batch_run_noalloc(const ci_batch_item *items, uint32_t n_items, voi
  * result whether the request runs alone or in any mix.  (CI_VAR_BBS16, whose
  * outputs depend on call boundaries, runs each request as one slice: one
  * call.)  Long requests over few streams run instead as one time-parallel
- * split job (see ci_generate_split), up to four at a time, each on its own
+ * split job (see ci_generate_split), up to sixteen at a time, each on its own
  * side stream beside the waves, with the same results.  New stream sets are
  * seeded in one launch per admission pass on another side stream.  Stream
  * state stays resident in the arena between requests; a request may continue

@@ -63,9 +63,10 @@ struct Req {
 };
 
 // Requests of at most this many warp groups may run as split jobs, at most
-// kSplitSlots of them at a time.
+// kSplitSlots of them at a time (measured on the serving mix: 16 slots against
+// 4 and 8 cut p99 from 75 % load up, with the same saturation throughput).
 constexpr uint64_t kSplitMaxGroups = 16;
-constexpr int kSplitSlots = 4;
+constexpr int kSplitSlots = 16;
 
 // A request run whole as one time-parallel split job (captured under the lock).
 struct SplitJob {
