@@ -239,3 +239,27 @@ def test_binding_buffer_checks(env):
     b.close()
     # the state did not move: the next outputs are the first ones
     assert np.array_equal(u32(st.generate(8)), oracle_gen("xor", "xor128", 32, 1, 0, 10).streams(8))
+
+
+@pytest.mark.parametrize("variant,xl", [("xor", "xor128"), ("xor", "xor64"), ("bbs", "xor128")])
+@pytest.mark.parametrize("S", [96, 90])
+def test_last_streams_of_the_index_range(env, variant, xl, S):
+    """The seeding draws of stream s are the counter-based indices s * 2^32 + k,
+    and first_stream + n_streams may reach 2^32.  The last 96 streams, and 90
+    streams whose padding lanes end at the last index, equal the oracle's
+    lanes there; one stream past the range is refused before anything runs."""
+    torch, ci = env
+    import oracle
+
+    L, C = 70, 32
+    first = 2**32 - 96  # a multiple of 32, as first_stream must be
+    st = ci.States(S, variant=variant, xl=xl, comb_size=C, seed=7, first_stream=first)
+    out = u32(st.generate(L))
+    var = oracle.VAR_BBS if variant == "bbs" else oracle.VAR_XOR
+    xli = {"xor128": oracle.XL_XOR128, "xor64": oracle.XL_XOR64}[xl]
+    lanes = oracle.init_lanes(var, xli, 7, first, 96)
+    ref, _ = oracle.run(var, xli, C, oracle.comb_arrays(var, C, 0), lanes, L)
+    assert np.array_equal(out, ref[:S])
+    with pytest.raises(ci.CIError) as e:
+        ci.States(97, variant=variant, xl=xl, comb_size=C, seed=7, first_stream=first)
+    assert e.value.status == -1
