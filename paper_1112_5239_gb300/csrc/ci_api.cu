@@ -401,7 +401,7 @@ ci_status ci_generate(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, void
     ci_status st = check_out(s, n, out, cap);
     if (st != CI_OK) return st;
     // A narrow state is a few serial chains: run it as time segments (identical results).
-    const uint64_t K = split_auto(*s, n);
+    const uint64_t K = split_auto(*s, n, CI_SINK_WRITTEN);
     if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_WRITTEN, out, n, 0, nullptr, K, cs));
     cudaError_t e = launch_generate(*s, n, out, cs);
     return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "generation kernel launch"));
@@ -417,7 +417,7 @@ ci_status ci_generate_bbs(ci_states s, uint64_t n, uint32_t *out, uint64_t cap, 
     if (st != CI_OK) return st;
     // Few streams leave most SMs idle on their serial squaring chains: run the
     // call as time segments instead (identical results).
-    const uint64_t K = split_auto(*s, n);
+    const uint64_t K = split_auto(*s, n, CI_SINK_WRITTEN);
     if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_WRITTEN, out, n, 0, nullptr, K, cs));
     cudaError_t e = launch_generate(*s, n, out, cs);
     return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "BBS generation kernel launch"));
@@ -430,7 +430,7 @@ ci_status ci_generate_fused_qc(ci_states s, uint64_t n, uint64_t *counts, void *
     if (n & 1ull) return fail(CI_E_INVAL, "n_per_stream must be even (outputs are consumed in pairs)");
     if (n == 0) return CI_OK;
     if (!counts) return fail(CI_E_INVAL, "counts_dev is NULL");
-    const uint64_t K = split_auto(*s, n);
+    const uint64_t K = split_auto(*s, n, CI_SINK_QC);
     if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_QC, nullptr, n, 0, counts, K, cs));
     cudaError_t e = launch_fused_qc(*s, n, counts, cs);
     return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "fused generation kernel launch"));
@@ -442,7 +442,7 @@ ci_status ci_generate_digest(ci_states s, uint64_t n, uint64_t *digest, void *st
     if (!valid_handle(s)) return fail(CI_E_STATE, "not a live ci_states handle");
     if (n == 0) return CI_OK;
     if (!digest) return fail(CI_E_INVAL, "digest_dev is NULL");
-    const uint64_t K = split_auto(*s, n);
+    const uint64_t K = split_auto(*s, n, CI_SINK_DIGEST);
     if (K > 1) return check_epilogue(cs, split_launch(*s, n, CI_SINK_DIGEST, nullptr, n, 0, digest, K, cs));
     cudaError_t e = launch_digest(*s, n, digest, cs);
     return check_epilogue(cs, e == cudaSuccess ? CI_OK : cuda_fail(e, "digest kernel launch"));

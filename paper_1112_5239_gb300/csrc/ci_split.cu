@@ -17,19 +17,27 @@
 //      powers for the xor-likes, x <- x^(2^(11 k len) mod lambda(M)) for BBS,
 //      each of the eight 16-bit generators by its own squaring count for
 //      Algorithm 5 as printed) and (s, x) = (0, 0) for k >= 1;
-//   2. pass 1 (k_split_run): written outputs of the BBS sources (62-bit and
-//      Algorithm 5 as printed): every segment from there
-//      into its output columns; otherwise segments 0 .. K-2 into a digest
-//      sink (only their end states are needed);
-//   3. k_split_carry: one block per warp group scans the segments: the true
-//      start of segment k is its predecessor's particular end plus
-//      (Q s_a, x_a ^ S s_a) with Q = P^len, S = P + ... + P^len (a chunked
-//      parallel scan over up to 16 warps);
-//   4. written BBS-source outputs: k_split_fixup XORs each segment's homogeneous
-//      part into its outputs (the mixing step with zero own words: two
-//      shuffles per output); otherwise pass 2 (k_split_run) runs every
-//      segment from its true start, with the own words k_split_setup jumped
-//      to, into the sink;
+//   2. written outputs of the BBS sources (62-bit and Algorithm 5 as
+//      printed), where generation is the cost, with many warp groups:
+//      k_split_run_fix runs every segment from there into its output
+//      columns, and as soon as a segment and its predecessor's true end are
+//      done, XORs the segment's homogeneous part into its outputs (the
+//      mixing step with zero own words: two shuffles per output), which also
+//      gives the segment's true end; the fix-ups overlap the other segments'
+//      generation;
+//   3. the same with few warp groups, where one serial chain of fix-ups per
+//      group would outlast the generation: pass 1 (k_split_run) into the
+//      output columns, the carry scan of step 4 (true starts only), then
+//      k_split_fixup runs all fix-ups at once;
+//   4. otherwise (xor-like outputs are cheaper to generate again than to
+//      read back, and consumer sinks have no outputs to fix): pass 1
+//      (k_split_run) runs segments 0 .. K-2 into a digest sink (only their
+//      end states are needed); k_split_carry, one block per warp group,
+//      scans the segments: the true start of segment k is its predecessor's
+//      particular end plus (Q s_a, x_a ^ S s_a) with Q = P^len,
+//      S = P + ... + P^len (a chunked parallel scan over up to 16 warps);
+//      pass 2 (k_split_run) runs every segment from its true start, with the
+//      own words k_split_setup jumped to, into the sink;
 //   5. the last segment's end state becomes the caller's state, and the
 //      per-segment quarter-circle counts or digests are combined.
 #include <cuda_runtime.h>
@@ -438,13 +446,78 @@ __global__ void __launch_bounds__(512) k_split_carry(SegSpace seg, uint32_t K, u
     }
 }
 
-// Written sink: segments k >= 1 wrote their particular outputs (zero start).
-// From the true start (s_a, x_a), the homogeneous part is h <- P h,
+// Written sink: segment k >= 1 wrote its particular outputs (zero start).
+// From its true start c = (s_a, x_a), the homogeneous part is h <- P h,
 // acc <- acc ^ h per iteration (two shuffles, as in the mixing step with a
-// zero own word); output i of the segment gets acc XORed in.  Work unit =
-// (segment k >= 1, warp group g); the warp stages 32 iterations of its 32
-// rows in the swizzled tile and updates the outputs as 16-byte row segments
-// (V4) or words.  The last segment also corrects its end state.
+// zero own word); output i of the segment gets acc XORed in.  The warp stages
+// 32 iterations of its 32 rows in the swizzled tile and updates the outputs
+// as 16-byte row segments (V4) or words.  Another warp wrote those outputs,
+// so they are read through L2 (ld.global.cg).  Returns H(c) = (h, acc) at the
+// segment's end.
+template <bool V4>
+__device__ __forceinline__ uint2 fix_segment(uint2 c, int p1, int p2, uint64_t n, uint32_t *base, uint64_t row0,
+                                             uint64_t S, uint64_t ld, uint4 *tile) {
+    const int lane = threadIdx.x & 31;
+    uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
+    uint32_t h = c.x, acc = c.y;
+    auto step = [&]() {
+        h = __shfl_sync(kFull, h, p1) ^ __shfl_sync(kFull, h, p2);
+        acc ^= h;
+        return acc;
+    };
+    const uint64_t nfull = n - n % 32;
+    for (uint64_t i0 = 0; i0 < nfull; i0 += 32) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint4 f;
+            f.x = step();
+            f.y = step();
+            f.z = step();
+            f.w = step();
+            tile[lane * 8 + (q ^ (lane & 7))] = f;
+        }
+        __syncwarp();
+        if (V4) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int r = 4 * kk + lane / 8, cc = lane % 8;
+                if (row0 + r < S) {
+                    uint4 *p = reinterpret_cast<uint4 *>(base + (row0 + r) * ld + i0 + 4 * cc);
+                    const uint4 v = tile[r * 8 + (cc ^ (r & 7))];
+                    uint4 o = __ldcg(p);
+                    o.x ^= v.x;
+                    o.y ^= v.y;
+                    o.z ^= v.z;
+                    o.w ^= v.w;
+                    store16<0>(reinterpret_cast<uint32_t *>(p), o);
+                }
+            }
+        } else {
+            for (int r = 0; r < 32; ++r)
+                if (row0 + r < S) {
+                    uint32_t *p = base + (row0 + r) * ld + i0 + lane;
+                    *p = __ldcg(p) ^ tw[tile_word<32>(r, lane)];
+                }
+        }
+        __syncwarp();
+    }
+    const int rem = (int)(n - nfull);
+    if (rem) {
+        for (int kk = 0; kk < rem; ++kk) tw[tile_word<32>(lane, kk)] = step();
+        __syncwarp();
+        for (int r = 0; r < 32; ++r)
+            if (lane < rem && row0 + r < S) {
+                uint32_t *p = base + (row0 + r) * ld + nfull + lane;
+                *p = __ldcg(p) ^ tw[tile_word<32>(r, lane)];
+            }
+        __syncwarp();
+    }
+    return make_uint2(h, acc);
+}
+
+// The fix-ups as a kernel of their own, after pass 1 and the carry scan:
+// work unit = (segment k >= 1, warp group g), all independent; the last
+// segment also corrects its end state.
 template <class Src, bool V4>
 __global__ void __launch_bounds__(256) k_split_fixup(SegSpace seg, const uint2 *starts, uint32_t K, uint64_t len,
                                                      uint64_t len_last, uint64_t groups, uint32_t *out, uint64_t ld,
@@ -452,12 +525,11 @@ __global__ void __launch_bounds__(256) k_split_fixup(SegSpace seg, const uint2 *
     __shared__ uint4 tiles[8][256];
     const int lane = threadIdx.x & 31;
     uint4 *tile = tiles[threadIdx.x >> 5];
-    uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
     const DevState s0 = seg.at(0);
-    const uint64_t P = s0.P, S = s0.S;
+    const uint64_t P = s0.P;
     const uint64_t units = (uint64_t)(K - 1) * groups;
     for (uint64_t u = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < units; u += (uint64_t)gridDim.x * 8) {
-        const uint64_t k = 1 + u / groups, g = u % groups, l = g * 32 + lane, row0 = g * 32;
+        const uint64_t k = 1 + u / groups, g = u % groups, l = g * 32 + lane;
         CI_WARP_CHECK(s0, k < K && g < P / 32, CHK_SEGMENT, k);
         CI_WARP_CHECK(s0, col0 + k * len + (k + 1 == K ? len_last : len) <= ld, CHK_SEG_COLS, k);
         if (V4) CI_WARP_CHECK(s0, ((col0 + k * len) | ld) % 4 == 0, CHK_V4_ALIGN, k);
@@ -465,61 +537,12 @@ __global__ void __launch_bounds__(256) k_split_fixup(SegSpace seg, const uint2 *
         src.load(s0, l);
         int a1, a2;
         src.arrays(s0, l, a1, a2);
-        const int p1 = s0.table[a1 * 32 + lane], p2 = s0.table[a2 * 32 + lane];
-        const uint2 st = starts[k * P + l];
-        uint32_t h = st.x, acc = st.y;
-        auto step = [&]() {
-            h = __shfl_sync(kFull, h, p1) ^ __shfl_sync(kFull, h, p2);
-            acc ^= h;
-            return acc;
-        };
-        const uint64_t n = k + 1 == K ? len_last : len;
-        uint32_t *base = out + col0 + k * len;
-        const uint64_t nfull = n - n % 32;
-        for (uint64_t i0 = 0; i0 < nfull; i0 += 32) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                uint4 f;
-                f.x = step();
-                f.y = step();
-                f.z = step();
-                f.w = step();
-                tile[lane * 8 + (q ^ (lane & 7))] = f;
-            }
-            __syncwarp();
-            if (V4) {
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const int r = 4 * kk + lane / 8, c = lane % 8;
-                    if (row0 + r < S) {
-                        uint4 *p = reinterpret_cast<uint4 *>(base + (row0 + r) * ld + i0 + 4 * c);
-                        const uint4 v = tile[r * 8 + (c ^ (r & 7))];
-                        uint4 o = *p;
-                        o.x ^= v.x;
-                        o.y ^= v.y;
-                        o.z ^= v.z;
-                        o.w ^= v.w;
-                        store16<0>(reinterpret_cast<uint32_t *>(p), o);
-                    }
-                }
-            } else {
-                for (int r = 0; r < 32; ++r)
-                    if (row0 + r < S) base[(row0 + r) * ld + i0 + lane] ^= tw[tile_word<32>(r, lane)];
-            }
-            __syncwarp();
-        }
-        const int rem = (int)(n - nfull);
-        if (rem) {
-            for (int kk = 0; kk < rem; ++kk) tw[tile_word<32>(lane, kk)] = step();
-            __syncwarp();
-            for (int r = 0; r < 32; ++r)
-                if (lane < rem && row0 + r < S) base[(row0 + r) * ld + nfull + lane] ^= tw[tile_word<32>(r, lane)];
-            __syncwarp();
-        }
+        const uint2 hk = fix_segment<V4>(starts[k * P + l], s0.table[a1 * 32 + lane], s0.table[a2 * 32 + lane],
+                                         k + 1 == K ? len_last : len, out + col0 + k * len, g * 32, s0.S, ld, tile);
         if (k + 1 == K) {
             const DevState d = seg.at(K - 1);
-            d.u32[F_SLOT * P + l] ^= h;
-            d.u32[F_X * P + l] ^= acc;
+            d.u32[F_SLOT * P + l] ^= hk.x;
+            d.u32[F_X * P + l] ^= hk.y;
         }
     }
 }
@@ -577,6 +600,14 @@ __global__ void __launch_bounds__(256) k_split_combine(const uint64_t *r, uint64
 constexpr uint32_t kMaxSegments = kSplitMaxSegments;
 constexpr uint64_t kMinSegment = 256;       // iterations per segment (auto choice, BBS)
 constexpr uint64_t kMinAutoSegment = 1024;  // ... xor-likes, and when a single call splits on its own
+// Written BBS-source outputs take the one-launch fix-up form from this many
+// warp groups per SM on: its fix-ups run as one serial chain per group among
+// the squaring warps, which keeps pace only with enough groups; below it,
+// pass 1, the carry scan and the fix-ups run as three launches.
+#ifndef CI_ONE_LAUNCH_GROUPS_PER_SM
+#define CI_ONE_LAUNCH_GROUPS_PER_SM 12
+#endif
+constexpr uint64_t kOneLaunchGroupsPerSm = CI_ONE_LAUNCH_GROUPS_PER_SM;
 
 // One pass over segments [k_begin, k_end): work unit u is segment
 // k_begin + u / groups, warp group u % groups, run for its length (len, the
@@ -628,6 +659,102 @@ cudaError_t launch_split_run(const SegSpace &sp, const DevState &caller, int zer
     const int blocks = (int)std::min<uint64_t>((units + 7) / 8, (uint64_t)sm_count() * per_sm);
     k_split_run<Src, SINK><<<blocks, 256, 0, stream>>>(sp, caller, zero, kb, ke, K, len, len_last, groups, out, ld,
                                                        col0, aux);
+    return cudaGetLastError();
+}
+
+// Written BBS-source outputs, fix-up form, in one launch.  Work units are the
+// pass-1 units (segment k, warp group g), taken from a device counter in
+// segment-major order.  Fix-up (g, k), k >= 1, needs two events: pass 1 of
+// (g, k) has written its particular outputs and end e_k, and the true start
+// c_k of segment k is known.  c_1 is the end of segment 0 (which ran from the
+// true state), and c_(k+1) = e_k ^ H(c_k), which fix-up (g, k) produces
+// itself by running the homogeneous recurrence through the segment, so the
+// carry needs no matrix powers.  Each event adds one to events[k groups + g];
+// the warp whose addition makes it two runs the fix-up at once, then goes on
+// to the group's next segment while that one's pass 1 is already done.  No
+// warp waits for another, and the fix-ups' memory traffic overlaps the other
+// warps' squarings.  The last segment's fix-up corrects the call's end state.
+
+// Adds one to the event count *ev once the earlier writes of every lane are
+// visible device-wide (the release half of the pattern); true in every lane
+// when this addition made the count two, the other event's writes then being
+// visible to the warp's L2 reads (the acquire half).
+__device__ __forceinline__ bool second_event(uint32_t *ev) {
+    __threadfence();
+    __syncwarp();
+    uint32_t old = 0;
+    if ((threadIdx.x & 31) == 0) old = atomicAdd(ev, 1u);
+    old = __shfl_sync(kFull, old, 0);
+    __threadfence();
+    return old == 1u;
+}
+
+template <class Src, int SINK>
+__global__ void __launch_bounds__(256, split_min_blocks<Src>()) k_split_run_fix(SegSpace seg, uint32_t K, uint64_t len,
+                                                       uint64_t len_last, uint64_t groups, uint32_t *out, uint64_t ld,
+                                                       uint64_t col0, uint2 *starts, uint32_t *events,
+                                                       unsigned long long *next_unit) {
+    __shared__ uint4 tiles[8][256];
+    uint4 *tile = tiles[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const DevState s0 = seg.at(0);
+    const uint64_t P = s0.P, units = (uint64_t)K * groups;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(next_unit, 1ull);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= units) return;
+        uint64_t k = u / groups;
+        const uint64_t g = u % groups, l = g * 32 + lane;
+        const DevState st = seg.at(k);
+        warp_task<Src, SINK>(st, g, k + 1 == K ? len_last : len, out, ld, col0 + k * len, nullptr, tile);
+        if (k == 0) {  // the same threads stored segment 0's end: c_1
+            starts[P + l] = make_uint2(st.u32[F_SLOT * P + l], st.u32[F_X * P + l]);
+            k = 1;
+        }
+        int p1 = -1, p2 = -1;
+        while (second_event(events + k * groups + g)) {
+            CI_WARP_CHECK(s0, k < K && g < P / 32, CHK_SEGMENT, k);
+            CI_WARP_CHECK(s0, col0 + k * len + (k + 1 == K ? len_last : len) <= ld, CHK_SEG_COLS, k);
+            if (SINK == SINK_V4) CI_WARP_CHECK(s0, ((col0 + k * len) | ld) % 4 == 0, CHK_V4_ALIGN, k);
+            if (p1 < 0) {
+                Src src;
+                src.load(s0, l);
+                int a1, a2;
+                src.arrays(s0, l, a1, a2);
+                p1 = s0.table[a1 * 32 + lane];
+                p2 = s0.table[a2 * 32 + lane];
+            }
+            const uint2 hk = fix_segment<SINK == SINK_V4>(__ldcg(starts + k * P + l), p1, p2,
+                                                          k + 1 == K ? len_last : len, out + col0 + k * len, g * 32,
+                                                          s0.S, ld, tile);
+            const DevState d = seg.at(k);
+            const uint32_t ts = __ldcg(d.u32 + F_SLOT * P + l) ^ hk.x, tx = __ldcg(d.u32 + F_X * P + l) ^ hk.y;
+            if (k + 1 == K) {
+                d.u32[F_SLOT * P + l] = ts;
+                d.u32[F_X * P + l] = tx;
+                break;
+            }
+            starts[(k + 1) * P + l] = make_uint2(ts, tx);
+            ++k;
+        }
+    }
+}
+
+template <class Src, int SINK>
+cudaError_t launch_split_run_fix(const SegSpace &sp, uint32_t K, uint64_t len, uint64_t len_last, uint64_t groups,
+                                 uint32_t *out, uint64_t ld, uint64_t col0, uint2 *starts, uint32_t *events,
+                                 unsigned long long *next_unit, cudaStream_t stream) {
+    static int per_sm = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_split_run_fix<Src, SINK>, 256, 0);
+        if (per_sm <= 0) per_sm = 1;
+    });
+    const uint64_t units = (uint64_t)K * groups;
+    const int blocks = (int)std::min<uint64_t>((units + 7) / 8, (uint64_t)sm_count() * per_sm);
+    k_split_run_fix<Src, SINK><<<blocks, 256, 0, stream>>>(sp, K, len, len_last, groups, out, ld, col0, starts, events,
+                                                           next_unit);
     return cudaGetLastError();
 }
 
@@ -698,19 +825,31 @@ uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested) {
     return (n + len - 1) / len;
 }
 
-uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n) {
-    const uint64_t groups = h.P / 32;
-    const uint64_t target = (uint64_t)sm_count() * 128;  // about two waves of resident BBS warps
-    if (h.variant != CI_VAR_BBS || groups * 2 > target) return 1;
-    uint64_t K = std::min<uint64_t>(target / groups, std::max<uint64_t>(1, n / kMinAutoSegment));
+uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n, int sink) {
+    if (h.variant != CI_VAR_BBS) return 1;
+    const uint64_t groups = h.P / 32, sms = (uint64_t)sm_count();
+    uint64_t K;
+    if (sink == CI_SINK_WRITTEN) {
+        // Measured on 2^9 .. 2^13 warp groups of 2^12 .. 2^15 iterations:
+        // about ten waves of resident warps (40 per SM) in the one-launch
+        // form, four in the three-launch form; segments of at least 256.
+        K = groups >= kOneLaunchGroupsPerSm * sms ? (400 * sms + groups / 2) / groups : 160 * sms / groups;
+        K = std::min<uint64_t>(K, n / kMinSegment);
+    } else {
+        // Consumer sinks generate twice (pass 1, then pass 2 from the true
+        // starts): only states that fill less than about two waves.
+        const uint64_t target = sms * 128;
+        if (groups * 2 > target) return 1;
+        K = std::min<uint64_t>(target / groups, std::max<uint64_t>(1, n / kMinAutoSegment));
+    }
     K = std::min<uint64_t>(K, kMaxSegments);
     if (K <= 1) return 1;
     const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;
     return (n + len - 1) / len;
 }
 
-uint64_t split_auto(const ci_states_s &h, uint64_t n) {
-    if (h.variant == CI_VAR_BBS) return split_auto_bbs(h, n);
+uint64_t split_auto(const ci_states_s &h, uint64_t n, int sink) {
+    if (h.variant == CI_VAR_BBS) return split_auto_bbs(h, n, sink);
     const uint64_t groups = h.P / 32, sms = (uint64_t)sm_count();
     // xor-likes: only states with no more warp groups than SMs (measured:
     // 4-11x faster up to 128 groups, slower from 512 groups on, where the
@@ -787,14 +926,43 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
                                                                        own, lam16);
     if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split setup");
 
-    uint2 *starts = reinterpret_cast<uint2 *>(res1);  // K * P (slot, x) pairs, after pass 1
-    if (st == CI_OK) {  // pass 1: particular solutions (fix-up: all segments, into their columns)
+    if (st == CI_OK && fixup && groups >= kOneLaunchGroupsPerSm * (uint64_t)sm_count()) {
+        // one launch: pass 1 with the fix-ups folded in; then the final state
+        uint2 *starts = reinterpret_cast<uint2 *>(res1);  // true starts (slot, x) of segments 1 .. K-1
+        unsigned long long *next_unit = reinterpret_cast<unsigned long long *>(res3);
+        uint32_t *events = reinterpret_cast<uint32_t *>(next_unit + 1);  // K * groups counts
+        const bool v4 = (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && ld % 4 == 0 && col0 % 4 == 0;
+        const uint32_t k32 = (uint32_t)K;
+        if ((e = cudaMemsetAsync(res3, 0, 8 + 4 * K * groups, stream)) == cudaSuccess) {
+            if (bbs)
+                e = v4 ? launch_split_run_fix<SrcBbs, SINK_V4>(sp, k32, len, len_last, groups, out, ld, col0, starts,
+                                                               events, next_unit, stream)
+                       : launch_split_run_fix<SrcBbs, SINK_SCALAR>(sp, k32, len, len_last, groups, out, ld, col0,
+                                                                   starts, events, next_unit, stream);
+            else
+                e = v4 ? launch_split_run_fix<SrcBbs16Seg, SINK_V4>(sp, k32, len, len_last, groups, out, ld, col0,
+                                                                    starts, events, next_unit, stream)
+                       : launch_split_run_fix<SrcBbs16Seg, SINK_SCALAR>(sp, k32, len, len_last, groups, out, ld, col0,
+                                                                        starts, events, next_unit, stream);
+        }
+        if (e == cudaSuccess) {
+            k_split_copy_back<<<split_block_count(h->P), 256, 0, stream>>>(src, segs[K - 1].view(), h->variant);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) st = cuda_fail(e, "split pass 1 with fix-ups");
+        cudaFreeAsync(ws, stream);
+        return st;
+    }
+    // pass 1: particular solutions (fix-up: all segments, into their columns;
+    // otherwise segments 0 .. K-2, of which only the end states are needed)
+    if (st == CI_OK) {
         e = fixup ? split_run(*h, sink, sp, 0, 0, (uint32_t)K, (uint32_t)K, len, len_last, out, ld, col0, nullptr,
                               stream)
                   : split_run(*h, CI_SINK_DIGEST, sp, 0, 0, (uint32_t)K - 1, (uint32_t)K, len, len_last, nullptr, 0,
                               0, res1, stream);
         if (e != cudaSuccess) st = cuda_fail(e, "split pass 1");
     }
+    uint2 *starts = reinterpret_cast<uint2 *>(res1);  // K * P (slot, x) pairs, after pass 1
     if (st == CI_OK) {
         const unsigned threads = 32u * (unsigned)std::min<uint64_t>(16, K - 1);
         if (bbs)

@@ -17,14 +17,18 @@ constexpr uint32_t kSplitMaxSegments = 8192;
 // 1 means unsplit.
 uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested);
 
-// Segment count ci_generate_bbs uses on its own: > 1 only for CI_VAR_BBS
+// Segment count ci_generate_bbs (and the BBS consumer calls) use on their
+// own for CI_VAR_BBS states, 1 for others.  Written sink: from the GPU size
+// and the form split_launch takes (one launch from 12 warp groups per SM on,
+// three launches below); consumer sinks, which generate twice: > 1 only for
 // states that fill less than about two waves of resident warps.
-uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n);
+uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n, int sink);
 
-// Segment count the single-call entry points use on their own: split_auto_bbs
-// for CI_VAR_BBS; for xor-like states only with no more warp groups than SMs
-// (and segments of at least 1024 iterations); 1 otherwise.
-uint64_t split_auto(const ci_states_s &h, uint64_t n);
+// Segment count the single-call entry points use on their own for `sink`
+// (CI_SINK_*): split_auto_bbs for CI_VAR_BBS; for xor-like states only with
+// no more warp groups than SMs (and segments of at least 1024 iterations);
+// 1 otherwise.
+uint64_t split_auto(const ci_states_s &h, uint64_t n, int sink);
 
 // n iterations of h as K segments into `sink` (written: out[r * ld + col0 + i];
 // consumers: aux[r]), with results equal to one sequential call.  Calls on

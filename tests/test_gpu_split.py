@@ -134,3 +134,46 @@ def test_one_segment_is_the_unsplit_call():
         assert np.array_equal(u32(st.generate_split(n, segments=1)), orc.streams(n))
         d = st.generate_split(n, sink="digest", segments=1).cpu().numpy().view(np.uint64)
         assert np.array_equal(d, digest_rows(orc.streams(n)))
+
+
+@pytest.mark.parametrize("variant", ["bbs", "bbs16"])
+def test_written_word_stores(variant):
+    """Written outputs that cannot take 16-byte stores go through the word
+    path of generation and fix-up alike: an odd row length, and an output
+    that starts one word past a 16-byte boundary.  Both equal the oracle, and
+    the state continues exactly."""
+    torch, ci = cuda_or_skip()
+    S, C = 40, 8
+    for n, offset in ((301, 0), (320, 1)):
+        seed = 31 + n + offset
+        st = _states(ci, variant, "xor128", C, seed, S)
+        orc = oracle_gen(variant, "xor128", C, seed, seed + 7, S)
+        buf = torch.zeros(S * n + 4, dtype=torch.int32, device="cuda")
+        out = buf[offset:offset + S * n]
+        st.generate_split(n, out=out, segments=5)
+        assert np.array_equal(u32(out).reshape(S, n), orc.streams(n)), (n, offset)
+        assert not buf[:offset].any() and not buf[offset + S * n:].any()  # nothing outside the output
+        assert np.array_equal(u32(st.generate(40)), orc.streams(40))
+
+
+@pytest.mark.parametrize("variant,n", [("bbs", 200), ("bbs", 201), ("bbs16", 200)])
+def test_many_groups_one_launch_form(variant, n):
+    """With many warp groups (2^17 - 8 streams: 4096 groups, the last one
+    ragged), written BBS-source outputs take the one-launch form, whose
+    fix-ups run inside the generation launch as each segment's predecessor
+    completes.  Every output and the whole end state equal one unsplit
+    launch's, sampled groups equal the oracle, and the next call continues
+    exactly.  n = 201 takes the word-store path."""
+    torch, ci = cuda_or_skip()
+    S, C, seed = (1 << 17) - 8, 32, 41
+    st = _states(ci, variant, "xor128", C, seed, S)
+    ref = _states(ci, variant, "xor128", C, seed, S)
+    out = st.generate_split(n, segments=4)
+    assert torch.equal(out, ref.generate_split(n, segments=1))
+    assert np.array_equal(st.export_state(), ref.export_state())
+    for g in (0, 1, 2047, S // 32):  # S // 32: the ragged last group
+        orc = oracle_gen(variant, "xor128", C, seed, seed + 7, S, lane0=32 * g, n_lanes=32)
+        rows = u32(out[32 * g: 32 * g + 32])
+        assert np.array_equal(rows, orc.streams(n)), g
+        assert np.array_equal(u32(st.generate(40)[32 * g: 32 * g + 32]), orc.streams(40)), g
+        st.import_state(ref.export_state())  # back to the state after the split call
