@@ -67,8 +67,9 @@ def parse_args():
 def run_profile_case(kind: str) -> None:
     """Small case for profiler captures: 2^19 streams x 256 written (512 MiB,
     larger than L2), 2^19 x 4096 fused (xor128 or xor64), 2^16 x 1024 BBS
-    written (256 MiB; unsplit), 2^16 x 4096 BBS written (1 GiB; run as time
-    segments), Algorithm 5 as printed or the naive generator, Blum-Goldwasser
+    written (256 MiB; one unsplit launch), the benchmark's BBS call (2^16 x
+    16384 written, 4 GiB, run as time segments), Algorithm 5 as printed or
+    the naive generator, Blum-Goldwasser
     encryption or decryption of 2^18 messages, or one batched launch of 300
     uneven requests; two warm-up calls and one more inside the NVTX range
     "profile"."""
@@ -92,11 +93,11 @@ def run_profile_case(kind: str) -> None:
     elif kind == "bbs":
         st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
-        run = lambda: st.generate(1024, out=out)  # noqa: E731
-    elif kind == "bbs_split":  # 2^16 BBS streams x 4096 written (1 GiB): the call runs as time segments
+        run = lambda: st.generate_split(1024, out=out, segments=1)  # noqa: E731
+    elif kind == "bbs_split":  # the benchmark's BBS call, 2^16 x 16384 written (4 GiB): run as time segments
         st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
-        out = torch.empty((S_BBS, 4096), dtype=torch.int32, device="cuda")
-        run = lambda: st.generate(4096, out=out)  # noqa: E731
+        out = torch.empty((S_BBS, L_BBS), dtype=torch.int32, device="cuda")
+        run = lambda: st.generate(L_BBS, out=out)  # noqa: E731
     elif kind == "bbs16":  # Algorithm 5 as printed, 2^16 streams x 1024 written (256 MiB)
         st = ci.States(S_BBS, variant="bbs16", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")

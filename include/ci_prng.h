@@ -186,10 +186,10 @@ ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev
  * t |= BBS & {0,1,3,7}[shift] -- 11 modular squarings per output, done with
  * 64x64->128-bit multiplies and Barrett reduction.  The stream's two
  * combination arrays are comb[sel1] and comb[8 + sel2] with sel1 = v & 7,
- * sel2 = (v >> 3) & 7 of its BBS seed v.  A CI_VAR_BBS state with too few
- * streams to fill the GPU (under about two waves of resident warps) is run as
- * time segments, as ci_generate_split does, with identical results; that
- * form allocates a stream-ordered workspace.  Errors as ci_generate
+ * sel2 = (v >> 3) & 7 of its BBS seed v.  A CI_VAR_BBS state is run as
+ * time segments, as ci_generate_split does, with identical results, unless
+ * its streams alone fill about ten waves of resident warps; that form
+ * allocates a stream-ordered workspace.  Errors as ci_generate
  * (CI_E_STATE for an xor handle). */
 ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out_dev,
                           uint64_t out_capacity_u32, void *cuda_stream);
@@ -202,7 +202,8 @@ ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out
  * with a^2 + b^2 < 1 (exact integer test (o0>>8)^2 + (o1>>8)^2 < 2^48).
  * Works for both variants; the state advances exactly as in the written
  * form.  n_per_stream must be even (CI_E_INVAL otherwise).  Narrow states run
- * as time segments as in ci_generate / ci_generate_bbs (identical counts). */
+ * as time segments (identical counts): xor-like states as in ci_generate,
+ * CI_VAR_BBS states under about two waves of resident warps. */
 ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t *counts_dev,
                                void *cuda_stream);
 
@@ -213,7 +214,7 @@ ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t
  * stored; the state advances as in the written form.  Not a construct of the
  * paper: it lets very large runs be compared without holding their outputs.
  * n_per_stream == 0 is a no-op.  Narrow states run as time segments as in
- * ci_generate / ci_generate_bbs (identical digests).
+ * ci_generate_fused_qc (identical digests).
  * Errors: CI_E_STATE, CI_E_INVAL (digest_dev NULL with n > 0), CI_E_CUDA. */
 ci_status ci_generate_digest(ci_states states, uint64_t n_per_stream, uint64_t *digest_dev,
                              void *cuda_stream);
@@ -531,18 +532,22 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * ci_generate_bbs for CI_SINK_WRITTEN, ci_generate_fused_qc for CI_SINK_QC,
  * ci_generate_digest for CI_SINK_DIGEST).  For states with few streams and
  * long lengths, whose sequential chains leave most of the GPU idle.  (Those
- * single-call entry points split such states on their own: CI_VAR_BBS states
- * under about two waves of resident warps, xor-like states of at most one
- * warp group per SM, with segments of at least 1024 iterations.)
+ * single-call entry points split states on their own: written CI_VAR_BBS
+ * outputs unless the state fills about ten waves of resident warps, BBS
+ * consumer sinks under about two waves, xor-like states of at most one warp
+ * group per SM, with segments of at least 1024 iterations.)
  * Method: each segment's own generator is jumped ahead (xor-likes: GF(2)
  * matrix powers of their step; BBS: x <- x^(2^(11 k len) mod lcm(p-1, q-1))
  * mod M), the segments run from a zero mixing state, a per-warp scan restores
  * their true starts from the linearity of Algorithm 4/5's mixing and Eq.
  * (Oplus) over the lanes, and the segments run again from those starts into
  * the sink (written BBS outputs are corrected in place instead: the
- * homogeneous part is XORed in, two shuffles per output).  Cost: about twice
- * the generator work (once for written BBS outputs), spread over up to
- * n_segments times more warps.
+ * homogeneous part is XORed in, two shuffles per output; from 12 warp groups
+ * per SM on, inside the generation launch, each segment's correction run by
+ * the warp that completes the last of its two inputs, the segment's own
+ * outputs and its predecessor's true end).  Cost: about twice the generator
+ * work (once for written BBS outputs), spread over up to n_segments times
+ * more warps.
  * out_dev: uint32 outputs (CI_SINK_WRITTEN, out_capacity elements, layout as
  * ci_generate) or uint64[n_streams] (counts INCREMENTED for CI_SINK_QC,
  * digests SET for CI_SINK_DIGEST; out_capacity ignored).  n_segments == 0

@@ -156,7 +156,8 @@ cudaError_t ensure_jump_tables(cudaStream_t stream) {
 
 // ------------------------------------------------ BBS jump
 // x <- x^(2^E) mod M with E = 11 * dist squarings, through the exponent
-// 2^E mod lambda(M), lambda = lcm(p - 1, q - 1) (x is a unit mod M).
+// 2^E mod lambda(M), lambda = lcm(p - 1, q - 1) (x is a unit mod M);
+// lambda and its Barrett reciprocal come from k_split_lambda.
 __device__ __forceinline__ uint64_t gcd64(uint64_t a, uint64_t b) {
     while (b) {
         const uint64_t t = a % b;
@@ -176,11 +177,10 @@ __device__ __forceinline__ uint64_t pow_mod(const Barrett62 &B, uint64_t a, uint
     return r;
 }
 
-__device__ __forceinline__ uint64_t bbs_jump(uint64_t y, uint64_t M, uint64_t mu, uint64_t p, uint64_t q,
+__device__ __forceinline__ uint64_t bbs_jump(uint64_t y, uint64_t M, uint64_t mu, uint64_t lam, uint64_t lam_mu,
                                              uint64_t squarings) {
-    const uint64_t lam = (p - 1) / gcd64(p - 1, q - 1) * (q - 1);
     Barrett62 L;
-    L.set(lam, barrett_mu(lam));
+    L.set(lam, lam_mu);
     // 2^squarings mod lam by square-and-multiply on the exponent's bits
     const uint64_t e = pow_mod(L, 2 % lam, squarings);
     Barrett62 B;
@@ -234,6 +234,19 @@ struct SrcBbs16Seg : SrcBbs16 {
 // one chunk each, then BBS3 and BBS1, BBS7 and BBS2 for the two shift steps.
 __constant__ uint32_t c_bbs16_squarings[8] = {2, 2, 2, 1, 1, 1, 2, 1};
 
+// lambda(M) = lcm(p - 1, q - 1) of each lane's BBS modulus and its Barrett
+// reciprocal, once per lane (every segment's jump uses them):
+// lam[l] = lambda, lam[P + l] = barrett_mu(lambda).
+__global__ void __launch_bounds__(256) k_split_lambda(DevState src, uint64_t *lam) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < src.P; l += stride) {
+        const uint64_t p = src.u32[F_P * src.P + l], q = src.u32[F_Q * src.P + l];
+        const uint64_t v = (p - 1) / gcd64(p - 1, q - 1) * (q - 1);
+        lam[l] = v;
+        lam[src.P + l] = barrett_mu(v);
+    }
+}
+
 // lambda(M) = lcm(p - 1, q - 1) of each 16-bit modulus M = p q (p != q primes,
 // as seeded), by trial division; lam[k * P + l] for generator k of lane l.
 __global__ void __launch_bounds__(256) k_split_lambda16(DevState src, uint32_t *lam) {
@@ -272,7 +285,8 @@ __device__ __forceinline__ uint32_t pow_mod32(uint32_t a, uint64_t e, uint32_t m
 // partner table), jumps the own generator by k * len iterations and, for
 // k >= 1, clears slot and x.
 __global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg, uint32_t K, uint64_t len,
-                                                     int variant, int xl, OwnSave own, const uint32_t *lam16) {
+                                                     int variant, int xl, OwnSave own, const uint32_t *lam16,
+                                                     const uint64_t *lam64) {
     const int nf = variant == CI_VAR_BBS16 ? kU32FieldsBbs16 : kU32Fields;
     const uint64_t total = (uint64_t)(K + (variant == CI_VAR_BBS16 ? 1 : 0)) * src.P;  // BBS16: slot K, a copy of the start
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -299,8 +313,7 @@ __global__ void __launch_bounds__(256) k_split_setup(DevState src, SegSpace seg,
             }
         } else if (variant == CI_VAR_BBS) {
             d.u64[G_Y * src.P + l] = bbs_jump(src.u64[G_Y * src.P + l], src.u64[G_M * src.P + l],
-                                              src.u64[G_MU * src.P + l], src.u32[F_P * src.P + l],
-                                              src.u32[F_Q * src.P + l], 11ull * dist);
+                                              src.u64[G_MU * src.P + l], lam64[l], lam64[src.P + l], 11ull * dist);
         } else if (xl == CI_XL_XOR128) {
             uint32_t v[4];
             for (int w = 0; w < 4; ++w) v[w] = src.u32[(F_A + w) * src.P + l];
@@ -894,7 +907,7 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
     const int own_first = b16 ? (int)F_Y16 : (int)F_A, own_count = b16 ? 8 : kOwnWords;
     const uint64_t res_bytes = 8ull * K * h->P;  // per-segment consumer results
     const uint64_t own_bytes = fixup ? 0 : (4ull * own_count + (bbs ? 8ull : 0ull)) * K * h->P;
-    const uint64_t lam_bytes = b16 ? 4ull * 8 * h->P : 0;
+    const uint64_t lam_bytes = b16 ? 4ull * 8 * h->P : bbs ? 16ull * h->P : 0;
     uint8_t *ws = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void **>(&ws), stride * slots + 2 * res_bytes + own_bytes + lam_bytes,
                              stream)) != cudaSuccess)
@@ -908,6 +921,7 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
         own.u64 = bbs ? reinterpret_cast<uint64_t *>(own.u32 + (uint64_t)own_count * K * h->P) : nullptr;
     }
     uint32_t *lam16 = b16 ? reinterpret_cast<uint32_t *>(after + own_bytes) : nullptr;
+    uint64_t *lam64 = bbs ? reinterpret_cast<uint64_t *>(after + own_bytes) : nullptr;
 
     // Handles over the segment states (host copies of the caller's, moved).
     std::vector<ci_states_s> segs(slots, *h);
@@ -922,8 +936,9 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
 
     ci_status st = CI_OK;
     if (b16) k_split_lambda16<<<split_block_count(h->P), 256, 0, stream>>>(src, lam16);
+    if (bbs) k_split_lambda<<<split_block_count(h->P), 256, 0, stream>>>(src, lam64);
     k_split_setup<<<split_block_count(slots * h->P), 256, 0, stream>>>(src, sp, (uint32_t)K, len, h->variant, h->xl,
-                                                                       own, lam16);
+                                                                       own, lam16, lam64);
     if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "split setup");
 
     if (st == CI_OK && fixup && groups >= kOneLaunchGroupsPerSm * (uint64_t)sm_count()) {
