@@ -99,14 +99,16 @@ __device__ __forceinline__ bool bg_setup_decrypt(uint64_t p, uint64_t q, uint64_
     uint64_t x0 = 0, N = 3;
     if (ok) {
         const Barrett32 Bp1(p - 1), Bq1(q - 1);      // even moduli: Barrett
-        const Mont32 Mp(p), Mq(q);                    // odd primes: Montgomery
+        const Mont32 Mp((uint32_t)p), Mq((uint32_t)q);  // odd primes: Montgomery
         const uint64_t ep = Bp1.pow((p + 1) / 4, L);  // ((p+1)/4)^L mod (p-1)
         const uint64_t eq = Bq1.pow((q + 1) / 4, L);
-        const uint64_t rp = Mp.pow(y, ep);
-        const uint64_t rq_m = Mq.pow_m(Mq.to(y), eq);  // Montgomery forms mod q from here
-        const uint64_t pinv_m = Mq.pow_m(Mq.to(p), q - 2);  // Fermat: p^(q-2) = p^-1 mod q
-        const uint64_t rp_m = Mq.to(rp);
-        const uint64_t diff_m = rq_m >= rp_m ? rq_m - rp_m : rq_m + q - rp_m;
+        // y mod N < p q, below p 2^32 and q 2^32: taken to Montgomery form by REDC
+        const uint64_t yN = y < p * q ? y : y % (p * q);
+        const uint32_t rp = Mp.from(Mp.pow_m(Mp.to_wide(yN), ep));
+        const uint32_t rq_m = Mq.pow_m(Mq.to_wide(yN), eq);  // Montgomery forms mod q from here
+        const uint32_t pinv_m = Mq.pow_m(Mq.to_any((uint32_t)p), q - 2);  // Fermat: p^(q-2) = p^-1 mod q
+        const uint32_t rp_m = Mq.to_any(rp);
+        const uint32_t diff_m = rq_m >= rp_m ? rq_m - rp_m : (uint32_t)((uint64_t)rq_m + q - rp_m);
         const uint64_t t = Mq.from(Mq.mul(diff_m, pinv_m));  // (r_q - r_p) p^-1 mod q
         x0 = rp + p * t;                              // < p + p (q - 1) = N
         N = p * q;

@@ -37,62 +37,92 @@ struct Barrett32 {
 };
 
 // Montgomery arithmetic for an odd modulus 3 <= m < 2^32 with R = 2^32:
-// values in Montgomery form a R mod m, REDC(t) = t R^-1 mod m for t < m^2.
+// values in Montgomery form a R mod m, REDC(t) = t R^-1 mod m for t < m R.
 // REDC: u = (t mod R) m' mod R with m' = -m^-1 mod R; (t + u m) / R < 2m,
 // computed without the 65-bit sum: the low halves of t and u m cancel, with a
-// carry exactly when t mod R != 0.
+// carry exactly when t mod R != 0.  Operands are 32-bit words, so a product
+// is one 32 x 32 -> 64-bit multiply and REDC one low and one high product.
 struct Mont32 {
-    uint64_t m;
+    uint32_t m;
     uint32_t np;   // -m^-1 mod 2^32
-    uint64_t r2;   // R^2 mod m
-    uint64_t one;  // R mod m, the Montgomery form of 1
-    __device__ __forceinline__ explicit Mont32(uint64_t mod) : m(mod) {
-        uint32_t inv = (uint32_t)mod;  // Newton: each step doubles the correct low bits (3 to start)
+    uint32_t one;  // R mod m, the Montgomery form of 1
+    uint32_t r2;   // R^2 mod m
+    __device__ __forceinline__ explicit Mont32(uint32_t mod) : m(mod) {
+        uint32_t inv = mod;  // Newton: each step doubles the correct low bits (3 to start)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) inv *= 2u - (uint32_t)mod * inv;
+        for (int i = 0; i < 4; ++i) inv *= 2u - mod * inv;
         np = 0u - inv;
-        one = (1ull << 32) % mod;
-        r2 = one * one % mod;
+        one = (0u - mod) % mod;  // (2^32 - m) mod m = R mod m
+        r2 = (uint32_t)((uint64_t)one * one % mod);
     }
-    __device__ __forceinline__ uint64_t redc(uint64_t t) const {
+    __device__ __forceinline__ uint32_t redc(uint64_t t) const {  // t < m R
         const uint32_t u = (uint32_t)t * np;
-        uint64_t r = (t >> 32) + (((uint64_t)u * m) >> 32) + ((uint32_t)t != 0u ? 1u : 0u);
-        return r >= m ? r - m : r;
+        const uint64_t r = (t >> 32) + __umulhi(u, m) + ((uint32_t)t != 0u ? 1u : 0u);
+        return (uint32_t)(r >= m ? r - m : r);
     }
-    __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) const { return redc(a * b); }  // a, b < m
-    __device__ __forceinline__ uint64_t to(uint64_t a) const { return mul(a % m, r2); }
-    __device__ __forceinline__ uint64_t from(uint64_t a) const { return redc(a); }
-    // (a^e in Montgomery form) for a in Montgomery form.
-    __device__ __forceinline__ uint64_t pow_m(uint64_t a, uint64_t e) const {
-        uint64_t r = one;
-        while (e) {
-            if (e & 1ull) r = mul(r, a);
-            a = mul(a, a);
-            e >>= 1;
+    __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) const {  // a, b < m
+        return redc((uint64_t)a * b);
+    }
+    // Montgomery form of a < m; of any a, through one 32-bit remainder.
+    __device__ __forceinline__ uint32_t to(uint32_t a) const { return mul(a, r2); }
+    __device__ __forceinline__ uint32_t to_any(uint32_t a) const { return to(a < m ? a : a % m); }
+    // Montgomery form of t < m R without a 64-bit remainder: REDC(t) = t R^-1,
+    // and two products by R^2 give t R.
+    __device__ __forceinline__ uint32_t to_wide(uint64_t t) const { return mul(mul(redc(t), r2), r2); }
+    __device__ __forceinline__ uint32_t from(uint32_t a) const { return redc(a); }
+    // (a^e in Montgomery form) for a in Montgomery form, left to right over
+    // 2-bit windows of e: two squarings and one product by a^w (w = 0 takes
+    // the form of 1) per window, the same work in every lane whatever its
+    // exponent bits, so a warp never runs both sides of a branch.
+    __device__ __forceinline__ uint32_t pow_m(uint32_t a, uint64_t e) const {
+        if (e == 0) return one;
+        const uint32_t a2 = mul(a, a), a3 = mul(a2, a);
+        int i = (63 - __clzll((long long)e)) & ~1;  // the window that holds the top bit
+        uint32_t w = (uint32_t)(e >> i) & 3u;
+        uint32_t r = w == 1u ? a : w == 2u ? a2 : a3;
+        for (i -= 2; i >= 0; i -= 2) {
+            r = mul(r, r);
+            r = mul(r, r);
+            w = (uint32_t)(e >> i) & 3u;
+            r = mul(r, w == 0u ? one : w == 1u ? a : w == 2u ? a2 : a3);
         }
         return r;
     }
-    __device__ __forceinline__ uint64_t pow(uint64_t a, uint64_t e) const { return from(pow_m(to(a), e)); }
+    // (2^e in Montgomery form), left to right: a squaring per bit and, for a
+    // set bit, a doubling (the Montgomery form is linear, so 2 x R mod m is
+    // the doubled form), taken by a select.
+    __device__ __forceinline__ uint32_t pow2_m(uint32_t e) const {
+        uint32_t r = one;
+        for (int i = 31 - __clz((int)(e | 1u)); i >= 0; --i) {
+            r = mul(r, r);
+            const uint64_t d = 2ull * r;
+            const uint32_t rd = (uint32_t)(d >= m ? d - m : d);
+            r = (e >> i) & 1u ? rd : r;
+        }
+        return r;
+    }
 };
 
 // Miller-Rabin with bases 2, 7, 61: exact for odd n < 4,759,123,141
 // (Jaeschke 1993), so for every odd n in [3, 2^32).  A base that is a multiple
 // of n (n = 7, 61) proves nothing and is skipped.
-__device__ __forceinline__ bool is_prime_u32(uint64_t n) {
-    if (n < 3 || n >= (1ull << 32) || (n & 1ull) == 0) return n == 2;
+__device__ __forceinline__ bool is_prime_u32(uint64_t n64) {
+    if (n64 < 3 || n64 >= (1ull << 32) || (n64 & 1ull) == 0) return n64 == 2;
+    const uint32_t n = (uint32_t)n64;
     const Mont32 M(n);
-    const uint64_t one = M.one, minus_one = n - M.one;  // Montgomery forms of 1 and n - 1
-    uint64_t d = n - 1;
+    const uint32_t one = M.one, minus_one = n - M.one;  // Montgomery forms of 1 and n - 1
+    uint32_t d = n - 1;
     int s = 0;
-    while ((d & 1ull) == 0) {
+    while ((d & 1u) == 0) {
         d >>= 1;
         ++s;
     }
     const uint32_t bases[3] = {2u, 7u, 61u};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (bases[i] % n == 0) continue;
-        uint64_t x = M.pow_m(M.to(bases[i]), d);
+        const uint32_t b = bases[i] < n ? bases[i] : bases[i] % n;
+        if (b == 0) continue;
+        uint32_t x = b == 2u ? M.pow2_m(d) : M.pow_m(M.to(b), d);
         if (x == one || x == minus_one) continue;
         bool composite = true;
         for (int r = 1; r < s; ++r) {
