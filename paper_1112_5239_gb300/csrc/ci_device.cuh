@@ -161,17 +161,44 @@ __host__ __device__ __forceinline__ uint32_t bit_length64(uint64_t M) {
 #endif
 }
 
-// The stored reciprocal: floor(2^(2n+1) / M) by restoring long division of
-// 2^(2n+1) (remainders stay below M < 2^62), shifted as described above.
+// The stored reciprocal floor(2^(2n+1) / M), shifted as described above.
+// Scaled by 2^(64-n), it is the quotient of the 128-bit 2^(n+65) = hi 2^64 by
+// the normalised divisor d = M 2^(64-n) (top bit set, d > hi), found as two
+// 32-bit quotient digits, each estimated from the divisor's top half and
+// corrected at most twice (Knuth, TAOCP 2, Alg. 4.3.1D, in the two-digit form
+// of Warren's Hacker's Delight).  The only other case, M = 2^61 (d = hi),
+// and M < 2 take restoring long division.
 __host__ __device__ __forceinline__ uint64_t barrett_mu(uint64_t M) {
     const uint32_t n = bit_length64(M);
-    uint64_t r = 1, q = 0;
-    for (uint32_t i = 0; i < 2 * n + 1; ++i) {
-        r <<= 1;
-        q <<= 1;
-        if (r >= M) {
-            r -= M;
-            q |= 1;
+    uint64_t q;
+    const uint64_t d = n >= 2 ? M << (64 - n) : 0, hi = 1ull << (n + 1);
+    if (n >= 2 && hi < d) {
+        const uint64_t d1 = d >> 32, d0 = d & 0xFFFFFFFFull;
+        uint64_t q1 = hi / d1, r = hi - q1 * d1;  // digit 1 of (hi 2^32) / d
+        while ((q1 >> 32) || q1 * d0 > (r << 32)) {
+            --q1;
+            r += d1;
+            if (r >> 32) break;
+        }
+        const uint64_t u = (hi << 32) - q1 * d;  // partial remainder, below d
+        uint64_t q0 = u / d1;                    // digit 0 of (u 2^32) / d
+        r = u - q0 * d1;
+        while ((q0 >> 32) || q0 * d0 > (r << 32)) {
+            --q0;
+            r += d1;
+            if (r >> 32) break;
+        }
+        q = (q1 << 32) | q0;
+    } else {
+        uint64_t rem = 1;
+        q = 0;
+        for (uint32_t i = 0; i < 2 * n + 1; ++i) {
+            rem <<= 1;
+            q <<= 1;
+            if (rem >= M) {
+                rem -= M;
+                q |= 1;
+            }
         }
     }
     return n <= 61 ? q << (61 - n) : q;
