@@ -167,12 +167,20 @@ __device__ __forceinline__ uint64_t gcd64(uint64_t a, uint64_t b) {
     return a;
 }
 
+// a^e mod M for a < M, left to right over 2-bit windows of e: two squarings
+// and one product by a^w (by 1 for w = 0) per window, the same work in every
+// lane whatever its exponent bits.
 __device__ __forceinline__ uint64_t pow_mod(const Barrett62 &B, uint64_t a, uint64_t e) {
-    uint64_t r = 1 % B.M;
-    while (e) {
-        if (e & 1ull) r = B.mul(r, a);
-        a = B.mul(a, a);
-        e >>= 1;
+    if (e == 0) return 1 % B.M;
+    const uint64_t a2 = B.mul(a, a), a3 = B.mul(a2, a), one = 1 % B.M;
+    int i = (63 - __clzll((long long)e)) & ~1;  // the window that holds the top bit
+    uint32_t w = (uint32_t)(e >> i) & 3u;
+    uint64_t r = w == 1u ? a : w == 2u ? a2 : a3;
+    for (i -= 2; i >= 0; i -= 2) {
+        r = B.mul(r, r);
+        r = B.mul(r, r);
+        w = (uint32_t)(e >> i) & 3u;
+        r = B.mul(r, w == 0u ? one : w == 1u ? a : w == 2u ? a2 : a3);
     }
     return r;
 }
