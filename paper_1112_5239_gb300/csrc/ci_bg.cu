@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(kBgWarps * 32, CI_BG_MIN_BLOCKS)
     uint8_t *row = tile + lane * kBgRowPad;
     const uint64_t n_groups = (n_msgs + 31) / 32;
     const uint64_t stride = (uint64_t)gridDim.x * kBgWarps;
-    for (uint64_t g = (uint64_t)blockIdx.x * kBgWarps + (threadIdx.x >> 5); g < n_groups; g += stride) {
+    // warp w of block b starts at group w * gridDim.x + b, so a partial last
+    // round of warps is spread over every block (and SM)
+    for (uint64_t g = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; g < n_groups; g += stride) {
         const uint64_t m0 = g * 32;
         const uint64_t msg = m0 + lane;
         const bool live = msg < n_msgs;
@@ -210,7 +212,7 @@ int bg_grid(uint64_t n_msgs) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bg<kDecrypt, kVec>, kBgWarps * 32, 0);
         if (per_sm <= 0) per_sm = 1;
     });
-    const uint64_t blocks = (n_msgs + 32 * kBgWarps - 1) / (32 * kBgWarps);
+    const uint64_t blocks = (n_msgs + 31) / 32;  // a block per warp group at most
     return (int)std::min<uint64_t>(blocks, (uint64_t)sm_count() * per_sm);
 }
 

@@ -14,7 +14,9 @@ namespace ci {
 
 // One warp per group of 32 lanes, W warps per block, a persistent grid whose
 // warps stride over the warp groups; written sinks stage a 32 x KT tile per
-// warp in dynamic shared memory.
+// warp in dynamic shared memory.  Warp w of block b starts at group
+// w * gridDim.x + b: with fewer groups than resident warps, the idle warps are
+// spread over all blocks (hence all SMs) instead of leaving whole blocks idle.
 template <class Src, int SINK, int W, class TC>
 __global__ void __launch_bounds__(W * 32) k_generate(DevState st, uint64_t n, uint32_t *out, uint64_t *counts) {
     extern __shared__ uint4 dyn_tiles[];
@@ -22,7 +24,7 @@ __global__ void __launch_bounds__(W * 32) k_generate(DevState st, uint64_t n, ui
     uint4 *tile = dyn_tiles + (SINK >= dev::SINK_QC ? 0 : w * TC::KT * 8);
     const uint64_t ngroups = st.P / 32;
     const uint64_t gstride = (uint64_t)gridDim.x * W;
-    for (uint64_t g = (uint64_t)blockIdx.x * W + w; g < ngroups; g += gstride)
+    for (uint64_t g = (uint64_t)w * gridDim.x + blockIdx.x; g < ngroups; g += gstride)
         dev::warp_task<Src, SINK, TC>(st, g, n, out, n, 0, counts, tile);
 }
 
@@ -39,7 +41,7 @@ __global__ void __launch_bounds__(W * 32) k_generate_tma(DevState st, uint64_t n
     uint4 *tiles = base + w * 512;  // two 4 KB tiles per warp
     const uint64_t ngroups = st.P / 32;
     const uint64_t gstride = (uint64_t)gridDim.x * W;
-    for (uint64_t g = (uint64_t)blockIdx.x * W + w; g < ngroups; g += gstride)
+    for (uint64_t g = (uint64_t)w * gridDim.x + blockIdx.x; g < ngroups; g += gstride)  // as in k_generate
         dev::warp_task_tma<Src>(st, g, n, &map, out, n, 0, tiles);
     if ((threadIdx.x & 31) == 0) dev::tma_wait_all();  // every store complete before the block exits
     __syncwarp();
@@ -66,7 +68,7 @@ static cudaError_t launch_gen_tma(const DevState &st, uint64_t n, uint32_t *out,
             per_sm = ps;
     });
     const uint64_t cap = (uint64_t)sm_count() * per_sm;
-    const uint64_t need = (st.P / 32 + W - 1) / W;
+    const uint64_t need = st.P / 32;  // a block per group at most (the warps spread over the blocks)
     const unsigned grid = (unsigned)(need < cap ? need : cap);
     *used = true;
     if (grid == 0) return cudaSuccess;
@@ -88,7 +90,7 @@ static cudaError_t launch_gen_t(const DevState &st, uint64_t n, uint32_t *out, u
             per_sm = ps;
     });
     const uint64_t cap = (uint64_t)sm_count() * per_sm;
-    const uint64_t need = (st.P / 32 + W - 1) / W;
+    const uint64_t need = st.P / 32;  // a block per group at most (the warps spread over the blocks)
     const unsigned grid = (unsigned)(need < cap ? need : cap);
     if (grid == 0) return cudaSuccess;
     kern<<<grid, W * 32, smem, stream>>>(st, n, out, counts);

@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(256, CI_NAIVE_MIN_BLOCKS) k_naive_generate(Nai
     uint32_t *tw = reinterpret_cast<uint32_t *>(tile);
     const uint64_t groups = v.P / 32;
     const uint64_t wstride = (uint64_t)gridDim.x * 8;
-    for (uint64_t g = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); g < groups; g += wstride) {
+    // warp w of block b starts at group w * gridDim.x + b: a partial last
+    // round of warps is spread over every block (and SM)
+    for (uint64_t g = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; g < groups; g += wstride) {
         const uint64_t l = g * 32 + lane, row0 = g * 32;
         NaiveLane L;
         L.load(v.u64, v.x, v.P, l);
@@ -181,7 +183,7 @@ int naive_grid(uint64_t groups) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_naive_generate<V4>, 256, 0);
         if (per_sm <= 0) per_sm = 1;
     });
-    return (int)std::max<uint64_t>(1, std::min<uint64_t>((groups + 7) / 8, (uint64_t)sm_count() * per_sm));
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(groups, (uint64_t)sm_count() * per_sm));  // a block per group at most
 }
 
 }  // namespace

@@ -653,7 +653,9 @@ __global__ void __launch_bounds__(256, split_min_blocks<Src>()) k_split_run(SegS
     __shared__ uint4 tiles[8][256];
     uint4 *tile = tiles[threadIdx.x >> 5];
     const uint64_t units = (uint64_t)(k_end - k_begin) * groups;
-    for (uint64_t u = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < units; u += (uint64_t)gridDim.x * 8) {
+    // warp w of block b starts at unit w * gridDim.x + b: a partial last
+    // round of warps is spread over every block (and SM)
+    for (uint64_t u = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; u < units; u += (uint64_t)gridDim.x * 8) {
         const uint64_t k = k_begin + u / groups, g = u % groups;
         CI_WARP_CHECK(caller, k < K, CHK_SEGMENT, k);
         const DevState st = k != 0 ? seg.at(k) : zero < 0 ? caller : seg.at((uint64_t)zero);
@@ -677,7 +679,7 @@ cudaError_t launch_split_run(const SegSpace &sp, const DevState &caller, int zer
     });
     const uint64_t groups = caller.P / 32, units = (uint64_t)(ke - kb) * groups;
     if (units == 0) return cudaSuccess;
-    const int blocks = (int)std::min<uint64_t>((units + 7) / 8, (uint64_t)sm_count() * per_sm);
+    const int blocks = (int)std::min<uint64_t>(units, (uint64_t)sm_count() * per_sm);  // a block per unit at most
     k_split_run<Src, SINK><<<blocks, 256, 0, stream>>>(sp, caller, zero, kb, ke, K, len, len_last, groups, out, ld,
                                                        col0, aux);
     return cudaGetLastError();

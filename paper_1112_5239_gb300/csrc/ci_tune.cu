@@ -125,9 +125,11 @@ ci_status ci_autotune(uint32_t flags, void *cuda_stream, ci_tune_table *out) {
         table = g_table;
     }
     // Representative problems: xor sources 2^20 streams (written: 256 outputs
-    // per stream, a 1 GiB launch; consumers: 1024), BBS sources 2^16 x 128.
+    // per stream, a 1 GiB launch; consumers: 1024), BBS sources 2^16 x 1024
+    // (at 128 outputs the shapes' times were within noise of each other and
+    // the pick could be 4 % slower on long calls).
     const uint64_t S_xor = 1ull << 20, S_bbs = 1ull << 16;
-    const uint64_t L_written = 256, L_fused = 1024, L_bbs = 128;
+    const uint64_t L_written = 256, L_fused = 1024, L_bbs = 1024;
     ci_params p;
     std::memset(&p, 0, sizeof p);
     p.comb_size = 32;
