@@ -56,7 +56,8 @@ def parse_args():
                          "one launch per request; serving: Poisson arrivals through the serving loop")
     ap.add_argument("--requests", type=int, default=10_000, help="batched suite: number of requests")
     ap.add_argument("--serving-requests", type=int, default=20_000, help="serving suite: requests per rate")
-    ap.add_argument("--profile", choices=["written", "fused", "fused_xor64", "bbs", "bbs_split", "bbs16", "batched",
+    ap.add_argument("--profile", choices=["written", "fused", "fused_xor64", "bbs", "bbs_split", "bbs_split_1g", "bbs16",
+                                          "batched",
                                           "bg", "bg_dec", "naive"],
                     default=None,
                     help="small case for ncu: autotune, 2 warm-up launches, then 1 launch of one kernel inside "
@@ -68,7 +69,8 @@ def run_profile_case(kind: str) -> None:
     """Small case for profiler captures: 2^19 streams x 256 written (512 MiB,
     larger than L2), 2^19 x 4096 fused (xor128 or xor64), 2^16 x 1024 BBS
     written (256 MiB; one unsplit launch), the benchmark's BBS call (2^16 x
-    16384 written, 4 GiB, run as time segments), Algorithm 5 as printed or
+    16384 written, 4 GiB, run as time segments) or the same on 2^16 x 4096
+    (1 GiB), Algorithm 5 as printed or
     the naive generator, Blum-Goldwasser
     encryption or decryption of 2^18 messages, or one batched launch of 300
     uneven requests; two warm-up calls and one more inside the NVTX range
@@ -98,6 +100,10 @@ def run_profile_case(kind: str) -> None:
         st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
         out = torch.empty((S_BBS, L_BBS), dtype=torch.int32, device="cuda")
         run = lambda: st.generate(L_BBS, out=out)  # noqa: E731
+    elif kind == "bbs_split_1g":  # the same form on 2^16 x 4096 (1 GiB, 16 segments), small enough for a full capture
+        st = ci.States(S_BBS, variant="bbs", seed=SEED_BBS)
+        out = torch.empty((S_BBS, 4096), dtype=torch.int32, device="cuda")
+        run = lambda: st.generate(4096, out=out)  # noqa: E731
     elif kind == "bbs16":  # Algorithm 5 as printed, 2^16 streams x 1024 written (256 MiB)
         st = ci.States(S_BBS, variant="bbs16", seed=SEED_BBS)
         out = torch.empty((S_BBS, 1024), dtype=torch.int32, device="cuda")
