@@ -156,20 +156,21 @@ def test_written_word_stores(variant):
         assert np.array_equal(u32(st.generate(40)), orc.streams(40))
 
 
-@pytest.mark.parametrize("variant,n,C", [("bbs", 200, 32), ("bbs", 201, 32), ("bbs", 200, 8), ("bbs16", 200, 32)])
-def test_many_groups_one_launch_form(variant, n, C):
+@pytest.mark.parametrize("variant,n,C,K", [("bbs", 200, 32, 4), ("bbs", 201, 32, 4), ("bbs", 200, 8, 4),
+                                           ("bbs", 96, 32, 2), ("bbs16", 200, 32, 4)])
+def test_many_groups_one_launch_form(variant, n, C, K):
     """With many warp groups (2^17 - 8 streams: 4096 groups, the last one
     ragged), written BBS-source outputs take the one-launch form, whose
     fix-ups run inside the generation launch as each segment's predecessor
     completes.  Every output and the whole end state equal one unsplit
     launch's, sampled groups equal the oracle, and the next call continues
     exactly.  n = 201 takes the word-store path; C = 8 puts four mixing
-    groups in each warp."""
+    groups in each warp; K = 2 has a single fix-up per group."""
     torch, ci = cuda_or_skip()
     S, seed = (1 << 17) - 8, 41 + C
     st = _states(ci, variant, "xor128", C, seed, S)
     ref = _states(ci, variant, "xor128", C, seed, S)
-    out = st.generate_split(n, segments=4)
+    out = st.generate_split(n, segments=K)
     assert torch.equal(out, ref.generate_split(n, segments=1))
     assert np.array_equal(st.export_state(), ref.export_state())
     for g in (0, 1, 2047, S // 32):  # S // 32: the ragged last group
