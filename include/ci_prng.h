@@ -188,8 +188,9 @@ ci_status ci_generate(ci_states states, uint64_t n_per_stream, uint32_t *out_dev
  * combination arrays are comb[sel1] and comb[8 + sel2] with sel1 = v & 7,
  * sel2 = (v >> 3) & 7 of its BBS seed v.  A CI_VAR_BBS state is run as
  * time segments, as ci_generate_split does, with identical results, unless
- * its streams alone fill about ten waves of resident warps; that form
- * allocates a stream-ordered workspace.  Errors as ci_generate
+ * its streams alone fill about ten waves of resident warps; so is a
+ * CI_VAR_BBS16 state of at most one warp group (32 streams) per SM, within
+ * the one call.  That form allocates a stream-ordered workspace.  Errors as ci_generate
  * (CI_E_STATE for an xor handle). */
 ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out_dev,
                           uint64_t out_capacity_u32, void *cuda_stream);
@@ -202,8 +203,9 @@ ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out
  * with a^2 + b^2 < 1 (exact integer test (o0>>8)^2 + (o1>>8)^2 < 2^48).
  * Works for both variants; the state advances exactly as in the written
  * form.  n_per_stream must be even (CI_E_INVAL otherwise).  Narrow states run
- * as time segments (identical counts): xor-like states as in ci_generate,
- * CI_VAR_BBS states under about two waves of resident warps. */
+ * as time segments (identical counts): xor-like and CI_VAR_BBS16 states as
+ * in ci_generate / ci_generate_bbs, CI_VAR_BBS states under about two waves
+ * of resident warps. */
 ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t *counts_dev,
                                void *cuda_stream);
 
@@ -535,7 +537,8 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * single-call entry points split states on their own: written CI_VAR_BBS
  * outputs unless the state fills about ten waves of resident warps, BBS
  * consumer sinks under about two waves, xor-like states of at most one warp
- * group per SM, with segments of at least 1024 iterations.)
+ * group per SM, with segments of at least 1024 iterations, and CI_VAR_BBS16
+ * states of at most one warp group per SM.)
  * Method: each segment's own generator is jumped ahead (xor-likes: GF(2)
  * matrix powers of their step; BBS: x <- x^(2^(11 k len) mod lcm(p-1, q-1))
  * mod M), the segments run from a zero mixing state, a per-warp scan restores

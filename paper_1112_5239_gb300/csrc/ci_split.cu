@@ -639,10 +639,13 @@ constexpr uint64_t kOneLaunchGroupsPerSm = CI_ONE_LAUNCH_GROUPS_PER_SM;
 // Instantiated per source and sink, with at most 64 registers (4 blocks of 8
 // warps per SM): the all-source batched kernel needs 128, which held the
 // BBS segments to 16 resident warps per SM.  BBS segments (one serial
-// squaring chain per lane) ask for 5 blocks, i.e. 48 registers.
+// squaring chain per lane) ask for 5 blocks, i.e. 48 registers; segments of
+// Algorithm 5 as printed (eight generators per lane, 118 registers in the
+// single-call kernel) for 2 blocks, 128 registers, so that their loop does
+// not spill.
 template <class Src>
 constexpr int split_min_blocks() {
-    return std::is_same<Src, SrcBbs>::value ? 5 : 4;
+    return std::is_same<Src, SrcBbs>::value ? 5 : std::is_same<Src, SrcBbs16Seg>::value ? 2 : 4;
 }
 
 template <class Src, int SINK>
@@ -874,6 +877,19 @@ uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n, int sink) {
 uint64_t split_auto(const ci_states_s &h, uint64_t n, int sink) {
     if (h.variant == CI_VAR_BBS) return split_auto_bbs(h, n, sink);
     const uint64_t groups = h.P / 32, sms = (uint64_t)sm_count();
+    if (h.variant == CI_VAR_BBS16) {
+        // Algorithm 5 as printed: each warp is bound by its own eight chains,
+        // so only states of at most one warp group per SM gain from more
+        // warps (measured, written: 1 group 39x, 32 groups 7x, 128 groups
+        // 2.8x faster; 512 groups slower), with about two waves of the split
+        // kernels' 16 resident warps per SM and segments of at least 256.
+        if (groups > sms) return 1;
+        uint64_t K = std::min<uint64_t>(sms * 32 / groups, n / kMinSegment);
+        K = std::min<uint64_t>(K, kMaxSegments);
+        if (K <= 1) return 1;
+        const uint64_t len = ((n + K - 1) / K + 31) / 32 * 32;
+        return (n + len - 1) / len;
+    }
     // xor-likes: only states with no more warp groups than SMs (measured:
     // 4-11x faster up to 128 groups, slower from 512 groups on, where the
     // setup's GF(2) jumps outweigh the parallelism)

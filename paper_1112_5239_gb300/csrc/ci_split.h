@@ -27,7 +27,7 @@ uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n, int sink);
 // Segment count the single-call entry points use on their own for `sink`
 // (CI_SINK_*): split_auto_bbs for CI_VAR_BBS; for xor-like states only with
 // no more warp groups than SMs (and segments of at least 1024 iterations);
-// 1 otherwise.
+// for CI_VAR_BBS16 likewise (segments of at least 256); 1 otherwise.
 uint64_t split_auto(const ci_states_s &h, uint64_t n, int sink);
 
 // n iterations of h as K segments into `sink` (written: out[r * ld + col0 + i];

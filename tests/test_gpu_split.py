@@ -179,3 +179,23 @@ def test_many_groups_one_launch_form(variant, n, C, K):
         assert np.array_equal(rows, orc.streams(n)), g
         assert np.array_equal(u32(st.generate(40)[32 * g: 32 * g + 32]), orc.streams(40)), g
         st.import_state(ref.export_state())  # back to the state after the split call
+
+
+def test_single_calls_split_narrow_bbs16_states_on_their_own():
+    """Algorithm 5 as printed on one warp of streams over 2^13 iterations:
+    ci_generate_bbs, ci_generate_digest and ci_generate_fused_qc split the
+    call into time segments on their own and equal the oracle's single calls,
+    call after call (the arrays are chosen per call and the generators rotate
+    once per call, as in the oracle)."""
+    torch, ci = cuda_or_skip()
+    n = 1 << 13
+    st = _states(ci, "bbs16", "xor128", 32, 95, 32)
+    orc = oracle_gen("bbs16", "xor128", 32, 95, 102, 32)
+    assert np.array_equal(u32(st.generate(n)), orc.streams(n))
+    d = st.generate_digest(n).cpu().numpy().view(np.uint64)
+    assert np.array_equal(d, digest_rows(orc.streams(n)))
+    c = st.generate_fused_qc(n).cpu().numpy().view(np.uint64)
+    o = orc.streams(n)
+    hits = (((o[:, 0::2] >> 8).astype(np.uint64) ** 2 + (o[:, 1::2] >> 8).astype(np.uint64) ** 2) < (1 << 48)).sum(axis=1)
+    assert np.array_equal(c, hits.astype(np.uint64))
+    assert np.array_equal(u32(st.generate(100)), orc.streams(100))
