@@ -204,8 +204,10 @@ ci_status ci_generate_bbs(ci_states states, uint64_t n_per_stream, uint32_t *out
  * Works for both variants; the state advances exactly as in the written
  * form.  n_per_stream must be even (CI_E_INVAL otherwise).  Narrow states run
  * as time segments (identical counts): xor-like and CI_VAR_BBS16 states as
- * in ci_generate / ci_generate_bbs, CI_VAR_BBS states under about two waves
- * of resident warps. */
+ * in ci_generate / ci_generate_bbs; CI_VAR_BBS states as in ci_generate_bbs
+ * while n_streams * n_per_stream <= 2^29 (the outputs then pass through a
+ * stream-ordered scratch and are counted from there), otherwise under about
+ * two waves of resident warps. */
 ci_status ci_generate_fused_qc(ci_states states, uint64_t n_per_stream, uint64_t *counts_dev,
                                void *cuda_stream);
 
@@ -536,7 +538,8 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * long lengths, whose sequential chains leave most of the GPU idle.  (Those
  * single-call entry points split states on their own: written CI_VAR_BBS
  * outputs unless the state fills about ten waves of resident warps, BBS
- * consumer sinks under about two waves, xor-like states of at most one warp
+ * consumer sinks likewise up to 2^29 outputs per call and under about two
+ * waves above that, xor-like states of at most one warp
  * group per SM, with segments of at least 1024 iterations, and CI_VAR_BBS16
  * states of at most one warp group per SM.)
  * Method: each segment's own generator is jumped ahead (xor-likes: GF(2)
@@ -544,13 +547,15 @@ ci_status ci_naive_generate(void *state_dev, uint64_t n_streams, uint64_t n_per_
  * mod M), the segments run from a zero mixing state, a per-warp scan restores
  * their true starts from the linearity of Algorithm 4/5's mixing and Eq.
  * (Oplus) over the lanes, and the segments run again from those starts into
- * the sink (written BBS outputs are corrected in place instead: the
- * homogeneous part is XORed in, two shuffles per output; from 12 warp groups
+ * the sink (written BBS-source outputs are corrected in place instead: the
+ * homogeneous part is XORed in, two shuffles per output; their consumer sinks
+ * take the same written form into a scratch of up to 2^29 outputs, then count
+ * or digest it, so the squarings run once; from 12 warp groups
  * per SM on, inside the generation launch, each segment's correction run by
  * the warp that completes the last of its two inputs, the segment's own
  * outputs and its predecessor's true end).  Cost: about twice the generator
- * work (once for written BBS outputs), spread over up to n_segments times
- * more warps.
+ * work (once for BBS-source outputs written, or counted through the
+ * scratch), spread over up to n_segments times more warps.
  * out_dev: uint32 outputs (CI_SINK_WRITTEN, out_capacity elements, layout as
  * ci_generate) or uint64[n_streams] (counts INCREMENTED for CI_SINK_QC,
  * digests SET for CI_SINK_DIGEST; out_capacity ignored).  n_segments == 0

@@ -617,10 +617,60 @@ __global__ void __launch_bounds__(256) k_split_combine(const uint64_t *r, uint64
     out[l] = d;
 }
 
+// Consumer results from written rows: the scratch form of a BBS-source
+// consumer call, whose outputs were written (and fixed up) into `rows`, row r
+// (stride n) holding stream r's n outputs.  Work unit = (row r, chunk
+// [b, e) of clen outputs), one warp.  Quarter-circle sink: the chunk's hits
+// among its pairs (o_2k, o_2k+1) are added to out[r] (clen and n even).
+// Digest sink: the chunk contributes K^(n-e) sum_{b<=i<e} o_i K^(e-1-i), so
+// the contributions of all chunks sum to D = sum_i o_i K^(n-1-i); lane j
+// takes outputs e-1-j, e-1-j-32, ... with the running power K^j, K^(j+32), ...,
+// and out[r] (cleared before) receives the warp's sum.
+__device__ __forceinline__ uint64_t digest_pow(uint64_t e) {
+    uint64_t b = kDigestMul, p = 1;
+    while (e) {
+        if (e & 1ull) p *= b;
+        b *= b;
+        e >>= 1;
+    }
+    return p;
+}
+
+template <bool kDigest>
+__global__ void __launch_bounds__(256) k_consume_rows(const uint32_t *rows, uint64_t S, uint64_t n, uint64_t clen,
+                                                      uint64_t chunks, uint64_t *out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t units = S * chunks;
+    for (uint64_t u = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; u < units; u += (uint64_t)gridDim.x * 8) {
+        const uint64_t r = u / chunks, c = u % chunks;
+        const uint64_t b = c * clen, e = b + clen < n ? b + clen : n;
+        const uint32_t *row = rows + r * n;
+        uint64_t v = 0;
+        if (kDigest) {
+            uint64_t pw = digest_pow((uint64_t)lane);
+            const uint64_t step = digest_pow(32);
+            for (uint64_t t = (uint64_t)lane; t < e - b; t += 32) {
+                v += (uint64_t)row[e - 1 - t] * pw;
+                pw *= step;
+            }
+        } else {
+            const uint2 *pairs = reinterpret_cast<const uint2 *>(row + b);
+            for (uint64_t k = (uint64_t)lane; k < (e - b) / 2; k += 32) {
+                const uint2 o = pairs[k];
+                v += 1u - qc_miss(o.x, o.y);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(out + r), kDigest ? v * digest_pow(n - e) : v);
+    }
+}
+
 // ------------------------------------------------ host side
 constexpr uint32_t kMaxSegments = kSplitMaxSegments;
 constexpr uint64_t kMinSegment = 256;       // iterations per segment (auto choice, BBS)
 constexpr uint64_t kMinAutoSegment = 1024;  // ... xor-likes, and when a single call splits on its own
+constexpr uint64_t kScratchWords = 1ull << 29;  // scratch outputs of a BBS-source consumer call (2 GiB)
 // Written BBS-source outputs take the one-launch fix-up form from this many
 // warp groups per SM on: its fix-ups run as one serial chain per group among
 // the squaring warps, which keeps pace only with enough groups; below it,
@@ -855,15 +905,17 @@ uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n, int sink) {
     if (h.variant != CI_VAR_BBS) return 1;
     const uint64_t groups = h.P / 32, sms = (uint64_t)sm_count();
     uint64_t K;
-    if (sink == CI_SINK_WRITTEN) {
+    // consumer sinks whose outputs fit the scratch are written, fixed up and
+    // reduced (split_launch), so they take the written rule
+    if (sink == CI_SINK_WRITTEN || h.S <= kScratchWords / n) {
         // Measured on 2^9 .. 2^13 warp groups of 2^12 .. 2^15 iterations:
         // about ten waves of resident warps (40 per SM) in the one-launch
         // form, four in the three-launch form; segments of at least 256.
         K = groups >= kOneLaunchGroupsPerSm * sms ? (400 * sms + groups / 2) / groups : 160 * sms / groups;
         K = std::min<uint64_t>(K, n / kMinSegment);
     } else {
-        // Consumer sinks generate twice (pass 1, then pass 2 from the true
-        // starts): only states that fill less than about two waves.
+        // Larger consumer calls generate twice (pass 1, then pass 2 from the
+        // true starts): only states that fill less than about two waves.
         const uint64_t target = sms * 128;
         if (groups * 2 > target) return 1;
         K = std::min<uint64_t>(target / groups, std::max<uint64_t>(1, n / kMinAutoSegment));
@@ -918,6 +970,34 @@ ci_status split_launch(const ci_states_s &hs, uint64_t n, int sink, uint32_t *ou
             e = split_run(*h, sink, none, -1, 0, 1, 1, n, n, out, ld, col0, aux, stream);
         }
         return e == cudaSuccess ? CI_OK : cuda_fail(e, "split run");
+    }
+    // BBS-source consumer sinks: generation is the cost, so the outputs are
+    // written (and fixed up) once into a scratch of at most kScratchWords
+    // words and reduced into the sink, instead of generating the segments
+    // twice; larger calls take the regenerate form below.
+    if (sink != CI_SINK_WRITTEN && (bbs || b16) && h->S <= kScratchWords / n) {
+        uint32_t *rows = nullptr;
+        if ((e = cudaMallocAsync(reinterpret_cast<void **>(&rows), 4 * h->S * n, stream)) != cudaSuccess)
+            return cuda_fail(e, "scratch outputs");
+        ci_status st = CI_OK;
+        if (sink == CI_SINK_DIGEST && (e = cudaMemsetAsync(aux, 0, 8 * h->S, stream)) != cudaSuccess)
+            st = cuda_fail(e, "clearing digests");
+        if (st == CI_OK) st = split_launch(*h, n, CI_SINK_WRITTEN, rows, n, 0, nullptr, K, stream);
+        if (st == CI_OK) {
+            // about four waves of 8-warp blocks; chunks of whole 64-output steps
+            const uint64_t target = (uint64_t)sm_count() * 8 * 16;
+            uint64_t chunks = std::max<uint64_t>(1, std::min<uint64_t>((target + h->S - 1) / h->S, n / 1024));
+            const uint64_t clen = ((n + chunks - 1) / chunks + 63) / 64 * 64;
+            chunks = (n + clen - 1) / clen;
+            const int blocks = (int)std::min<uint64_t>(h->S * chunks, (uint64_t)sm_count() * 16);
+            if (sink == CI_SINK_DIGEST)
+                k_consume_rows<true><<<blocks, 256, 0, stream>>>(rows, h->S, n, clen, chunks, aux);
+            else
+                k_consume_rows<false><<<blocks, 256, 0, stream>>>(rows, h->S, n, clen, chunks, aux);
+            if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "consuming scratch outputs");
+        }
+        cudaFreeAsync(rows, stream);
+        return st;
     }
     if ((e = ensure_jump_tables(stream)) != cudaSuccess) return cuda_fail(e, "jump tables");
     const uint64_t groups = h->P / 32;

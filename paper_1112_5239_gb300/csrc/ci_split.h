@@ -18,10 +18,12 @@ constexpr uint32_t kSplitMaxSegments = 8192;
 uint64_t split_segments(const ci_states_s &h, uint64_t n, uint64_t requested);
 
 // Segment count ci_generate_bbs (and the BBS consumer calls) use on their
-// own for CI_VAR_BBS states, 1 for others.  Written sink: from the GPU size
-// and the form split_launch takes (one launch from 12 warp groups per SM on,
-// three launches below); consumer sinks, which generate twice: > 1 only for
-// states that fill less than about two waves of resident warps.
+// own for CI_VAR_BBS states, 1 for others.  Written sink, and consumer sinks
+// whose outputs fit the scratch (2^29 words; they are written, fixed up and
+// reduced): from the GPU size and the form split_launch takes (one launch
+// from 12 warp groups per SM on, three launches below); larger consumer
+// calls, which generate twice: > 1 only for states that fill less than about
+// two waves of resident warps.
 uint64_t split_auto_bbs(const ci_states_s &h, uint64_t n, int sink);
 
 // Segment count the single-call entry points use on their own for `sink`

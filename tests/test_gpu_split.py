@@ -199,3 +199,42 @@ def test_single_calls_split_narrow_bbs16_states_on_their_own():
     hits = (((o[:, 0::2] >> 8).astype(np.uint64) ** 2 + (o[:, 1::2] >> 8).astype(np.uint64) ** 2) < (1 << 48)).sum(axis=1)
     assert np.array_equal(c, hits.astype(np.uint64))
     assert np.array_equal(u32(st.generate(100)), orc.streams(100))
+
+
+@pytest.mark.parametrize("variant", ["bbs", "bbs16"])
+def test_consumer_sinks_through_the_scratch_form(variant):
+    """BBS-source consumer calls write their segments' outputs into a scratch,
+    fix them up and count or digest them there.  Rows long enough for several
+    chunks per row (4096 outputs, 2 streams short of a whole warp group),
+    and a chunk count whose last chunk is ragged: quarter-circle counts
+    (added to what the array holds) and digests equal the oracle's, and the
+    state continues exactly."""
+    torch, ci = cuda_or_skip()
+    S, C, n = 30, 32, 4096 + 320
+    st = _states(ci, variant, "xor128", C, 57, S)
+    orc = oracle_gen(variant, "xor128", C, 57, 64, S)
+    d = st.generate_split(n, sink="digest", segments=8).cpu().numpy().view(np.uint64)
+    assert np.array_equal(d, digest_rows(orc.streams(n)))
+    counts = torch.full((S,), 5, dtype=torch.int64, device="cuda")
+    st.generate_split(n, sink="qc", out=counts, segments=8)
+    o = orc.streams(n)
+    hits = (((o[:, 0::2] >> 8).astype(np.uint64) ** 2 + (o[:, 1::2] >> 8).astype(np.uint64) ** 2) < (1 << 48)).sum(axis=1)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint64), hits.astype(np.uint64) + 5)
+    assert np.array_equal(u32(st.generate(64)), orc.streams(64))
+
+
+def test_large_bbs_consumer_call_takes_the_regenerate_form():
+    """Above 2^29 outputs a BBS consumer call generates its segments twice
+    (no scratch); digests and counts equal those of one unsplit launch of the
+    single-call kernel, which the oracle pins elsewhere."""
+    torch, ci = cuda_or_skip()
+    S, n = 1056, 1 << 19  # 5.5e8 outputs
+    a = _states(ci, "bbs", "xor128", 32, 61, S)
+    b = _states(ci, "bbs", "xor128", 32, 61, S)
+    da = a.generate_split(n, sink="digest", segments=16).cpu().numpy()
+    db = b.generate_split(n, sink="digest", segments=1).cpu().numpy()
+    assert np.array_equal(da, db)
+    ca = a.generate_split(n, sink="qc", segments=16).cpu().numpy()
+    cb = b.generate_split(n, sink="qc", segments=1).cpu().numpy()
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(a.export_state(), b.export_state())
